@@ -1,0 +1,277 @@
+"""ctypes wrapper of the FP64 CPU oracle (TEST INFRASTRUCTURE ONLY).
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg may import
+this module.  It builds ``mm_oracle.c`` with gcc into ``oracle/_build`` and
+composes one hydro step in the order of the paper's outline (Sec. 2):
+tessellate -> charges to states -> mesh velocity and CFL timestep ->
+limited gradient and half step -> limited half-step gradient -> face fluxes
+in the face frame -> charge update -> drift.
+
+Arrays are array-of-structs float64: pos (n,3), W and U (n,5), grad (n,5,3).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SRC = os.path.join(_HERE, "mm_oracle.c")
+_HDR = os.path.join(_HERE, "mm_oracle.h")
+_LIB = os.path.join(_BUILD, "libmm_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+AREA_REL = 1e-10  # faces below this fraction of V^(2/3) are dropped (tie rule)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (plain C, -O2, no fast-math) if it is out of date."""
+    os.makedirs(_BUILD, exist_ok=True)
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=gnu11", "-fno-fast-math",
+                               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Cfg(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("cfl", ctypes.c_double), ("eta", ctypes.c_double),
+                ("chi", ctypes.c_double), ("zeta", ctypes.c_double), ("theta", ctypes.c_double),
+                ("rho_floor", ctypes.c_double), ("eps_floor", ctypes.c_double),
+                ("limiter", ctypes.c_int), ("regularize", ctypes.c_int)]
+
+
+def make_cfg(gamma=5.0 / 3.0, cfl=0.3, eta=1.0, chi=1.0, zeta=0.25, theta=0.49,
+             rho_floor=1e-10, eps_floor=1e-10, limiter=1, regularize=0) -> Cfg:
+    return Cfg(gamma, cfl, eta, chi, zeta, theta, rho_floor, eps_floor, limiter, regularize)
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            L.orc_tessellate.argtypes = [_I64, _P, _P, ctypes.c_int, ctypes.c_double, _P, _P, _I64, _P,
+                                         _P, _P, _P, _P, _P, _P]
+            L.orc_tessellate.restype = ctypes.c_int
+            L.orc_tessellate_subset.argtypes = [_I64, _P, _P, ctypes.c_double, _I64, _P, _P, _P, _I64,
+                                                _P, _P, _P, _P, _P, _P, _P]
+            L.orc_tessellate_subset.restype = ctypes.c_int
+            L.orc_gradient.argtypes = [_I64, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
+            L.orc_half_step.argtypes = [_I64, _P, _P, _P, ctypes.c_double, _P]
+            L.orc_face_flux.argtypes = [_I64, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                                        _P, _P]
+            L.orc_update.argtypes = [_I64, _I64, _P, _P, _P, ctypes.c_double, _P, _P, _P]
+            L.orc_mesh_velocity.argtypes = [_I64, _P, _P, _P, _P, _P, _P]
+            L.orc_timestep.argtypes = [_I64, _P, _P, _P, _P]
+            L.orc_timestep.restype = ctypes.c_double
+            L.orc_drift.argtypes = [_I64, _P, _P, ctypes.c_double, _P]
+            L.orc_floor_state.argtypes = [_P, _P, _P, _P]
+            L.orc_euler_flux.argtypes = [_P, _P, ctypes.c_double, _P]
+            L.orc_flux_jacobian.argtypes = [_P, ctypes.c_int, ctypes.c_double, _P]
+            L.orc_riemann_lab.argtypes = [_P, _P, _P, _P, _P, _P]
+            L.orc_hllc_1d.argtypes = [_P, _P, ctypes.c_double, _P]
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dtype=np.float64):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def tessellate(pos, box, mode=1, area_rel=AREA_REL, cells=None):
+    """Voronoi cells of the periodic box (Sec. 3).  Returns a dict with
+    volume (n,), centroid (n,3) and the directed faces cell, nb, shift (k,3),
+    area, normal (k,3), centroid (k,3).  ``cells`` restricts the work to a
+    subset (grid mode); volume/centroid are then only valid on that subset."""
+    pos = _c(pos)
+    box = _c(box)
+    n = pos.shape[0]
+    m = n if cells is None else len(cells)
+    cap = max(64, 48 * m)
+    vol = np.zeros(n)
+    cen = np.zeros((n, 3))
+    f_cell = np.zeros(cap, np.int32)
+    f_nb = np.zeros(cap, np.int32)
+    f_sh = np.zeros((cap, 3), np.int32)
+    f_a = np.zeros(cap)
+    f_n = np.zeros((cap, 3))
+    f_c = np.zeros((cap, 3))
+    nf = ctypes.c_int64(0)
+    L = lib()
+    if cells is None:
+        rc = L.orc_tessellate(n, _p(pos), _p(box), mode, area_rel, _p(vol), _p(cen), cap,
+                              ctypes.byref(nf), _p(f_cell), _p(f_nb), _p(f_sh), _p(f_a), _p(f_n),
+                              _p(f_c))
+    else:
+        cl = _c(cells, np.int64)
+        rc = L.orc_tessellate_subset(n, _p(pos), _p(box), area_rel, m, _p(cl), _p(vol), _p(cen),
+                                     cap, ctypes.byref(nf), _p(f_cell), _p(f_nb), _p(f_sh), _p(f_a),
+                                     _p(f_n), _p(f_c))
+    if rc != 0:
+        raise OracleError(f"orc_tessellate failed with code {rc}")
+    k = nf.value
+    return dict(volume=vol, centroid=cen, cell=f_cell[:k].copy(), nb=f_nb[:k].copy(),
+                shift=f_sh[:k].copy(), area=f_a[:k].copy(), normal=f_n[:k].copy(),
+                fcentroid=f_c[:k].copy(), box=box.copy(), n=n)
+
+
+def shift_code(shift):
+    s = np.asarray(shift)
+    return (s[..., 0] + 1) + 3 * (s[..., 1] + 1) + 9 * (s[..., 2] + 1)
+
+
+def unique_faces(T):
+    """One record per shared face: i < j, or i == j with the image shift
+    whose code is above the zero-shift code (the other copy is its mirror)."""
+    code = shift_code(T["shift"])
+    keep = (T["cell"] < T["nb"]) | ((T["cell"] == T["nb"]) & (code > 13))
+    return dict(i=T["cell"][keep].copy(), j=T["nb"][keep].copy(), shift=T["shift"][keep].copy(),
+                area=T["area"][keep].copy(), normal=T["normal"][keep].copy(),
+                centroid=T["fcentroid"][keep].copy())
+
+
+def charges_from_prims(volume, rho, vel, pres, gamma, e_add=None):
+    """U = W V with W = (rho, rho v, P/(gamma-1) + rho v^2/2) (Sec. 4)."""
+    vol = np.asarray(volume)
+    W = np.zeros((vol.shape[0], 5))
+    W[:, 0] = rho
+    W[:, 1:4] = rho[:, None] * vel
+    W[:, 4] = pres / (gamma - 1.0) + 0.5 * rho * np.sum(vel * vel, axis=1)
+    U = W * vol[:, None]
+    if e_add is not None:
+        U[:, 4] += e_add
+    return U
+
+
+def gradient(F, volume, centroid, box, W, cfg):
+    n = W.shape[0]
+    grad = np.zeros((n, 5, 3))
+    fi, fj, sh = _c(F["i"], np.int32), _c(F["j"], np.int32), _c(F["shift"], np.int32)
+    area, nrm = _c(F["area"]), _c(F["normal"])
+    cen, box, W = _c(centroid), _c(box), _c(W)
+    lib().orc_gradient(n, fi.shape[0], _p(fi), _p(fj), _p(sh), _p(area), _p(nrm), _p(cen), _p(box),
+                       _p(W), ctypes.byref(cfg), _p(grad))
+    return grad
+
+
+def half_step(W, grad, cfg, dt):
+    W, grad = _c(W), _c(grad)
+    Wh = np.zeros_like(W)
+    lib().orc_half_step(W.shape[0], _p(W), _p(grad), ctypes.byref(cfg), float(dt), _p(Wh))
+    return Wh
+
+
+def face_flux(F, pos, centroid, box, Wh, grad, w, cfg):
+    nf = F["i"].shape[0]
+    flux = np.zeros((nf, 5))
+    fi, fj, sh = _c(F["i"], np.int32), _c(F["j"], np.int32), _c(F["shift"], np.int32)
+    area, nrm, fc = _c(F["area"]), _c(F["normal"]), _c(F["centroid"])
+    pos, cen, box, Wh, grad, w = _c(pos), _c(centroid), _c(box), _c(Wh), _c(grad), _c(w)
+    lib().orc_face_flux(Wh.shape[0], nf, _p(fi), _p(fj), _p(sh), _p(area), _p(nrm), _p(fc), _p(pos),
+                        _p(cen), _p(box), _p(Wh), _p(grad), _p(w), ctypes.byref(cfg), _p(flux))
+    return flux
+
+
+def update(F, flux, dt, volume, cfg, U):
+    U = _c(U).copy()
+    fi, fj = _c(F["i"], np.int32), _c(F["j"], np.int32)
+    flux, vol = _c(flux), _c(volume)
+    lib().orc_update(U.shape[0], fi.shape[0], _p(fi), _p(fj), _p(flux), float(dt), _p(vol),
+                     ctypes.byref(cfg), _p(U))
+    return U
+
+
+def mesh_velocity(pos, U, volume, centroid, cfg):
+    pos, U, vol, cen = _c(pos), _c(U), _c(volume), _c(centroid)
+    w = np.zeros((U.shape[0], 3))
+    lib().orc_mesh_velocity(U.shape[0], _p(pos), _p(U), _p(vol), _p(cen), ctypes.byref(cfg), _p(w))
+    return w
+
+
+def timestep(U, volume, w, cfg):
+    U, vol, w = _c(U), _c(volume), _c(w)
+    return lib().orc_timestep(U.shape[0], _p(U), _p(vol), _p(w), ctypes.byref(cfg))
+
+
+def drift(pos, w, dt, box):
+    pos = _c(pos).copy()
+    w, box = _c(w), _c(box)
+    lib().orc_drift(pos.shape[0], _p(pos), _p(w), float(dt), _p(box))
+    return pos
+
+
+def floor_state(W, cfg):
+    W = _c(W)
+    out = np.zeros(5)
+    ch = ctypes.c_int(0)
+    lib().orc_floor_state(_p(W), ctypes.byref(cfg), _p(out), ctypes.byref(ch))
+    return out, bool(ch.value)
+
+
+def euler_flux(W, nrm, gamma):
+    W, nrm = _c(W), _c(nrm)
+    F = np.zeros(5)
+    lib().orc_euler_flux(_p(W), _p(nrm), float(gamma), _p(F))
+    return F
+
+
+def flux_jacobian(W, d, gamma):
+    W = _c(W)
+    A = np.zeros((5, 5))
+    lib().orc_flux_jacobian(_p(W), int(d), float(gamma), _p(A))
+    return A
+
+
+def riemann_lab(WL, WR, nrm, wface, cfg):
+    WL, WR, nrm, wface = _c(WL), _c(WR), _c(nrm), _c(wface)
+    F = np.zeros(5)
+    lib().orc_riemann_lab(_p(WL), _p(WR), _p(nrm), _p(wface), ctypes.byref(cfg), _p(F))
+    return F
+
+
+def hllc_1d(primL, primR, gamma):
+    L, R = _c(primL), _c(primR)
+    F = np.zeros(5)
+    lib().orc_hllc_1d(_p(L), _p(R), float(gamma), _p(F))
+    return F
+
+
+def step(pos, U, box, cfg, mode=1, dt=None, tess=None):
+    """One step of the moving-mesh method (Sec. 2), returning every stage."""
+    pos = _c(pos)
+    T = tess if tess is not None else tessellate(pos, box, mode)
+    F = unique_faces(T)
+    vol, cen = T["volume"], T["centroid"]
+    W = U / vol[:, None]
+    w = mesh_velocity(pos, U, vol, cen, cfg)
+    dt_cfl = timestep(U, vol, w, cfg)
+    if dt is None:
+        dt = dt_cfl
+    g0 = gradient(F, vol, cen, box, W, cfg)
+    Wh = half_step(W, g0, cfg, dt)
+    g1 = gradient(F, vol, cen, box, Wh, cfg)
+    flux = face_flux(F, pos, cen, box, Wh, g1, w, cfg)
+    U1 = update(F, flux, dt, vol, cfg, U)
+    pos1 = drift(pos, w, dt, box)
+    return dict(tess=T, faces=F, W=W, w=w, dt=dt, dt_cfl=dt_cfl, grad0=g0, Wh=Wh, grad1=g1,
+                flux=flux, U=U1, pos=pos1)
