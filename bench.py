@@ -1,0 +1,321 @@
+#!/usr/bin/env python
+"""Throughput of the moving-mesh hot path on GB300: cell-updates per second.
+
+One step = one pass of the whole path on the resident state (pos, U):
+bin generators, clip every Voronoi cell, compact faces, mesh velocity and CFL
+timestep, limited gradient + half step, limited half-step gradient, face-frame
+HLLC fluxes, conservative update, drift (mm_step).
+
+Default workload: the 3-D shear layer with 256^3 jittered-lattice generators
+in the periodic unit box (inputs far larger than L2).  With N GPUs every rank
+advances its own copy of the box (independent replicas, weak scaling); value
+is the cells all ranks updated divided by the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle instead (a bounded sample of the
+same workload recipe per step, on the host cores), printing the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s per GB300 (tessellate+MUSCL flux), plain FP64 vs mixed/batched"
+UNIT = "cell-updates/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--n-side", type=int, default=256, help="shear layer generators per axis")
+    p.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--cpu-sample-side", type=int, default=24)
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# --------------------------------------------------------------------------- clocks
+CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def clocks_start(gpu_index):
+    f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+    try:
+        proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={CLOCK_Q}",
+                                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=f,
+                                stderr=subprocess.DEVNULL)
+    except (OSError, ValueError):
+        proc = None
+    return proc, f.name
+
+
+def clocks_stop(proc, path):
+    if proc is not None:
+        proc.terminate()
+        try:
+            proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            proc.kill()
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    try:
+        for line in open(path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower() == "active":
+                    reasons.add(nm)
+    finally:
+        try:
+            os.unlink(path)
+        except OSError:
+            pass
+    return {"sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(smax) if smax else None,
+            "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- peaks
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------- oracle timing
+def oracle_rate(n_side, seconds, gamma_cfg=None):
+    """Cells per second of the oracle's whole step (tessellation + hydro) on
+    the shear-layer recipe at n_side^3 generators; one thread."""
+    from oracle import oracle as O
+    from paper_1707_05333_gb300 import workloads as WL
+    O.build()
+    w = WL.shear_layer(n_side)
+    cfg = O.make_cfg(gamma=w.gamma, cfl=w.cfl, limiter=1)
+    T = O.tessellate(w.pos, w.box, 1)
+    U = O.charges_from_prims(T["volume"], w.rho, w.vel, w.pres, w.gamma)
+    pos = w.pos
+    cells, t0 = 0, time.perf_counter()
+    steps = 0
+    while True:
+        S = O.step(pos, U, w.box, cfg, mode=1)
+        pos, U = S["pos"], S["U"]
+        cells += w.n
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return cells / el, steps, el, w.n
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state beyond the first build
+    from oracle import oracle as O
+    O.build()
+    side = args.cpu_sample_side
+    total_cells, total_t = 0, 0.0
+    per_step = max(1.0, args.cpu_seconds / max(1, args.steps))
+    for _ in range(args.steps):
+        rate, steps, el, n = oracle_rate(side, per_step)
+        total_cells += rate * el
+        total_t += el
+    value = total_cells / total_t
+    sample = f"shear-layer recipe at {side}^3 generators, whole oracle step, {args.steps} x ~{per_step:.0f} s"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * (side ** 3) / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"shear_layer_{args.n_side}^3", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- our path
+# Algorithmic HBM bytes per launch of the memory-bound stages, from the data
+# layout (FP64, struct of arrays): n cells, F unique faces, I = 2F incidences.
+def algorithmic_bytes(stage, n, F):
+    I = 2 * F
+    if stage == "gradient_half_step":
+        # U, V, c of every cell + per incidence (face id, A, n, shift, i/j) + neighbour U,V,c gathers; write W_half
+        return n * (5 * 8 + 8 + 24) + n * 4 + I * 4 + F * (8 + 24 + 12) + n * 5 * 8
+    if stage == "gradient":
+        return n * (5 * 8 + 24) + n * 4 + I * 4 + F * (8 + 24 + 12) + n * 15 * 8
+    if stage == "face_flux":
+        return F * (12 + 8 + 24 + 24) + n * (5 + 15 + 3 + 3 + 3) * 8 + F * 5 * 8
+    if stage == "update":
+        return n * 4 + I * 4 + F * 5 * 8 + n * (8 + 2 * 5 * 8)
+    if stage == "clip":
+        # compulsory: sorted generators in, volume + centroid + face slots out
+        return n * 32 + n * 32 + F * 2 * (4 + 1 + 8 + 24)
+    return None
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_1707_05333_gb300 import build as B
+    from paper_1707_05333_gb300 import binding as BD
+    from paper_1707_05333_gb300 import workloads as WL
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    B.build()
+    w = WL.shear_layer(args.n_side)
+    prec = 0 if args.precision == "fp64" else 1
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = BD.Context(stream=stream, gamma=w.gamma, cfl=w.cfl, limiter=1, precision=prec)
+        pos0 = torch.tensor(w.pos.T.copy(), dtype=torch.float64, device="cuda")
+        mesh = ctx.mm_tessellate(pos0, w.box)
+        U0 = ctx.mm_prims_to_charges(mesh, torch.tensor(w.rho, device="cuda"),
+                                     torch.tensor(w.vel.T.copy(), device="cuda"),
+                                     torch.tensor(w.pres, device="cuda"))
+        pos, U = pos0.clone(), U0.clone()
+        for _ in range(args.warmup):
+            ctx.mm_step(pos, U, w.box)
+        stream.synchronize()
+
+        def barrier():
+            if world > 1:
+                import torch.distributed as dist
+                dist.barrier()
+
+        # ---- device-resident timed region
+        ctx.mm_set_timing(True)
+        launches0 = ctx.mm_kernel_launches()
+        barrier()
+        torch.cuda.synchronize()
+        proc, cpath = clocks_start(local)
+        time.sleep(0.3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            ctx.mm_step(pos, U, w.box)
+        e1.record(stream)
+        stream.synchronize()
+        torch.cuda.synchronize()
+        barrier()
+        clocks = clocks_stop(proc, cpath)
+        launches = ctx.mm_kernel_launches() - launches0
+        ms = e0.elapsed_time(e1)
+        stages = ctx.mm_stage_times()
+        ctx.mm_set_timing(False)
+        nf = ctx.mm_tessellate(pos, w.box).nfaces  # faces of the current mesh, for the byte counts
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        n = w.n
+        value = world * n * args.steps / (ms / 1e3)
+
+        # ---- end to end through the ABI with host buffers
+        pos_h = torch.empty_like(pos, device="cpu").pin_memory()
+        U_h = torch.empty_like(U, device="cpu").pin_memory()
+        pos_h.copy_(pos0.cpu())
+        U_h.copy_(U0.cpu())
+        pd, Ud = torch.empty_like(pos), torch.empty_like(U)
+        barrier()
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.e2e_steps):
+            pd.copy_(pos_h, non_blocking=True)
+            Ud.copy_(U_h, non_blocking=True)
+            ctx.mm_step(pd, Ud, w.box)
+            pos_h.copy_(pd, non_blocking=True)
+            U_h.copy_(Ud, non_blocking=True)
+        f1.record(stream)
+        stream.synchronize()
+        e2e_ms = f0.elapsed_time(f1)
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": world * n * args.e2e_steps / (e2e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(pos.numel() * 8 + U.numel() * 8),
+               "d2h_bytes_per_step": int(pos.numel() * 8 + U.numel() * 8)}
+
+    # ---- roofline of the dominant kernel, from the live stage times
+    dom = max(stages, key=lambda k: stages[k][0])
+    dom_ms = stages[dom][0] / max(1, stages[dom][1])
+    peak, peak_kind = measured_peaks()
+    byts = algorithmic_bytes(dom, n, nf)
+    roofline = None
+    if byts is not None:
+        ach = byts / (dom_ms / 1e3) / 1e9
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                    "frac": ach / peak, "traffic": None, "peak_source": peak_kind,
+                    "algorithmic_bytes_per_launch": byts, "launch_ms": dom_ms}
+    stage_ms = {k: v[0] / max(1, v[1]) for k, v in stages.items()}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, steps, el, ncpu = oracle_rate(args.cpu_sample_side, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"shear-layer recipe at {args.cpu_sample_side}^3 generators, {steps} whole oracle "
+                         f"steps in {el:.1f} s, one thread"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f64+f32",
+                "data": "synthetic",
+                "config": {"workload": f"shear_layer_{args.n_side}^3", "cells": n, "faces": nf,
+                           "precision": args.precision, "parallelism": f"replicas x{world}",
+                           "l2": "inputs larger than L2 (state + mesh >> 129 MB), no flush"},
+                "roofline": roofline, "stage_ms": stage_ms, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,198 @@
+/* mm.h -- C ABI of the GB300 moving-mesh hot path (arXiv:1707.05333).
+ *
+ * One call sequence advances a periodic box of Voronoi cells by one step of
+ * the paper's arbitrary Lagrangian-Eulerian scheme (Sec. 2):
+ *   mm_tessellate     Voronoi cells of the generators by half-space clipping (Sec. 3)
+ *   mm_mesh_velocity  generator velocities w = eta v + roundness correction (Sec. 4.2)
+ *   mm_timestep       global CFL timestep, kept on the device (Sec. 4.2)
+ *   mm_flux_step      limited gradients, half step, face reconstruction, face-frame
+ *                     HLLC and the conservative charge update (Sec. 4, 4.1)
+ *   mm_drift          move the generators by w dt (Sec. 2, step 5)
+ * mm_step runs the whole sequence; mm_gradients exposes the gradient stage.
+ *
+ * Conventions for every call:
+ *  - Arrays passed in are DEVICE pointers owned by the caller, struct-of-
+ *    arrays, float64: positions pos[3][n] (x row, y row, z row), charges
+ *    U[5][n] = (mass, momentum x,y,z, total energy) per cell, per-volume
+ *    states W[5][n] = U / V, velocities w[3][n], gradients grad[15][n] with
+ *    row 3*k+d holding d(W_k)/dx_d.  n >= 1 and n <= MM_MAX_CELLS.
+ *  - Positions must lie in [0, box[d]); generators must be distinct.
+ *  - Every call is enqueued on the context's stream and returns without
+ *    waiting, except mm_tessellate and mm_step, which wait once for the
+ *    face count and the device status word.
+ *  - No call aborts.  A failure returns a nonzero mm_status and
+ *    mm_last_error() describes it; device-side failures (a cell whose
+ *    candidate, plane or vertex list overflowed, non-finite input) are
+ *    reported by the next call that reads the status word.
+ *  - Not thread-safe per context; distinct contexts are independent.
+ */
+#ifndef MM_H
+#define MM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MM_MAX_CELLS 100000000LL /* index arithmetic is 32-bit per face/incidence */
+
+typedef enum {
+    MM_OK = 0,
+    MM_EINVAL = 1,      /* bad argument, position outside the box, non-finite value */
+    MM_ENOMEM = 2,      /* device allocation failed                                  */
+    MM_ECAPACITY = 3,   /* a cell exceeded a fixed per-cell list (see mm_config)     */
+    MM_EDEGENERATE = 4, /* clipping met an inconsistent (numerically degenerate) cut */
+    MM_ECUDA = 5,       /* a CUDA runtime call failed                               */
+    MM_ETIMEOUT = 6     /* reserved: a bounded device wait gave up                   */
+} mm_status;
+
+typedef struct {
+    double gamma;     /* ideal-gas index: P = (gamma - 1) rho eps (Sec. 6)                  */
+    double cfl;       /* eta_CFL of the per-cell timestep (Sec. 4.2)                        */
+    double eta;       /* mesh velocity w = eta v; 0 static mesh, 1 Lagrangian (Sec. 4.2)    */
+    double chi;       /* roundness correction speed, in sound speeds (Sec. 4.2)             */
+    double zeta;      /* roundness correction radius, in effective radii (Sec. 4.2)         */
+    double theta;     /* Duffell-MacFadyen limiter parameter (Sec. 4.1)                      */
+    double rho_floor; /* density floor (Sec. 4.1)                                           */
+    double eps_floor; /* specific internal energy floor (Sec. 4.1)                          */
+    double area_rel;  /* faces with area <= area_rel (V_box/n)^(2/3) are dropped            */
+    int limiter;      /* 0 none, 1 S10, 2 S10 times Duffell-MacFadyen (Sec. 4.1)            */
+    int regularize;   /* 1: add the roundness correction to w (Sec. 4.2)                    */
+    int precision;    /* 0: plain FP64 throughout; 1: mixed (see mm_set_precision)          */
+    int reserved;
+} mm_config;
+
+/* Fill a config with the defaults: gamma 5/3, cfl 0.3, eta 1, chi 1, zeta
+ * 0.25, theta 0.49, floors 1e-10, area_rel 1e-10, S10 limiter, no
+ * roundness correction, FP64. */
+void mm_default_config(mm_config *cfg);
+
+typedef struct mm_ctx mm_ctx;
+
+/* The mesh of the last mm_tessellate: DEVICE pointers owned by the context,
+ * valid until the next mm_tessellate / mm_step or mm_destroy.
+ * Faces are unique: face f joins cells face_i[f] and face_j[f], where the
+ * neighbour sits at its periodic image pos_j + s L with s decoded from
+ * face_shift[f] = (sx+1) + 3 (sy+1) + 9 (sz+1); face_i < face_j, or
+ * face_i == face_j with face_shift > 13 (a cell touching its own image).
+ * face_normal is the unit vector from i towards j's image; face_centroid is
+ * in cell i's frame (add -s L for j's).  Cell k's faces are
+ * inc_face[inc_off[k] .. inc_off[k+1]); an entry f >= 0 means k is face_i[f]
+ * (outward normal +n), an entry ~f (< 0) means k is face_j[f] (normal -n).
+ * cell_centroid is r_k + (centroid relative to r_k): it may lie outside the
+ * box near the boundary. */
+typedef struct {
+    int64_t n, nfaces, nincident;
+    int64_t face_stride; /* row stride of face_normal and face_centroid (>= nfaces) */
+    double box[3];
+    const int32_t *face_i, *face_j, *face_shift;
+    const double *face_area;     /* [F]    */
+    const double *face_normal;   /* [3][face_stride] */
+    const double *face_centroid; /* [3][face_stride] */
+    const double *cell_volume;   /* [n]    */
+    const double *cell_centroid; /* [3][n] */
+    const int32_t *inc_off;      /* [n+1]  */
+    const int32_t *inc_face;     /* [nincident] */
+} mm_mesh;
+
+/* Create a context whose work runs on `cuda_stream` (a cudaStream_t, or NULL
+ * for the legacy default stream) of the current device.  The context owns
+ * its device workspace and grows it on demand. */
+mm_status mm_create(mm_ctx **ctx, const mm_config *cfg, void *cuda_stream);
+void mm_destroy(mm_ctx *ctx);
+const char *mm_last_error(const mm_ctx *ctx);
+mm_status mm_set_config(mm_ctx *ctx, const mm_config *cfg);
+
+/* Voronoi tessellation of the periodic box [0,box) (Sec. 3).  Each cell
+ * starts as the box centred on its generator (whose six faces are the
+ * bisectors with the generator's own images) and is clipped by the
+ * bisector planes of neighbouring generators and images in increasing
+ * distance, until every remaining generator is more than twice as far as
+ * the farthest vertex.  pos[3][n] device.  Waits for completion. */
+mm_status mm_tessellate(mm_ctx *ctx, const double *pos, int64_t n, const double box[3], mm_mesh *out);
+
+/* Limited cell-centred gradient of per-volume states W[5][n] (Sec. 4.1):
+ * grad W_i = M_i^-1 b_i with M_i = 1/2 sum_j A n (x) (c_j - c_i) and
+ * b_i = 1/2 sum_j A (W_j - W_i) n, then the S10 factor min(1, psi_ij) and,
+ * for limiter 2, the Duffell-MacFadyen factor.  grad[15][n] device. */
+mm_status mm_gradients(mm_ctx *ctx, const mm_mesh *mesh, const double *W, double *grad);
+
+/* w = eta v (+ chi c_s d/|d| ramp(|d| / zeta R) when regularize) (Sec. 4.2).
+ * pos[3][n], U[5][n] in; w[3][n] out. */
+mm_status mm_mesh_velocity(mm_ctx *ctx, const mm_mesh *mesh, const double *pos, const double *U,
+                           double *w);
+
+/* dt = min_i cfl R_i / (c_s,i + |v_i - w_i|), written to the device scalar
+ * *dt (Sec. 4.2). */
+mm_status mm_timestep(mm_ctx *ctx, const mm_mesh *mesh, const double *U, const double *w, double *dt);
+
+/* One conservative update of the charges U[5][n] (in place) over the mesh:
+ * gradient of W^n, half step W^(n+1/2) = W^n - dt/2 sum_d A_d dW/dx_d, its
+ * gradient, reconstruction to face centroids, floors, boost into the frame
+ * of each moving face, HLLC, boost back, and U_i -= dt sum_faces (+-) A F
+ * (Sec. 4, 4.1).  dt is a DEVICE pointer to one double (e.g. from
+ * mm_timestep).  pos[3][n] are the generator positions the mesh was built
+ * from; w[3][n] the generator velocities. */
+mm_status mm_flux_step(mm_ctx *ctx, const mm_mesh *mesh, const double *pos, const double *w,
+                       const double *dt, double *U);
+
+/* pos += w dt, wrapped into [0, box) (Sec. 2, step 5).  dt device scalar. */
+mm_status mm_drift(mm_ctx *ctx, double *pos, int64_t n, const double *w, const double *dt,
+                   const double box[3]);
+
+/* One whole step in place: tessellate pos, w = mesh velocity, dt = CFL
+ * timestep (or *dt_fixed when dt_fixed != NULL, a device scalar), flux step
+ * on U, drift pos.  dt_out (device scalar, may be NULL) receives dt and
+ * w_out (device [3][n], may be NULL) receives w. */
+mm_status mm_step(mm_ctx *ctx, double *pos, double *U, int64_t n, const double box[3],
+                  const double *dt_fixed, double *dt_out, double *w_out);
+
+/* Charges from per-volume primitives on the current mesh:
+ * U = (rho, rho v, P/(gamma-1) + rho |v|^2 / 2) V.  rho[n], vel[3][n], P[n]. */
+mm_status mm_prims_to_charges(mm_ctx *ctx, const mm_mesh *mesh, const double *rho, const double *vel,
+                              const double *P, double *U);
+
+/* Per-component totals of U[5][n] as compensated (Neumaier) FP64 sums,
+ * written to the device array totals[5]. */
+mm_status mm_totals(mm_ctx *ctx, const double *U, int64_t n, double *totals);
+
+/* Stream-ordered device-to-device copy of `bytes` bytes (a convenience for
+ * bindings that read the context-owned mesh arrays into their own buffers). */
+mm_status mm_copy(mm_ctx *ctx, void *dst, const void *src, int64_t bytes);
+
+/* Device-side counters of the last tessellation, copied to the host:
+ * [0] max candidates gathered by a cell, [1] max planes, [2] max vertices,
+ * [3] cells needing more than one search ring, [4] total cuts. */
+mm_status mm_tess_stats(mm_ctx *ctx, int64_t stats[5]);
+
+/* Stages of a step, for per-stage device timing. */
+typedef enum {
+    MM_STAGE_BIN = 0,           /* generator binning (neighbour search structure)   */
+    MM_STAGE_CLIP = 1,          /* per-cell clipping                                */
+    MM_STAGE_FACES = 2,         /* face confirmation, scans, unique faces, CSR      */
+    MM_STAGE_MESH_VELOCITY = 3, /* mesh velocity and CFL timestep                   */
+    MM_STAGE_GRADIENT_HALF = 4, /* limited gradient of W^n fused with the half step */
+    MM_STAGE_GRADIENT = 5,      /* limited gradient of W^(n+1/2)                    */
+    MM_STAGE_FACE_FLUX = 6,     /* reconstruction, face-frame HLLC, back-boost      */
+    MM_STAGE_UPDATE = 7,        /* conservative charge update                       */
+    MM_STAGE_DRIFT = 8,         /* generator drift                                  */
+    MM_NSTAGES = 9
+} mm_stage;
+
+/* on != 0: from now on record CUDA events around every stage on the
+ * context's stream (a few microseconds of host work per stage); resets the
+ * accumulated times.  on == 0 stops recording. */
+mm_status mm_set_timing(mm_ctx *ctx, int on);
+
+/* Wait for the stream, then return the summed device time in ms of each
+ * stage since mm_set_timing, and how many times each stage ran. */
+mm_status mm_stage_times(mm_ctx *ctx, double ms[MM_NSTAGES], int64_t runs[MM_NSTAGES]);
+
+/* Number of kernels this context has launched since it was created. */
+int64_t mm_kernel_launches(const mm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,115 @@
+// mm_faces.cu -- unique faces and the per-cell incident-face lists.
+//
+// Every shared face was written twice by the clipper, once from each side.
+// A face counts only if both sides have it (so the two cells always agree on
+// their neighbours); it is stored once, by the cell with the smaller index,
+// or, for a cell touching its own periodic image, by the copy whose image
+// code is above the zero-shift code.  Offsets come from exclusive scans of
+// per-cell counts, so face ids and every cell's incident list are
+// deterministic: no atomics on the data path.
+#include "mm_internal.cuh"
+
+namespace mm {
+
+// Per cell: find the partner slot of each face in the neighbour's list,
+// then mark which faces are confirmed and which this cell stores.
+__global__ void k_face_confirm(int64_t n, Slots sl, unsigned long long *__restrict__ emit_mask,
+                               unsigned long long *__restrict__ conf_mask, signed char *__restrict__ partner,
+                               int *__restrict__ emit_cnt, int *__restrict__ conf_cnt)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int cnt = sl.cnt[i];
+    unsigned long long em = 0, cm = 0;
+    for (int k = 0; k < cnt; ++k) {
+        const int64_t s = i * MAXF + k;
+        const int j = sl.nb[s];
+        const int code = sl.sh[s];
+        const int want = 26 - code;  // the mirrored image seen from j
+        const int cj = sl.cnt[j];
+        int m = -1;
+        for (int t = 0; t < cj; ++t) {
+            const int64_t u = (int64_t)j * MAXF + t;
+            if (sl.nb[u] == (int)i && sl.sh[u] == want) { m = t; break; }
+        }
+        partner[s] = (signed char)m;
+        if (m >= 0) {
+            cm |= 1ull << k;
+            if (i < j || (i == j && code > 13)) em |= 1ull << k;
+        }
+    }
+    emit_mask[i] = em;
+    conf_mask[i] = cm;
+    emit_cnt[i] = __popcll(em);
+    conf_cnt[i] = __popcll(cm);
+}
+
+__global__ void k_face_write(int64_t n, const double *__restrict__ pos, Grid g, Slots sl,
+                             const unsigned long long *__restrict__ emit_mask,
+                             const unsigned long long *__restrict__ conf_mask,
+                             const signed char *__restrict__ partner, const int *__restrict__ face_off,
+                             const int *__restrict__ inc_off, int *__restrict__ face_i, int *__restrict__ face_j,
+                             int *__restrict__ face_shift, double *__restrict__ face_area,
+                             double *__restrict__ face_normal, double *__restrict__ face_cen, int64_t fcap,
+                             int *__restrict__ inc_face)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const unsigned long long em = emit_mask[i], cm = conf_mask[i];
+    const int fbase = face_off[i];
+    int e = inc_off[i];
+    const int64_t ns = n * (int64_t)MAXF;
+    unsigned long long rest = cm;
+    while (rest) {
+        const int k = __ffsll((long long)rest) - 1;
+        rest &= rest - 1;
+        const int64_t s = i * MAXF + k;
+        const int j = sl.nb[s];
+        const int code = sl.sh[s];
+        if ((em >> k) & 1ull) {
+            const int f = fbase + __popcll(em & ((1ull << k) - 1ull));
+            if (f < fcap) {
+                const int sx = code % 3 - 1, sy = (code / 3) % 3 - 1, sz = code / 9 - 1;
+                const double qx = pos[j] + sx * g.box[0] - pos[i];
+                const double qy = pos[n + j] + sy * g.box[1] - pos[n + i];
+                const double qz = pos[2 * n + j] + sz * g.box[2] - pos[2 * n + i];
+                const double inv = 1.0 / sqrt(qx * qx + qy * qy + qz * qz);
+                face_i[f] = (int)i;
+                face_j[f] = j;
+                face_shift[f] = code;
+                face_area[f] = sl.area[s];
+                face_normal[f] = qx * inv;
+                face_normal[fcap + f] = qy * inv;
+                face_normal[2 * fcap + f] = qz * inv;
+                face_cen[f] = sl.fc[s];
+                face_cen[fcap + f] = sl.fc[ns + s];
+                face_cen[2 * fcap + f] = sl.fc[2 * ns + s];
+            }
+            inc_face[e++] = f;
+        } else {
+            const int m = partner[s];
+            const unsigned long long ej = emit_mask[j];
+            const int f = face_off[j] + __popcll(ej & ((1ull << m) - 1ull));
+            inc_face[e++] = ~f;
+        }
+    }
+}
+
+void launch_face_confirm(int64_t n, Slots sl, unsigned long long *emit_mask, unsigned long long *conf_mask,
+                         signed char *partner, int *emit_cnt, int *conf_cnt, cudaStream_t s)
+{
+    int nb = (int)((n + 127) / 128);
+    k_face_confirm<<<nb, 128, 0, s>>>(n, sl, emit_mask, conf_mask, partner, emit_cnt, conf_cnt);
+}
+
+void launch_face_write(int64_t n, const double *pos, const Grid &g, Slots sl, const unsigned long long *emit_mask,
+                       const unsigned long long *conf_mask, const signed char *partner, const int *face_off,
+                       const int *inc_off, int *face_i, int *face_j, int *face_shift, double *face_area,
+                       double *face_normal, double *face_cen, int64_t fcap, int *inc_face, cudaStream_t s)
+{
+    int nb = (int)((n + 127) / 128);
+    k_face_write<<<nb, 128, 0, s>>>(n, pos, g, sl, emit_mask, conf_mask, partner, face_off, inc_off, face_i,
+                                    face_j, face_shift, face_area, face_normal, face_cen, fcap, inc_face);
+}
+
+}  // namespace mm

@@ -1,0 +1,600 @@
+// mm_hydro.cu -- the finite-volume stages of one step on the Voronoi mesh
+// (Sec. 4, 4.1, 4.2).  All loops are cell-centric over the incident-face
+// lists (gradients, update) or face-centric over unique faces (fluxes); no
+// atomics touch the conserved data, so results are bitwise reproducible.
+#include "mm_internal.cuh"
+
+namespace mm {
+
+constexpr unsigned FULL_MASK_HYDRO = 0xffffffffu;
+
+struct Box3 {
+    double L[3];
+};
+
+__device__ __forceinline__ void decode_shift(int code, double &sx, double &sy, double &sz)
+{
+    sx = (double)(code % 3 - 1);
+    sy = (double)((code / 3) % 3 - 1);
+    sz = (double)(code / 9 - 1);
+}
+
+// Neighbour across incident entry e of a cell: other cell, outward normal
+// scale (+1/-1) and the image offset s L of the neighbour in this cell's frame.
+struct Nbr {
+    int f, o;
+    double sg;
+    double ox, oy, oz;
+};
+
+__device__ __forceinline__ Nbr neighbour(const MeshDev &m, int e)
+{
+    Nbr r;
+    int f = m.inc_face[e];
+    bool fwd = f >= 0;
+    if (!fwd) f = ~f;
+    r.f = f;
+    r.o = fwd ? m.face_j[f] : m.face_i[f];
+    r.sg = fwd ? 1.0 : -1.0;
+    double sx, sy, sz;
+    decode_shift(m.face_shift[f], sx, sy, sz);
+    r.ox = r.sg * sx * m.box[0];
+    r.oy = r.sg * sy * m.box[1];
+    r.oz = r.sg * sz * m.box[2];
+    return r;
+}
+
+__device__ __forceinline__ void load5(const double *S, int64_t n, int64_t i, double inv_v, double w[5])
+{
+#pragma unroll
+    for (int k = 0; k < 5; ++k) w[k] = S[k * n + i] * inv_v;
+}
+
+// Floors on density and specific internal energy (Sec. 4.1); momentum kept,
+// energy rewritten only when its floor triggers.  Returns true if changed.
+__device__ __forceinline__ bool apply_floor(double W[5], double rho_floor, double eps_floor)
+{
+    bool ch = false;
+    double rho = W[0];
+    if (!(rho >= rho_floor)) { rho = rho_floor; ch = true; }
+    const double ke = 0.5 * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]) / rho;
+    if (!(W[4] - ke >= rho * eps_floor)) { W[4] = rho * eps_floor + ke; ch = true; }
+    W[0] = rho;
+    return ch;
+}
+
+// ---------------------------------------------------------------------------
+// Gradient + limiter (+ half-step predictor when PREDICT)
+// ---------------------------------------------------------------------------
+template <bool FROM_CHARGES, bool PREDICT>
+__global__ void __launch_bounds__(128) k_gradient(MeshDev m, HydroCfg c, const double *__restrict__ S,
+                                                  double *__restrict__ grad, double *__restrict__ Wh,
+                                                  const double *__restrict__ dtp)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t n = m.n;
+    if (i >= n) return;
+    const double ivi = FROM_CHARGES ? 1.0 / m.vol[i] : 1.0;
+    double Wi[5];
+    load5(S, n, i, ivi, Wi);
+    const double cix = m.cen[i], ciy = m.cen[n + i], ciz = m.cen[2 * n + i];
+    const int e0 = m.inc_off[i], e1 = m.inc_off[i + 1];
+
+    // M = 1/2 sum A n (x) d,  b_k = 1/2 sum A (W_o - W_i)_k n
+    double M[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double b[15];
+    double wmax[5], wmin[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) { wmax[k] = Wi[k]; wmin[k] = Wi[k]; }
+#pragma unroll
+    for (int k = 0; k < 15; ++k) b[k] = 0.0;
+    for (int e = e0; e < e1; ++e) {
+        const Nbr q = neighbour(m, e);
+        const double ha = 0.5 * m.area[q.f];
+        const double nx = q.sg * m.normal[q.f], ny = q.sg * m.normal[m.fs + q.f], nz = q.sg * m.normal[2 * m.fs + q.f];
+        const double dx = m.cen[q.o] + q.ox - cix, dy = m.cen[n + q.o] + q.oy - ciy, dz = m.cen[2 * n + q.o] + q.oz - ciz;
+        const double ax = ha * nx, ay = ha * ny, az = ha * nz;
+        M[0] += ax * dx; M[1] += ax * dy; M[2] += ax * dz;
+        M[3] += ay * dx; M[4] += ay * dy; M[5] += ay * dz;
+        M[6] += az * dx; M[7] += az * dy; M[8] += az * dz;
+        const double ivo = FROM_CHARGES ? 1.0 / m.vol[q.o] : 1.0;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const double wo = S[k * n + q.o] * ivo;
+            const double dw = wo - Wi[k];
+            b[3 * k + 0] += ax * dw;
+            b[3 * k + 1] += ay * dw;
+            b[3 * k + 2] += az * dw;
+            wmax[k] = fmax(wmax[k], wo);
+            wmin[k] = fmin(wmin[k], wo);
+        }
+    }
+    // g = M^-1 b by the adjugate
+    const double c00 = M[4] * M[8] - M[5] * M[7], c01 = M[5] * M[6] - M[3] * M[8], c02 = M[3] * M[7] - M[4] * M[6];
+    const double c10 = M[2] * M[7] - M[1] * M[8], c11 = M[0] * M[8] - M[2] * M[6], c12 = M[1] * M[6] - M[0] * M[7];
+    const double c20 = M[1] * M[5] - M[2] * M[4], c21 = M[2] * M[3] - M[0] * M[5], c22 = M[0] * M[4] - M[1] * M[3];
+    const double idet = 1.0 / (M[0] * c00 + M[1] * c01 + M[2] * c02);
+    double g[15];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const double b0 = b[3 * k], b1 = b[3 * k + 1], b2 = b[3 * k + 2];
+        g[3 * k + 0] = (c00 * b0 + c10 * b1 + c20 * b2) * idet;
+        g[3 * k + 1] = (c01 * b0 + c11 * b1 + c21 * b2) * idet;
+        g[3 * k + 2] = (c02 * b0 + c12 * b1 + c22 * b2) * idet;
+    }
+    if (c.limiter >= 1) {
+        // S10: alpha = min(1, min_j psi_ij); with c_max = W_max - W_i >= 0 and
+        // c_min = W_min - W_i <= 0 the minimum over j is attained at the
+        // largest positive and the most negative Delta_ij = g . d_ij.
+        // DM: min_j max(0, theta (W_j - W_i) / Delta_ij), tracked as a
+        // fraction (num, den > 0) to avoid a division per face.
+        double dmax[5], dmin[5], rn[5], rd[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) { dmax[k] = 0.0; dmin[k] = 0.0; rn[k] = 1.0; rd[k] = 1.0; }
+        for (int e = e0; e < e1; ++e) {
+            const Nbr q = neighbour(m, e);
+            const double dx = m.cen[q.o] + q.ox - cix, dy = m.cen[n + q.o] + q.oy - ciy, dz = m.cen[2 * n + q.o] + q.oz - ciz;
+            const double ivo = FROM_CHARGES ? 1.0 / m.vol[q.o] : 1.0;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                const double del = g[3 * k] * dx + g[3 * k + 1] * dy + g[3 * k + 2] * dz;
+                dmax[k] = fmax(dmax[k], del);
+                dmin[k] = fmin(dmin[k], del);
+                if (c.limiter >= 2 && del != 0.0) {
+                    double num = c.theta * (S[k * n + q.o] * ivo - Wi[k]);
+                    double den = del;
+                    if (den < 0.0) { num = -num; den = -den; }
+                    if (num < 0.0) num = 0.0;
+                    if (num * rd[k] < rn[k] * den) { rn[k] = num; rd[k] = den; }
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            double a = 1.0;
+            if (dmax[k] > 0.0) a = fmin(a, (wmax[k] - Wi[k]) / dmax[k]);
+            if (dmin[k] < 0.0) a = fmin(a, (wmin[k] - Wi[k]) / dmin[k]);
+            if (c.limiter >= 2) a *= fmin(1.0, rn[k] / rd[k]);
+            g[3 * k] *= a;
+            g[3 * k + 1] *= a;
+            g[3 * k + 2] *= a;
+        }
+    }
+    if (!PREDICT) {
+#pragma unroll
+        for (int k = 0; k < 15; ++k) grad[k * n + i] = g[k];
+        return;
+    }
+    // half-step predictor: dW/dt = -div F written through the chain rule on
+    // (rho, m, E):  d_d u_k = (d_d m_k - u_k d_d rho) / rho,
+    // d_d P = (gamma-1)(d_d E - u . d_d m + |u|^2/2 d_d rho)
+    const double gm1 = c.gamma - 1.0;
+    const double ir = 1.0 / Wi[0];
+    const double ux = Wi[1] * ir, uy = Wi[2] * ir, uz = Wi[3] * ir;
+    const double u2 = ux * ux + uy * uy + uz * uz;
+    const double P = gm1 * (Wi[4] - 0.5 * Wi[0] * u2);
+    const double u[3] = {ux, uy, uz};
+    double du[3][3];  // du[k][d] = d u_k / d x_d
+    double dP[3];
+    double divu = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double drho = g[d];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) du[k][d] = (g[3 * (1 + k) + d] - u[k] * drho) * ir;
+        dP[d] = gm1 * (g[12 + d] - (ux * g[3 + d] + uy * g[6 + d] + uz * g[9 + d]) + 0.5 * u2 * drho);
+        divu += du[d][d];
+    }
+    double rate[5];
+    rate[0] = -(g[3] + g[7] + g[11]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double s = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) s += u[d] * g[3 * (1 + k) + d];
+        rate[1 + k] = -(s + Wi[1 + k] * divu) - dP[k];
+    }
+    {
+        double s = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) s += u[d] * (g[12 + d] + dP[d]);
+        rate[4] = -(s + (Wi[4] + P) * divu);
+    }
+    const double hdt = 0.5 * (*dtp);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) Wh[k * n + i] = Wi[k] + hdt * rate[k];
+}
+
+void launch_gradient(const MeshDev &m, const HydroCfg &c, const double *S, bool from_charges, double *grad,
+                     double *W_half, const double *dt, cudaStream_t s)
+{
+    int nb = (int)((m.n + 127) / 128);
+    if (W_half) {
+        if (from_charges) k_gradient<true, true><<<nb, 128, 0, s>>>(m, c, S, grad, W_half, dt);
+        else k_gradient<false, true><<<nb, 128, 0, s>>>(m, c, S, grad, W_half, dt);
+    } else {
+        if (from_charges) k_gradient<true, false><<<nb, 128, 0, s>>>(m, c, S, grad, W_half, dt);
+        else k_gradient<false, false><<<nb, 128, 0, s>>>(m, c, S, grad, W_half, dt);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Face fluxes: reconstruct, floor, boost into the face frame, HLLC, boost back
+// ---------------------------------------------------------------------------
+struct FaceState {
+    double rho, vx, vy, vz, P;  // velocity already in the face frame
+};
+
+// HLLC in vector form along unit normal (nx,ny,nz): the tangential velocity
+// rides along with the normal mass flux, so no explicit tangent basis is
+// needed.  Davis wave speeds; contact speed from the jump conditions.
+__device__ __forceinline__ void hllc(const FaceState &L, const FaceState &R, double nx, double ny, double nz,
+                                     double gamma, double F[5])
+{
+    const double gm1 = gamma - 1.0;
+    const double ul = L.vx * nx + L.vy * ny + L.vz * nz;
+    const double ur = R.vx * nx + R.vy * ny + R.vz * nz;
+    const double cl = sqrt(gamma * L.P / L.rho), cr = sqrt(gamma * R.P / R.rho);
+    const double El = L.P / gm1 + 0.5 * L.rho * (L.vx * L.vx + L.vy * L.vy + L.vz * L.vz);
+    const double Er = R.P / gm1 + 0.5 * R.rho * (R.vx * R.vx + R.vy * R.vy + R.vz * R.vz);
+    const double sl = fmin(ul - cl, ur - cr);
+    const double sr = fmax(ul + cl, ur + cr);
+    const double ml = L.rho * (sl - ul), mr = R.rho * (sr - ur);
+    const double ss = (R.P - L.P + ul * ml - ur * mr) / (ml - mr);
+    // branch order: S_L >= 0 -> F_L; S* >= 0 -> F*_L; S_R > 0 -> F*_R; else F_R
+    const bool left = (sl >= 0.0) || (ss >= 0.0);
+    const bool star = (sl < 0.0) && (left || sr > 0.0);
+    const FaceState &K = left ? L : R;
+    const double uk = left ? ul : ur;
+    const double Ek = left ? El : Er;
+    const double sk = left ? sl : sr;
+    const double mk = K.rho * uk;
+    // physical flux of side K
+    F[0] = mk;
+    F[1] = mk * K.vx + K.P * nx;
+    F[2] = mk * K.vy + K.P * ny;
+    F[3] = mk * K.vz + K.P * nz;
+    F[4] = (Ek + K.P) * uk;
+    if (star) {
+        // U*_K = rho_K (S_K - u_K)/(S_K - S*) (1, v_K + (S* - u_K) n, E_K/rho_K + (S* - u_K)(S* + P_K/(rho_K (S_K - u_K))))
+        const double f = K.rho * (sk - uk) / (sk - ss);
+        const double du = ss - uk;
+        const double es = f * (Ek / K.rho + du * (ss + K.P / (K.rho * (sk - uk))));
+        F[0] += sk * (f - K.rho);
+        F[1] += sk * (f * (K.vx + du * nx) - K.rho * K.vx);
+        F[2] += sk * (f * (K.vy + du * ny) - K.rho * K.vy);
+        F[3] += sk * (f * (K.vz + du * nz) - K.rho * K.vz);
+        F[4] += sk * (es - Ek);
+    }
+}
+
+__global__ void __launch_bounds__(128) k_face_flux(MeshDev m, HydroCfg c, const double *__restrict__ pos,
+                                                   const double *__restrict__ w, const double *__restrict__ Wh,
+                                                   const double *__restrict__ grad, double *__restrict__ flux)
+{
+    const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= m.nf) return;
+    const int64_t n = m.n, fs = m.fs;
+    const int i = m.face_i[f], j = m.face_j[f];
+    double sx, sy, sz;
+    decode_shift(m.face_shift[f], sx, sy, sz);
+    const double ox = sx * m.box[0], oy = sy * m.box[1], oz = sz * m.box[2];
+    const double fx = m.fcen[f], fy = m.fcen[fs + f], fz = m.fcen[2 * fs + f];
+    const double nx = m.normal[f], ny = m.normal[fs + f], nz = m.normal[2 * fs + f];
+    // reconstruction to the face centroid: W_face = W_half + (x_f - c) . grad
+    const double dlx = fx - m.cen[i], dly = fy - m.cen[n + i], dlz = fz - m.cen[2 * n + i];
+    const double drx = fx - (m.cen[j] + ox), dry = fy - (m.cen[n + j] + oy), drz = fz - (m.cen[2 * n + j] + oz);
+    double WL[5], WR[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        WL[k] = Wh[k * n + i] + dlx * grad[(3 * k) * n + i] + dly * grad[(3 * k + 1) * n + i] + dlz * grad[(3 * k + 2) * n + i];
+        WR[k] = Wh[k * n + j] + drx * grad[(3 * k) * n + j] + dry * grad[(3 * k + 1) * n + j] + drz * grad[(3 * k + 2) * n + j];
+    }
+    apply_floor(WL, c.rho_floor, c.eps_floor);
+    apply_floor(WR, c.rho_floor, c.eps_floor);
+    // face velocity (Sec. 4): mean generator velocity plus the correction for
+    // the face centroid lying off the generators' midpoint
+    const double rix = pos[i], riy = pos[n + i], riz = pos[2 * n + i];
+    const double rjx = pos[j] + ox, rjy = pos[n + j] + oy, rjz = pos[2 * n + j] + oz;
+    const double drgx = rjx - rix, drgy = rjy - riy, drgz = rjz - riz;
+    const double wix = w[i], wiy = w[n + i], wiz = w[2 * n + i];
+    const double wjx = w[j], wjy = w[n + j], wjz = w[2 * n + j];
+    const double il2 = 1.0 / (drgx * drgx + drgy * drgy + drgz * drgz);
+    const double corr = ((wix - wjx) * (fx - 0.5 * (rix + rjx)) + (wiy - wjy) * (fy - 0.5 * (riy + rjy)) +
+                         (wiz - wjz) * (fz - 0.5 * (riz + rjz))) * il2;
+    const double wfx = corr * drgx + 0.5 * (wix + wjx);
+    const double wfy = corr * drgy + 0.5 * (wiy + wjy);
+    const double wfz = corr * drgz + 0.5 * (wiz + wjz);
+    // primitives, boosted into the face frame (pressure is frame independent)
+    const double gm1 = c.gamma - 1.0;
+    FaceState L, R;
+    {
+        const double ir = 1.0 / WL[0];
+        L.rho = WL[0];
+        L.P = gm1 * (WL[4] - 0.5 * (WL[1] * WL[1] + WL[2] * WL[2] + WL[3] * WL[3]) * ir);
+        L.vx = WL[1] * ir - wfx; L.vy = WL[2] * ir - wfy; L.vz = WL[3] * ir - wfz;
+    }
+    {
+        const double ir = 1.0 / WR[0];
+        R.rho = WR[0];
+        R.P = gm1 * (WR[4] - 0.5 * (WR[1] * WR[1] + WR[2] * WR[2] + WR[3] * WR[3]) * ir);
+        R.vx = WR[1] * ir - wfx; R.vy = WR[2] * ir - wfy; R.vz = WR[3] * ir - wfz;
+    }
+    double F[5];
+    hllc(L, R, nx, ny, nz, c.gamma, F);
+    // back to the lab frame: p -> p + m w, E -> E + p.w + |w|^2/2 m
+    const double A = m.area[f];
+    const double fm = F[0];
+    const double fe = F[4] + F[1] * wfx + F[2] * wfy + F[3] * wfz + 0.5 * (wfx * wfx + wfy * wfy + wfz * wfz) * fm;
+    const int64_t nf = m.nf;
+    flux[f] = A * fm;
+    flux[nf + f] = A * (F[1] + fm * wfx);
+    flux[2 * nf + f] = A * (F[2] + fm * wfy);
+    flux[3 * nf + f] = A * (F[3] + fm * wfz);
+    flux[4 * nf + f] = A * fe;
+}
+
+void launch_face_flux(const MeshDev &m, const HydroCfg &c, const double *pos, const double *w, const double *Wh,
+                      const double *grad, double *flux, cudaStream_t s)
+{
+    if (m.nf == 0) return;
+    int nb = (int)((m.nf + 127) / 128);
+    k_face_flux<<<nb, 128, 0, s>>>(m, c, pos, w, Wh, grad, flux);
+}
+
+// ---------------------------------------------------------------------------
+// Conservative update: U_i -= dt sum_{f in i} (+/-) Phi_f, then floors
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_update(MeshDev m, HydroCfg c, const double *__restrict__ flux,
+                                                const double *__restrict__ dtp, double *__restrict__ U)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t n = m.n, nf = m.nf;
+    if (i >= n) return;
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int e = m.inc_off[i]; e < m.inc_off[i + 1]; ++e) {
+        int f = m.inc_face[e];
+        if (f >= 0) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) acc[k] += flux[k * nf + f];
+        } else {
+            f = ~f;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) acc[k] -= flux[k * nf + f];
+        }
+    }
+    const double dt = *dtp;
+    double Un[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) Un[k] = U[k * n + i] - dt * acc[k];
+    const double V = m.vol[i], iv = 1.0 / V;
+    double W[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) W[k] = Un[k] * iv;
+    if (apply_floor(W, c.rho_floor, c.eps_floor)) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) Un[k] = W[k] * V;
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) U[k * n + i] = Un[k];
+}
+
+void launch_update(const MeshDev &m, const HydroCfg &c, const double *flux, const double *dt, double *U,
+                   cudaStream_t s)
+{
+    int nb = (int)((m.n + 255) / 256);
+    k_update<<<nb, 256, 0, s>>>(m, c, flux, dt, U);
+}
+
+// ---------------------------------------------------------------------------
+// Mesh velocity (Sec. 4.2) fused with the per-cell CFL timestep and its
+// global minimum.  Positive doubles order like their bit patterns, so the
+// minimum is an unsigned 64-bit atomicMin: exact and order independent.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double sound_speed(const double W[5], double gamma)
+{
+    const double ke = 0.5 * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]) / W[0];
+    double P = (gamma - 1.0) * (W[4] - ke);
+    if (P < 0.0) P = 0.0;
+    return sqrt(gamma * P / W[0]);
+}
+
+__global__ void __launch_bounds__(256) k_mesh_velocity(MeshDev m, HydroCfg c, const double *__restrict__ pos,
+                                                       const double *__restrict__ U, double *__restrict__ w,
+                                                       unsigned long long *__restrict__ dt_bits)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t n = m.n;
+    double dti = __longlong_as_double(0x7ff0000000000000LL);
+    if (i < n) {
+        const double V = m.vol[i];
+        double W[5];
+        load5(U, n, i, 1.0 / V, W);
+        const double vx = U[n + i] / U[i], vy = U[2 * n + i] / U[i], vz = U[3 * n + i] / U[i];
+        double wx = c.eta * vx, wy = c.eta * vy, wz = c.eta * vz;
+        const double cs = sound_speed(W, c.gamma);
+        const double R = cbrt(3.0 * V / (4.0 * 3.14159265358979323846));
+        if (c.regularize) {
+            const double dx = m.cen[i] - pos[i], dy = m.cen[n + i] - pos[n + i], dz = m.cen[2 * n + i] - pos[2 * n + i];
+            const double d = sqrt(dx * dx + dy * dy + dz * dz);
+            const double zr = c.zeta * R;
+            double ramp = 0.0;
+            if (d > 1.1 * zr) ramp = 1.0;
+            else if (d >= 0.9 * zr) ramp = (d - 0.9 * zr) / (0.2 * zr);
+            if (ramp > 0.0 && d > 0.0) {
+                const double s = c.chi * cs * ramp / d;
+                wx += s * dx; wy += s * dy; wz += s * dz;
+            }
+        }
+        if (w) { w[i] = wx; w[n + i] = wy; w[2 * n + i] = wz; }
+        const double rx = vx - wx, ry = vy - wy, rz = vz - wz;
+        dti = c.cfl * R / (cs + sqrt(rx * rx + ry * ry + rz * rz));
+    }
+    // block minimum, then one atomic per block
+    __shared__ double sm[8];
+    for (int o = 16; o > 0; o >>= 1) dti = fmin(dti, __shfl_xor_sync(FULL_MASK_HYDRO, dti, o));
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = dti;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = sm[0];
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) v = fmin(v, sm[k]);
+        if (dt_bits && v > 0.0) atomicMin(dt_bits, (unsigned long long)__double_as_longlong(v));
+    }
+}
+
+// CFL timestep for a given generator velocity w (Sec. 4.2).
+__global__ void __launch_bounds__(256) k_timestep(MeshDev m, HydroCfg c, const double *__restrict__ U,
+                                                  const double *__restrict__ w, unsigned long long *__restrict__ dt_bits)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t n = m.n;
+    double dti = __longlong_as_double(0x7ff0000000000000LL);
+    if (i < n) {
+        const double V = m.vol[i];
+        double W[5];
+        load5(U, n, i, 1.0 / V, W);
+        const double rx = U[n + i] / U[i] - w[i], ry = U[2 * n + i] / U[i] - w[n + i], rz = U[3 * n + i] / U[i] - w[2 * n + i];
+        const double R = cbrt(3.0 * V / (4.0 * 3.14159265358979323846));
+        dti = c.cfl * R / (sound_speed(W, c.gamma) + sqrt(rx * rx + ry * ry + rz * rz));
+    }
+    __shared__ double sm[8];
+    for (int o = 16; o > 0; o >>= 1) dti = fmin(dti, __shfl_xor_sync(FULL_MASK_HYDRO, dti, o));
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = dti;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = sm[0];
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) v = fmin(v, sm[k]);
+        if (v > 0.0) atomicMin(dt_bits, (unsigned long long)__double_as_longlong(v));
+    }
+}
+
+void launch_timestep(const MeshDev &m, const HydroCfg &c, const double *U, const double *w, double *dt_min,
+                     cudaStream_t s)
+{
+    int nb = (int)((m.n + 255) / 256);
+    k_timestep<<<nb, 256, 0, s>>>(m, c, U, w, reinterpret_cast<unsigned long long *>(dt_min));
+}
+
+__global__ void k_dt_init(double *dt) { *dt = __longlong_as_double(0x7ff0000000000000LL); }
+
+void launch_dt_init(double *dt, cudaStream_t s) { k_dt_init<<<1, 1, 0, s>>>(dt); }
+
+void launch_mesh_velocity(const MeshDev &m, const HydroCfg &c, const double *pos, const double *U, double *w,
+                          double *dt_min, cudaStream_t s)
+{
+    int nb = (int)((m.n + 255) / 256);
+    k_mesh_velocity<<<nb, 256, 0, s>>>(m, c, pos, U, w, reinterpret_cast<unsigned long long *>(dt_min));
+}
+
+// ---------------------------------------------------------------------------
+// Drift: r += w dt wrapped into [0, L)
+// ---------------------------------------------------------------------------
+__global__ void k_drift(double *__restrict__ pos, int64_t n, const double *__restrict__ w,
+                        const double *__restrict__ dtp, Box3 b)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double dt = *dtp;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double L = b.L[d];
+        double x = fmod(pos[d * n + i] + w[d * n + i] * dt, L);
+        if (x < 0.0) x += L;
+        if (x >= L) x -= L;
+        pos[d * n + i] = x;
+    }
+}
+
+void launch_drift(double *pos, int64_t n, const double *w, const double *dt, const double *box3, cudaStream_t s)
+{
+    Box3 b{{box3[0], box3[1], box3[2]}};
+    int nb = (int)((n + 255) / 256);
+    k_drift<<<nb, 256, 0, s>>>(pos, n, w, dt, b);
+}
+
+// ---------------------------------------------------------------------------
+// Charges from primitives, and compensated totals
+// ---------------------------------------------------------------------------
+__global__ void k_prims_to_charges(MeshDev m, HydroCfg c, const double *__restrict__ rho, const double *__restrict__ vel,
+                                   const double *__restrict__ P, double *__restrict__ U)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t n = m.n;
+    if (i >= n) return;
+    const double V = m.vol[i], r = rho[i];
+    const double vx = vel[i], vy = vel[n + i], vz = vel[2 * n + i];
+    U[i] = r * V;
+    U[n + i] = r * vx * V;
+    U[2 * n + i] = r * vy * V;
+    U[3 * n + i] = r * vz * V;
+    U[4 * n + i] = (P[i] / (c.gamma - 1.0) + 0.5 * r * (vx * vx + vy * vy + vz * vz)) * V;
+}
+
+void launch_prims_to_charges(const MeshDev &m, const HydroCfg &c, const double *rho, const double *vel,
+                             const double *P, double *U, cudaStream_t s)
+{
+    int nb = (int)((m.n + 255) / 256);
+    k_prims_to_charges<<<nb, 256, 0, s>>>(m, c, rho, vel, P, U);
+}
+
+// Neumaier sum pair (s, comp): value = s + comp.
+__device__ __forceinline__ void neumaier_add(double &s, double &comp, double x)
+{
+    const double t = s + x;
+    if (fabs(s) >= fabs(x)) comp += (s - t) + x;
+    else comp += (x - t) + s;
+    s = t;
+}
+
+// Each block reduces a contiguous range per component with a Neumaier sum
+// per thread and a fixed-order tree over threads; a second pass sums the
+// block partials in order.  Deterministic for a given launch shape.
+__global__ void k_totals_partial(const double *__restrict__ U, int64_t n, double *__restrict__ partial)
+{
+    __shared__ double ss[256], sc[256];
+    const int nblk = gridDim.x;
+    const int64_t per = (n + nblk - 1) / nblk;
+    const int64_t lo = blockIdx.x * per, hi = min(n, lo + per);
+    for (int k = 0; k < 5; ++k) {
+        double s = 0.0, cmp = 0.0;
+        for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) neumaier_add(s, cmp, U[k * n + i]);
+        ss[threadIdx.x] = s;
+        sc[threadIdx.x] = cmp;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) {
+                double a = ss[threadIdx.x], ca = sc[threadIdx.x];
+                neumaier_add(a, ca, ss[threadIdx.x + o]);
+                ca += sc[threadIdx.x + o];
+                ss[threadIdx.x] = a;
+                sc[threadIdx.x] = ca;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            partial[2 * (k * nblk + blockIdx.x)] = ss[0];
+            partial[2 * (k * nblk + blockIdx.x) + 1] = sc[0];
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_totals_final(const double *__restrict__ partial, int nblk, double *__restrict__ totals)
+{
+    const int k = threadIdx.x;
+    if (k >= 5) return;
+    double s = 0.0, cmp = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+        neumaier_add(s, cmp, partial[2 * (k * nblk + b)]);
+        cmp += partial[2 * (k * nblk + b) + 1];
+    }
+    totals[k] = s + cmp;
+}
+
+void launch_totals(const double *U, int64_t n, double *partial, int nblocks, double *totals, cudaStream_t s)
+{
+    k_totals_partial<<<nblocks, 256, 0, s>>>(U, n, partial);
+    k_totals_final<<<1, 32, 0, s>>>(partial, nblocks, totals);
+}
+
+}  // namespace mm

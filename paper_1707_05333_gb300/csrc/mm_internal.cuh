@@ -1,0 +1,107 @@
+// mm_internal.cuh -- shared declarations of the CUDA moving-mesh library.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/mm.h"
+
+namespace mm {
+
+// Per-cell fixed capacities of the clipping kernel (Sec. 3).  A cell that
+// exceeds one reports MM_ECAPACITY for the tessellation.
+constexpr int CMAX = 128;   // candidates gathered per search ring
+constexpr int PMAX = 64;    // planes that ever cut the cell (6 box planes included)
+constexpr int TMAX = 128;   // vertices (triangles of the dual) alive at once
+constexpr int NSTAGE = 32;  // vertices created by one cut
+constexpr int MAXF = 48;    // faces written per cell
+constexpr int MAXRING = 48; // search rings before giving up
+constexpr int CLIP_WARPS = 4;
+
+// Device status word, read by the host after a tessellation.
+enum : int {
+    ST_EINVAL = 1,
+    ST_ECAP_CAND = 2,
+    ST_ECAP_PLANE = 4,
+    ST_ECAP_TRI = 8,
+    ST_ECAP_STAGE = 16,
+    ST_ECAP_FACE = 32,
+    ST_ECAP_RING = 64,
+    ST_EDEGEN = 128,
+};
+
+struct DevStatus {
+    int flags;
+    int bad_cell;
+    int max_cand, max_planes, max_tris;
+    int multi_ring;
+    unsigned long long cuts;
+};
+
+struct Grid {
+    int g[3];
+    double bs[3];  // bin edge per axis
+    double box[3];
+};
+
+struct Slots {         // per-cell face slots written by the clipper
+    int *cnt;          // [n]
+    int *nb;           // [n*MAXF]
+    unsigned char *sh; // [n*MAXF] shift code
+    double *area;      // [n*MAXF]
+    double *fc;        // [3][n*MAXF] face centroid, absolute, cell frame
+};
+
+// kernels' host launchers (stream-ordered, no syncs)
+void launch_bin_count(const double *pos, int64_t n, const Grid &g, int *bin_of, int *count,
+                      DevStatus *st, cudaStream_t s);
+void launch_bin_scatter(const double *pos, int64_t n, const int *bin_of, const int *start, int *cursor,
+                        double4_32a *sorted, cudaStream_t s);
+void launch_bin_sort(const int *start, int64_t nbins, double4_32a *sorted, cudaStream_t s);
+// exclusive scan of in[0..n) into out[0..n], out[n] = total; tmp >= scan_tmp_size(n) ints
+size_t scan_tmp_size(int64_t n);
+void launch_scan(const int *in, int *out, int64_t n, int *tmp, cudaStream_t s);
+
+void launch_clip(const double4_32a *sorted, const int *start, int64_t n, const Grid &g, double amin,
+                 int precision, double *vol, double *cen, Slots sl, DevStatus *st, cudaStream_t s);
+
+void launch_face_confirm(int64_t n, Slots sl, unsigned long long *emit_mask, unsigned long long *conf_mask,
+                         signed char *partner, int *emit_cnt, int *conf_cnt, cudaStream_t s);
+void launch_face_write(int64_t n, const double *pos, const Grid &g, Slots sl,
+                       const unsigned long long *emit_mask, const unsigned long long *conf_mask,
+                       const signed char *partner, const int *face_off, const int *inc_off,
+                       int *face_i, int *face_j, int *face_shift, double *face_area, double *face_normal,
+                       double *face_cen, int64_t fcap, int *inc_face, cudaStream_t s);
+
+struct MeshDev {
+    int64_t n, nf, fs;  // cells, faces, row stride of the [3][.] face arrays
+    double box[3];
+    const int *face_i, *face_j, *face_shift;
+    const double *area, *normal, *fcen;
+    const double *vol, *cen;
+    const int *inc_off, *inc_face;
+};
+
+struct HydroCfg {
+    double gamma, cfl, eta, chi, zeta, theta, rho_floor, eps_floor;
+    int limiter, regularize;
+};
+
+void launch_gradient(const MeshDev &m, const HydroCfg &c, const double *U_or_W, bool from_charges,
+                     double *grad, double *W_half, const double *dt, cudaStream_t s);
+void launch_face_flux(const MeshDev &m, const HydroCfg &c, const double *pos, const double *w,
+                      const double *Wh, const double *grad, double *flux, cudaStream_t s);
+void launch_update(const MeshDev &m, const HydroCfg &c, const double *flux, const double *dt, double *U,
+                   cudaStream_t s);
+void launch_mesh_velocity(const MeshDev &m, const HydroCfg &c, const double *pos, const double *U,
+                          double *w, double *dt_min, cudaStream_t s);
+void launch_dt_init(double *dt, cudaStream_t s);
+void launch_timestep(const MeshDev &m, const HydroCfg &c, const double *U, const double *w, double *dt_min,
+                     cudaStream_t s);
+void launch_drift(double *pos, int64_t n, const double *w, const double *dt, const double *box3,
+                  cudaStream_t s);
+void launch_prims_to_charges(const MeshDev &m, const HydroCfg &c, const double *rho, const double *vel,
+                             const double *P, double *U, cudaStream_t s);
+void launch_totals(const double *U, int64_t n, double *partial, int nblocks, double *totals, cudaStream_t s);
+
+}  // namespace mm

@@ -1,0 +1,183 @@
+"""GPU hydro stages and the whole step (mm_gradients, mm_mesh_velocity,
+mm_timestep, mm_flux_step, mm_drift, mm_step) against the oracle."""
+import numpy as np
+import pytest
+
+from paper_1707_05333_gb300 import workloads as WL
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+RTOL_STEP = 1e-10  # one-step conserved states, FP64 path
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    c, torch = H.gpu_context()
+    yield c, torch
+    c.close()
+
+
+def setup(oracle, w, rho=None, vel=None, pres=None):
+    T = oracle.tessellate(w.pos, w.box, 1)
+    U = oracle.charges_from_prims(T["volume"], w.rho if rho is None else rho, w.vel if vel is None else vel,
+                                  w.pres if pres is None else pres, w.gamma, w.e_add)
+    return T, U
+
+
+def cfg_pair(oracle, gamma, **kw):
+    from paper_1707_05333_gb300 import binding
+    o = oracle.make_cfg(gamma=gamma, **kw)
+    g = binding.default_config(gamma=gamma, **kw)
+    return o, g
+
+
+def assert_state_close(G, O, rtol=RTOL_STEP):
+    # per component, relative to the component's scale (momenta can vanish)
+    for k in range(5):
+        scale = np.abs(O[:, k]).max()
+        np.testing.assert_allclose(G[k], O[:, k], rtol=rtol, atol=rtol * scale, err_msg=f"component {k}")
+
+
+@pytest.mark.parametrize("limiter", [0, 1, 2])
+def test_gradients_match_oracle(oracle, gpu, limiter):
+    c, torch = gpu
+    w = WL.smooth_wave(12)
+    rho, vel, pres = WL.random_state(w.n, seed=limiter)
+    T, U = setup(oracle, w, rho, vel, pres)
+    ocfg, gcfg = cfg_pair(oracle, w.gamma, limiter=limiter)
+    c.set_config(**{f: getattr(gcfg, f) for f, _ in gcfg._fields_})
+    mesh, P, G = H.gpu_tessellate(c, torch, w.pos, w.box)
+    W = U / T["volume"][:, None]
+    og = oracle.gradient(oracle.unique_faces(T), T["volume"], T["centroid"], w.box, W, ocfg)
+    gg = c.mm_gradients(mesh, H.to_dev(torch, W.T)).cpu().numpy()
+    og = og.reshape(w.n, 15).T
+    for r in range(15):
+        np.testing.assert_allclose(gg[r], og[r], rtol=1e-9, atol=1e-9 * np.abs(og[r]).max() + 1e-14)
+
+
+CONFIGS = {
+    "smooth_wave_16^3_S10": dict(maker=lambda: WL.smooth_wave(16), kw=dict(limiter=1)),
+    "smooth_wave_random_state_DM_regularized": dict(maker=lambda: WL.smooth_wave(10), kw=dict(limiter=2, regularize=1),
+                                                    random=True),
+    "shock_tube_64x6x6": dict(maker=lambda: WL.shock_tube(64, 6, 6), kw=dict(limiter=1)),
+    "point_blast_12^3": dict(maker=lambda: WL.point_blast(12), kw=dict(limiter=1)),
+    "static_mesh_eta0": dict(maker=lambda: WL.smooth_wave(9), kw=dict(limiter=1, eta=0.0), random=True),
+    "no_limiter_ragged_11^3": dict(maker=lambda: WL.smooth_wave(11), kw=dict(limiter=0), random=True),
+}
+
+
+@pytest.mark.parametrize("case", list(CONFIGS))
+def test_one_step_matches_oracle(oracle, gpu, case):
+    c, torch = gpu
+    spec = CONFIGS[case]
+    w = spec["maker"]()
+    if spec.get("random"):
+        rho, vel, pres = WL.random_state(w.n, seed=3)
+        T, U = setup(oracle, w, rho, vel, pres)
+    else:
+        T, U = setup(oracle, w)
+    ocfg, gcfg = cfg_pair(oracle, w.gamma, cfl=w.cfl, **spec["kw"])
+    c.set_config(**{f: getattr(gcfg, f) for f, _ in gcfg._fields_})
+    S = oracle.step(w.pos, U, w.box, ocfg, tess=T)
+    # same dt on both sides: the oracle's CFL value
+    pos = H.to_dev(torch, w.pos.T)
+    Ud = H.to_dev(torch, U.T)
+    dt_fixed = torch.tensor([S["dt"]], dtype=torch.float64, device="cuda")
+    w_out = torch.empty((3, w.n), dtype=torch.float64, device="cuda")
+    dt_out = torch.empty((1,), dtype=torch.float64, device="cuda")
+    c.mm_step(pos, Ud, w.box, dt_fixed=dt_fixed, dt_out=dt_out, w_out=w_out)
+    np.testing.assert_allclose(w_out.cpu().numpy().T, S["w"], rtol=1e-12, atol=1e-14)
+    assert_state_close(Ud.cpu().numpy(), S["U"])
+    dp = pos.cpu().numpy().T - S["pos"]
+    dp -= np.round(dp / w.box) * w.box
+    assert np.abs(dp).max() <= 1e-12
+    # the CFL timestep itself, computed on the device
+    c.mm_step(H.to_dev(torch, w.pos.T), H.to_dev(torch, U.T), w.box, dt_out=dt_out)
+    assert float(dt_out.item()) == pytest.approx(S["dt_cfl"], rel=1e-13)
+
+
+def test_stagewise_calls_equal_mm_step(oracle, gpu):
+    c, torch = gpu
+    w = WL.smooth_wave(10)
+    rho, vel, pres = WL.random_state(w.n, seed=5)
+    T, U = setup(oracle, w, rho, vel, pres)
+    c.set_config(limiter=1, regularize=1, gamma=w.gamma, eta=1.0)
+    pos = H.to_dev(torch, w.pos.T)
+    Ud = H.to_dev(torch, U.T)
+    mesh = c.mm_tessellate(pos, w.box)
+    wv = c.mm_mesh_velocity(mesh, pos, Ud)
+    dt = c.mm_timestep(mesh, Ud, wv)
+    c.mm_flux_step(mesh, pos, wv, dt, Ud)
+    c.mm_drift(pos, wv, dt, w.box)
+    pos2 = H.to_dev(torch, w.pos.T)
+    U2 = H.to_dev(torch, U.T)
+    c.mm_step(pos2, U2, w.box)
+    assert torch.equal(Ud, U2) and torch.equal(pos, pos2)
+
+
+def test_conservation_and_determinism_on_device(oracle, gpu):
+    c, torch = gpu
+    w = WL.smooth_wave(20)
+    rho, vel, pres = WL.random_state(w.n, seed=6)
+    T, U = setup(oracle, w, rho, vel, pres)
+    c.set_config(limiter=2, regularize=1, gamma=w.gamma)
+    outs = []
+    for _ in range(2):
+        pos = H.to_dev(torch, w.pos.T)
+        Ud = H.to_dev(torch, U.T)
+        t0 = c.mm_totals(Ud).cpu().numpy()
+        for _ in range(3):
+            c.mm_step(pos, Ud, w.box)
+        t1 = c.mm_totals(Ud).cpu().numpy()
+        scale = np.abs(U).sum(0)
+        scale[1:4] = scale[1:4].max()
+        assert np.all(np.abs(t1 - t0) <= 1e-13 * scale)
+        outs.append((pos.clone(), Ud.clone()))
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+
+
+def test_uniform_flow_is_preserved(oracle, gpu):
+    c, torch = gpu
+    w = WL.smooth_wave(12)
+    n = w.n
+    T = oracle.tessellate(w.pos, w.box, 1)
+    vel = np.tile([0.3, -0.2, 0.1], (n, 1))
+    U = oracle.charges_from_prims(T["volume"], np.full(n, 1.2), vel, np.full(n, 0.8), w.gamma)
+    c.set_config(limiter=1, regularize=0, gamma=w.gamma, eta=1.0)
+    pos = H.to_dev(torch, w.pos.T)
+    Ud = H.to_dev(torch, U.T)
+    dt = torch.tensor([1e-3], dtype=torch.float64, device="cuda")
+    c.mm_step(pos, Ud, w.box, dt_fixed=dt)
+    np.testing.assert_allclose(Ud.cpu().numpy().T, U, rtol=1e-12, atol=1e-16)
+
+
+def test_prims_to_charges(oracle, gpu):
+    c, torch = gpu
+    w = WL.smooth_wave(8)
+    c.set_config(gamma=w.gamma)
+    mesh, P, G = H.gpu_tessellate(c, torch, w.pos, w.box)
+    U = c.mm_prims_to_charges(mesh, H.to_dev(torch, w.rho), H.to_dev(torch, w.vel.T), H.to_dev(torch, w.pres))
+    O = oracle.charges_from_prims(G["cell_volume"], w.rho, w.vel, w.pres, w.gamma)
+    np.testing.assert_allclose(U.cpu().numpy().T, O, rtol=1e-14, atol=1e-18)
+
+
+def test_full_size_shear_layer_step_properties(gpu):
+    """The bench workload: one full step conserves mass, momentum and energy
+    and keeps every charge finite and positive."""
+    c, torch = gpu
+    w = WL.shear_layer(256)
+    c.set_config(limiter=1, regularize=0, gamma=w.gamma, cfl=w.cfl, eta=1.0)
+    pos = H.to_dev(torch, w.pos.T)
+    mesh = c.mm_tessellate(pos, w.box)
+    U = c.mm_prims_to_charges(mesh, H.to_dev(torch, w.rho), H.to_dev(torch, w.vel.T), H.to_dev(torch, w.pres))
+    t0 = c.mm_totals(U).cpu().numpy()
+    scale = U.abs().sum(1).cpu().numpy()
+    dt = torch.empty((1,), dtype=torch.float64, device="cuda")
+    c.mm_step(pos, U, w.box, dt_out=dt)
+    t1 = c.mm_totals(U).cpu().numpy()
+    # momentum components share one scale (one of them is identically zero here)
+    scale[1:4] = scale[1:4].max()
+    assert np.all(np.abs(t1 - t0) <= 1e-13 * scale)
+    assert bool(torch.isfinite(U).all()) and bool((U[0] > 0).all())
+    assert 0 < float(dt.item()) < 1e-2

@@ -1,0 +1,126 @@
+"""GPU tessellation (mm_tessellate) against the oracle, element by element."""
+import numpy as np
+import pytest
+
+from paper_1707_05333_gb300 import workloads as WL
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c, torch = H.gpu_context()
+    yield c, torch
+    c.close()
+
+
+def lattice(kind, m):
+    s = 1.0 / m
+    basis = {"sc": [(0, 0, 0)], "bcc": [(0, 0, 0), (0.5, 0.5, 0.5)],
+             "fcc": [(0, 0, 0), (0.5, 0.5, 0), (0.5, 0, 0.5), (0, 0.5, 0.5)]}[kind]
+    pts = [((i + b[0] + 0.25) * s, (j + b[1] + 0.25) * s, (k + b[2] + 0.25) * s)
+           for k in range(m) for j in range(m) for i in range(m) for b in basis]
+    return np.array(pts)
+
+
+CASES = {
+    "smooth_wave_16^3": lambda: (WL.smooth_wave(16).pos, np.ones(3)),
+    "jittered_13^3_ragged": lambda: (WL.smooth_wave(13).pos, np.ones(3)),
+    "random_1001": lambda: (WL.random_points(1001, seed=4), np.ones(3)),
+    "random_box_2x1x0.5": lambda: (WL.random_points(777, box=(2.0, 1.0, 0.5), seed=5), np.array([2.0, 1.0, 0.5])),
+    "shock_tube_64x8x8": lambda: (WL.shock_tube(64, 8, 8).pos, np.array([8.0, 1.0, 1.0])),
+    "cubic_lattice_exact_ties": lambda: (lattice("sc", 8), np.ones(3)),
+    "bcc_lattice": lambda: (lattice("bcc", 5), np.ones(3)),
+    "fcc_degenerate_vertices": lambda: (lattice("fcc", 4), np.ones(3)),
+    "n1": lambda: (np.array([[0.3, 0.6, 0.9]]), np.ones(3)),
+    "n2": lambda: (np.array([[0.1, 0.5, 0.5], [0.6, 0.55, 0.45]]), np.ones(3)),
+    "n5": lambda: (WL.random_points(5, seed=6), np.ones(3)),
+    "n37": lambda: (WL.random_points(37, seed=7), np.ones(3)),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_tessellation_matches_oracle(oracle, ctx, case):
+    c, torch = ctx
+    pos, box = CASES[case]()
+    T = oracle.tessellate(pos, box, 0 if len(pos) <= 1100 else 1)
+    mesh, P, G = H.gpu_tessellate(c, torch, pos, box)
+    ncommon = H.compare_tessellations(oracle, T, G, pos, box)
+    assert ncommon > 0
+    H.check_incidence(G)
+    assert abs(G["cell_volume"].sum() - np.prod(box)) <= 1e-11 * np.prod(box)
+
+
+def test_tessellation_is_deterministic(ctx):
+    c, torch = ctx
+    pos = WL.random_points(3000, seed=8)
+    _, _, A = H.gpu_tessellate(c, torch, pos, np.ones(3))
+    _, _, B = H.gpu_tessellate(c, torch, pos, np.ones(3))
+    for k in A:
+        np.testing.assert_array_equal(A[k], B[k])
+
+
+def test_mixed_precision_predicates_give_same_mesh(ctx):
+    c, torch = ctx
+    pos = WL.random_points(2000, seed=9)
+    _, _, A = H.gpu_tessellate(c, torch, pos, np.ones(3))
+    c.set_config(precision=1)
+    try:
+        _, _, B = H.gpu_tessellate(c, torch, pos, np.ones(3))
+    finally:
+        c.set_config(precision=0)
+    for k in ("face_i", "face_j", "face_shift", "inc_off", "inc_face"):
+        np.testing.assert_array_equal(A[k], B[k])
+    np.testing.assert_allclose(B["face_area"], A["face_area"], rtol=1e-12, atol=1e-18)
+    np.testing.assert_allclose(B["cell_volume"], A["cell_volume"], rtol=1e-12)
+
+
+def test_rejects_bad_positions(ctx):
+    from paper_1707_05333_gb300.binding import MMError
+    c, torch = ctx
+    pos = WL.random_points(100, seed=10)
+    pos[17, 1] = 1.0  # == box: outside [0, L)
+    with pytest.raises(MMError) as e:
+        H.gpu_tessellate(c, torch, pos, np.ones(3))
+    assert e.value.status == 1
+    pos[17, 1] = np.nan
+    with pytest.raises(MMError):
+        H.gpu_tessellate(c, torch, pos, np.ones(3))
+    # the context stays usable
+    pos[17, 1] = 0.5
+    H.gpu_tessellate(c, torch, pos, np.ones(3))
+
+
+def test_full_size_shear_layer_sampled_cells(oracle, ctx):
+    """The bench workload (256^3 generators): sampled cells against the
+    oracle computed one by one, plus the tiling invariant over all cells."""
+    c, torch = ctx
+    w = WL.shear_layer(256)
+    mesh, P, G = H.gpu_tessellate(c, torch, w.pos, w.box)
+    n = w.n
+    assert abs(G["cell_volume"].sum() - 1.0) <= 1e-10
+    H.check_incidence(G)
+    rng = np.random.default_rng(0)
+    cells = np.sort(rng.choice(n, 64, replace=False))
+    T = oracle.tessellate(w.pos, w.box, cells=cells)
+    scale = (1.0 / n) ** (2.0 / 3.0)
+    np.testing.assert_allclose(G["cell_volume"][cells], T["volume"][cells], rtol=1e-9)
+    np.testing.assert_allclose(G["cell_centroid"][:, cells].T, T["centroid"][cells], atol=1e-9 * np.sqrt(scale))
+    # per sampled cell: the directed oracle faces equal the GPU incident faces
+    off, inc = G["inc_off"], G["inc_face"]
+    for ci in cells:
+        ent = inc[off[ci]:off[ci + 1]]
+        got = {}
+        for e in ent:
+            if e >= 0:
+                got[(int(G["face_j"][e]), int(G["face_shift"][e]))] = G["face_area"][e]
+            else:
+                f = ~e
+                got[(int(G["face_i"][f]), 26 - int(G["face_shift"][f]))] = G["face_area"][f]
+        sel = T["cell"] == ci
+        want = {(int(j), int(oracle.shift_code(s))): a for j, s, a in zip(T["nb"][sel], T["shift"][sel], T["area"][sel])
+                if a > 1e-8 * scale}
+        for k, a in want.items():
+            assert k in got, (ci, k)
+            assert abs(got[k] - a) <= 1e-9 * scale
