@@ -566,13 +566,22 @@ int orc_tessellate_subset(int64_t n, const double *pos, const double *box, doubl
 /* Equation of state and floors (Sec. 4, 4.1, 6)                             */
 /* ------------------------------------------------------------------------ */
 /* Floors on density and specific internal energy, applied to a per-volume
- * state (rho, m, E).  Momentum is kept; E is rewritten only when the energy
- * floor triggers, so an untouched state is returned bit for bit. */
+ * state (rho, m, E).  Below the density floor the state carries no usable
+ * velocity (it may even be negative after reconstruction), so it is reset to
+ * the floor density at rest with the floor internal energy.  Otherwise only
+ * the internal energy is raised to rho * eps_floor if needed, keeping rho and
+ * m; an untouched state is returned bit for bit. */
 void orc_floor_state(const double *W, const orc_cfg *cfg, double *Wout, int *changed)
 {
     int ch = 0;
+    if (!(W[0] >= cfg->rho_floor)) {
+        Wout[0] = cfg->rho_floor;
+        Wout[1] = Wout[2] = Wout[3] = 0.0;
+        Wout[4] = cfg->rho_floor * cfg->eps_floor;
+        if (changed) *changed = 1;
+        return;
+    }
     double rho = W[0];
-    if (!(rho >= cfg->rho_floor)) { rho = cfg->rho_floor; ch = 1; }
     double m2 = W[1] * W[1] + W[2] * W[2] + W[3] * W[3];
     double ke = 0.5 * m2 / rho;
     double E = W[4];

@@ -50,17 +50,24 @@ __device__ __forceinline__ void load5(const double *S, int64_t n, int64_t i, dou
     for (int k = 0; k < 5; ++k) w[k] = S[k * n + i] * inv_v;
 }
 
-// Floors on density and specific internal energy (Sec. 4.1); momentum kept,
-// energy rewritten only when its floor triggers.  Returns true if changed.
+// Floors on density and specific internal energy (Sec. 4.1).  A state below
+// the density floor is reset to the floor density at rest with the floor
+// internal energy; otherwise only the internal energy is raised if needed.
+// Returns true if the state changed (an untouched state is left bit for bit).
 __device__ __forceinline__ bool apply_floor(double W[5], double rho_floor, double eps_floor)
 {
-    bool ch = false;
-    double rho = W[0];
-    if (!(rho >= rho_floor)) { rho = rho_floor; ch = true; }
-    const double ke = 0.5 * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]) / rho;
-    if (!(W[4] - ke >= rho * eps_floor)) { W[4] = rho * eps_floor + ke; ch = true; }
-    W[0] = rho;
-    return ch;
+    if (!(W[0] >= rho_floor)) {
+        W[0] = rho_floor;
+        W[1] = W[2] = W[3] = 0.0;
+        W[4] = rho_floor * eps_floor;
+        return true;
+    }
+    const double ke = 0.5 * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]) / W[0];
+    if (!(W[4] - ke >= W[0] * eps_floor)) {
+        W[4] = W[0] * eps_floor + ke;
+        return true;
+    }
+    return false;
 }
 
 // ---------------------------------------------------------------------------

@@ -181,12 +181,20 @@ def test_floor_leaves_physical_state_untouched(oracle):
     assert not ch and np.array_equal(out, W)
 
 
-def test_floors_raise_density_and_energy(oracle):
+def test_density_floor_resets_to_rest(oracle):
     cfg = oracle.make_cfg(rho_floor=1e-3, eps_floor=1e-2)
-    W = np.array([1e-5, 1e-5, 0.0, 0.0, 1e-9])
+    for rho in (1e-5, -0.05):
+        out, ch = oracle.floor_state(np.array([rho, 0.3, -0.1, 0.2, 1.0]), cfg)
+        assert ch
+        np.testing.assert_array_equal(out, [1e-3, 0.0, 0.0, 0.0, 1e-5])
+
+
+def test_temperature_floor_raises_internal_energy_only(oracle):
+    cfg = oracle.make_cfg(rho_floor=1e-3, eps_floor=1e-2)
+    W = np.array([0.5, 0.1, 0.0, 0.0, 0.0101])  # internal energy density 1e-4 < 0.5 * 1e-2
     out, ch = oracle.floor_state(W, cfg)
-    assert ch and out[0] == 1e-3 and out[1] == 1e-5
-    ke = 0.5 * 1e-10 / 1e-3
+    assert ch and np.array_equal(out[:4], W[:4])
+    ke = 0.5 * 0.01 / 0.5
     assert (out[4] - ke) / out[0] == pytest.approx(1e-2, rel=1e-12)
 
 
