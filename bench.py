@@ -104,6 +104,18 @@ def clocks_stop(proc, path):
 
 
 # --------------------------------------------------------------------------- peaks
+# GB300 FP64 ALU peak from unit counts and the maximum SM clock: 152 SMs x 2
+# FP64 FMA lanes per SM per clock x 2 flops x 2.07 GHz (an FMA-chain probe on
+# this pool measured 1.19 TFLOP/s at 1.995 GHz, consistent with 2 lanes/SM).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+# Algorithmic FP64 flops per unit of clipping work: a plane test q.v > o
+# (2 FMA + 1 MUL -> 5 flops), a three-plane solve (3 cross products, the
+# determinant, the reciprocal and the scaled numerators -> 51 flops), and a
+# face-fan term of the area/centroid sums (33 flops).
+FLOPS_PLANE_TEST, FLOPS_SOLVE, FLOPS_FAN = 5, 51, 33
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -209,6 +221,11 @@ def run_ours(args, world, rank, local):
         pos, U = pos0.clone(), U0.clone()
         for _ in range(args.warmup):
             ctx.mm_step(pos, U, w.box)
+        # one counted tessellation of the current state (outside the timed region)
+        ctx.set_config(collect_stats=1)
+        ctx.mm_tessellate(pos, w.box)
+        tstats = ctx.mm_tess_stats()
+        ctx.set_config(collect_stats=0)
         stream.synchronize()
 
         def barrier():
@@ -277,13 +294,22 @@ def run_ours(args, world, rank, local):
     dom = max(stages, key=lambda k: stages[k][0])
     dom_ms = stages[dom][0] / max(1, stages[dom][1])
     peak, peak_kind = measured_peaks()
-    byts = algorithmic_bytes(dom, n, nf)
     roofline = None
-    if byts is not None:
-        ach = byts / (dom_ms / 1e3) / 1e9
-        roofline = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                    "frac": ach / peak, "traffic": None, "peak_source": peak_kind,
-                    "algorithmic_bytes_per_launch": byts, "launch_ms": dom_ms}
+    if dom == "clip":
+        flops = (FLOPS_PLANE_TEST * tstats["fp64_plane_tests"] + FLOPS_SOLVE * tstats["fp64_vertex_solves"] +
+                 FLOPS_FAN * tstats["fp64_fan_terms"])
+        ach = flops / (dom_ms / 1e3) / 1e12
+        roofline = {"kernel": "k_clip", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz (FP64 ALU)",
+                    "algorithmic_flops_per_launch": flops, "flops_per_cell": flops / n, "launch_ms": dom_ms}
+    else:
+        byts = algorithmic_bytes(dom, n, nf)
+        if byts is not None:
+            ach = byts / (dom_ms / 1e3) / 1e9
+            roofline = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                        "frac": ach / peak, "traffic": None, "peak_source": peak_kind,
+                        "algorithmic_bytes_per_launch": byts, "launch_ms": dom_ms}
     stage_ms = {k: v[0] / max(1, v[1]) for k, v in stages.items()}
 
     cpu = None
@@ -300,7 +326,8 @@ def run_ours(args, world, rank, local):
                 "config": {"workload": f"shear_layer_{args.n_side}^3", "cells": n, "faces": nf,
                            "precision": args.precision, "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (state + mesh >> 129 MB), no flush"},
-                "roofline": roofline, "stage_ms": stage_ms, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "stage_ms": stage_ms, "tess_stats_per_cell": {k: v / n for k, v in tstats.items()
+                                                                                   if not k.startswith("max")}, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -59,13 +59,14 @@ typedef struct {
     double area_rel;  /* faces with area <= area_rel (V_box/n)^(2/3) are dropped            */
     int limiter;      /* 0 none, 1 S10, 2 S10 times Duffell-MacFadyen (Sec. 4.1)            */
     int regularize;   /* 1: add the roundness correction to w (Sec. 4.2)                    */
-    int precision;    /* 0: plain FP64 throughout; 1: mixed (see mm_set_precision)          */
-    int reserved;
+    int precision;    /* 0: plain FP64 throughout; 1: mixed (FP32 clipping filter with      */
+                      /*    exact FP64 fallback, FP32 gradients and fluxes, FP64 update)      */
+    int collect_stats;/* 1: the clipper records the counters read by mm_tess_stats          */
 } mm_config;
 
 /* Fill a config with the defaults: gamma 5/3, cfl 0.3, eta 1, chi 1, zeta
  * 0.25, theta 0.49, floors 1e-10, area_rel 1e-10, S10 limiter, no
- * roundness correction, FP64. */
+ * roundness correction, FP64, no counters. */
 void mm_default_config(mm_config *cfg);
 
 typedef struct mm_ctx mm_ctx;
@@ -161,10 +162,14 @@ mm_status mm_totals(mm_ctx *ctx, const double *U, int64_t n, double *totals);
  * bindings that read the context-owned mesh arrays into their own buffers). */
 mm_status mm_copy(mm_ctx *ctx, void *dst, const void *src, int64_t bytes);
 
-/* Device-side counters of the last tessellation, copied to the host:
- * [0] max candidates gathered by a cell, [1] max planes, [2] max vertices,
- * [3] cells needing more than one search ring, [4] total cuts. */
-mm_status mm_tess_stats(mm_ctx *ctx, int64_t stats[5]);
+/* Device-side counters of the last tessellation made with
+ * mm_config.collect_stats = 1, copied to the host:
+ * [0] max candidates in one sorted batch, [1] max planes of a cell,
+ * [2] max vertices of a cell, [3] cells needing more than one search ring,
+ * [4] total cuts, [5] FP64 plane tests, [6] FP64 three-plane solves,
+ * [7] FP64 face-fan terms, [8] candidates tested. */
+#define MM_NSTATS 9
+mm_status mm_tess_stats(mm_ctx *ctx, int64_t stats[MM_NSTATS]);
 
 /* Stages of a step, for per-stage device timing. */
 typedef enum {

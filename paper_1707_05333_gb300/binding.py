@@ -41,7 +41,7 @@ class Config(ctypes.Structure):
                 ("chi", ctypes.c_double), ("zeta", ctypes.c_double), ("theta", ctypes.c_double),
                 ("rho_floor", ctypes.c_double), ("eps_floor", ctypes.c_double),
                 ("area_rel", ctypes.c_double), ("limiter", ctypes.c_int), ("regularize", ctypes.c_int),
-                ("precision", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("collect_stats", ctypes.c_int)]
 
 
 class MeshStruct(ctypes.Structure):
@@ -56,6 +56,9 @@ EXPORTS = ["mm_default_config", "mm_create", "mm_destroy", "mm_last_error", "mm_
            "mm_tessellate", "mm_gradients", "mm_mesh_velocity", "mm_timestep", "mm_flux_step",
            "mm_drift", "mm_step", "mm_prims_to_charges", "mm_totals", "mm_copy", "mm_tess_stats",
            "mm_set_timing", "mm_stage_times", "mm_kernel_launches"]
+
+STATS = ["max_candidates", "max_planes", "max_vertices", "multi_ring_cells", "cuts", "fp64_plane_tests",
+         "fp64_vertex_solves", "fp64_fan_terms", "candidates_tested"]
 
 STAGES = ["bin", "clip", "faces", "mesh_velocity", "gradient_half_step", "gradient", "face_flux", "update",
           "drift"]
@@ -277,7 +280,8 @@ class Context:
     def mm_kernel_launches(self) -> int:
         return int(self.L.mm_kernel_launches(self.h))
 
-    def mm_tess_stats(self) -> list:
-        arr = (_c_i64 * 5)()
+    def mm_tess_stats(self) -> dict:
+        """Counters of the last tessellation made with collect_stats=1."""
+        arr = (_c_i64 * len(STATS))()
         self._call("mm_tess_stats", self.h, arr)
-        return list(arr)
+        return dict(zip(STATS, list(arr)))

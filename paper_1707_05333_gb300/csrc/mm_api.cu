@@ -323,7 +323,8 @@ mm_status mm_tessellate(mm_ctx *c, const double *pos, int64_t n, const double bo
     Slots sl{P<int>(c->s_cnt), P<int>(c->s_nb), P<unsigned char>(c->s_sh), P<double>(c->s_area), P<double>(c->s_fc)};
     const double amin = c->cfg.area_rel * std::pow(box[0] * box[1] * box[2] / (double)n, 2.0 / 3.0);
     stage_mark(c, MM_STAGE_CLIP, true);
-    launch_clip(P<double4_32a>(c->sorted), P<int>(c->bin_start), n, g, amin, c->cfg.precision, P<double>(c->vol),
+    launch_clip(P<double4_32a>(c->sorted), P<int>(c->bin_start), n, g, amin, c->cfg.precision, c->cfg.collect_stats,
+                P<double>(c->vol),
                 P<double>(c->cen), sl, c->st, s);
     CKLAUNCH();
     stage_mark(c, MM_STAGE_CLIP, false);
@@ -568,7 +569,7 @@ mm_status mm_stage_times(mm_ctx *c, double ms[MM_NSTAGES], int64_t runs[MM_NSTAG
 
 int64_t mm_kernel_launches(const mm_ctx *c) { return c ? c->launches : 0; }
 
-mm_status mm_tess_stats(mm_ctx *c, int64_t stats[5])
+mm_status mm_tess_stats(mm_ctx *c, int64_t stats[MM_NSTATS])
 {
     if (!c || !stats) return MM_EINVAL;
     CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream));
@@ -578,6 +579,10 @@ mm_status mm_tess_stats(mm_ctx *c, int64_t stats[5])
     stats[2] = c->st_host->max_tris;
     stats[3] = c->st_host->multi_ring;
     stats[4] = (int64_t)c->st_host->cuts;
+    stats[5] = (int64_t)c->st_host->pred64;
+    stats[6] = (int64_t)c->st_host->solve64;
+    stats[7] = (int64_t)c->st_host->fan64;
+    stats[8] = (int64_t)c->st_host->tested;
     return MM_OK;
 }
 

@@ -8,38 +8,57 @@
 //    bisectors with p's own periodic images, so the true cell lies inside.
 //  * The cell is kept as its dual: every vertex is a triangle (a,b,c) of
 //    plane indices, oriented so det(q_a, q_b, q_c) > 0; its position is the
-//    intersection of those three planes, solved in FP64.  A cut removes the
-//    triangles beyond the plane; the directed edges of removed triangles
-//    whose reverse edge is not also removed form the rim of the hole, and
-//    each rim edge x->y becomes a new triangle (x, y, k).  A 64x64 bit
-//    matrix in shared memory answers "is y->x removed" in O(1).
+//    intersection of those three planes.  A cut removes the triangles beyond
+//    the plane; the directed edges of removed triangles whose reverse edge is
+//    not also removed form the rim of the hole, and each rim edge x->y
+//    becomes a new triangle (x, y, k).  A 64x64 bit matrix in shared memory
+//    answers "is y->x removed" in O(1).
 //  * Candidates come from a uniform grid of bins, ring by ring (Chebyshev
-//    distance in bins), filtered by |q| < 2 r_max, sorted by (|q|, id,
-//    image) with a warp bitonic sort, and clipped in that order.  The cell
-//    is complete once 2 r_max is inside the radius the gathered rings are
-//    guaranteed to cover.
+//    distance in bins), filtered by |q| < 2 r_max, sorted by (|q|, id, image)
+//    with a warp bitonic sort, and clipped in that order.  The cell is
+//    complete once 2 r_max is inside the radius the gathered rings cover.
 //  * Geometry: a face's polygon is walked around its plane in the dual, its
 //    area and centroid come from a fan, and the cell volume and centroid
 //    from the pyramids (apex p) over the faces: V_f = A h / 3 with h = |q|/2,
 //    centroid 3/4 of the way from p to the face centroid.
+//
+// Precision.  GB300 issues FP64 at 1/64 of the FP32 rate, and the warp-wide
+// FP64 instruction count bounds this kernel.  PREC 0 solves every vertex in
+// FP64 when it is created and classifies it in FP64.  PREC 1 keeps the
+// vertices in FP32 during clipping together with a forward error bound, and
+// classifies with FP32 where the bound settles the sign; where it does not,
+// it solves that vertex in FP64 and classifies exactly as PREC 0 does.  At the
+// end every vertex is solved in FP64 from its three planes.  Both variants
+// therefore take the same decisions and produce the same FP64 geometry.
 #include "mm_internal.cuh"
 
 namespace mm {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int CBATCH = 64;  // candidate buffer; flushed (sorted + clipped) when full
+static_assert(CBATCH == PMAX, "the candidate buffer doubles as per-face storage");
 
+template <int PREC>
 struct ClipSmem {
-    double cx[CBATCH], cy[CBATCH], cz[CBATCH], cd[CBATCH];  // candidates: q and |q|^2
+    union {
+        struct {
+            double x[CBATCH], y[CBATCH], z[CBATCH];
+            long long d2[CBATCH];  // bit pattern of |q|^2 (non-negative: orders like the value)
+        } c;
+        struct {
+            double a[PMAX], x[PMAX], y[PMAX], z[PMAX];  // per-face area and centroid
+        } f;
+    } u;
     int cid[CBATCH], csh[CBATCH];
     double px[PMAX], py[PMAX], pz[PMAX], po[PMAX];  // planes x.q <= po
     int pnb[PMAX], psh[PMAX];
-    double tx[TMAX], ty[TMAX], tz[TMAX];  // vertices
+    double tx[TMAX], ty[TMAX], tz[TMAX];  // FP64 vertices (PREC 1: only after clipping)
+    long long tr2[TMAX];                  // bits of |v|^2 (PREC 1: an upper bound)
     unsigned tv[TMAX];                    // a | b << 8 | c << 16
     unsigned long long bm[PMAX];          // removed directed edges x -> y
     unsigned stage[NSTAGE];               // triangles created by the current cut
-    // per-plane face results, written during finalisation
-    double fa[PMAX], fcx[PMAX], fcy[PMAX], fcz[PMAX];
+    float pfx[PREC ? PMAX : 1], pfy[PREC ? PMAX : 1], pfz[PREC ? PMAX : 1], pfo[PREC ? PMAX : 1];
+    float tfx[PREC ? TMAX : 1], tfy[PREC ? TMAX : 1], tfz[PREC ? TMAX : 1], terr[PREC ? TMAX : 1];
 };
 
 __device__ __forceinline__ unsigned lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
@@ -50,10 +69,10 @@ __device__ __forceinline__ double warp_sum(double v)
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     return v;
 }
-__device__ __forceinline__ double warp_max(double v)
+__device__ __forceinline__ long long warp_max_ll(long long v)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, o));
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(FULL, v, o));
     return v;
 }
 __device__ __forceinline__ unsigned long long warp_or64(unsigned long long v)
@@ -63,49 +82,98 @@ __device__ __forceinline__ unsigned long long warp_or64(unsigned long long v)
     return v;
 }
 
-// Intersection of planes a, b, c: x = (o_a (q_b x q_c) + o_b (q_c x q_a) + o_c (q_a x q_b)) / det.
-__device__ __forceinline__ void plane_vertex(const ClipSmem &S, int a, int b, int c, double &x, double &y,
-                                             double &z)
+// Intersection of planes a, b, c in FP64 with explicitly rounded operations
+// (so every caller gets the same bits):
+// x = (o_a (q_b x q_c) + o_b (q_c x q_a) + o_c (q_a x q_b)) / det(q_a, q_b, q_c).
+template <class S_t>
+__device__ __forceinline__ void vertex64(const S_t &S, int a, int b, int c, double &x, double &y, double &z)
 {
     const double ax = S.px[a], ay = S.py[a], az = S.pz[a], ao = S.po[a];
     const double bx = S.px[b], by = S.py[b], bz = S.pz[b], bo = S.po[b];
     const double cx = S.px[c], cy = S.py[c], cz = S.pz[c], co = S.po[c];
-    const double bcx = by * cz - bz * cy, bcy = bz * cx - bx * cz, bcz = bx * cy - by * cx;
-    const double cax = cy * az - cz * ay, cay = cz * ax - cx * az, caz = cx * ay - cy * ax;
-    const double abx = ay * bz - az * by, aby = az * bx - ax * bz, abz = ax * by - ay * bx;
-    const double inv = 1.0 / (ax * bcx + ay * bcy + az * bcz);
-    x = (ao * bcx + bo * cax + co * abx) * inv;
-    y = (ao * bcy + bo * cay + co * aby) * inv;
-    z = (ao * bcz + bo * caz + co * abz) * inv;
+    const double bcx = __fma_rn(by, cz, -__dmul_rn(bz, cy)), bcy = __fma_rn(bz, cx, -__dmul_rn(bx, cz)),
+                 bcz = __fma_rn(bx, cy, -__dmul_rn(by, cx));
+    const double cax = __fma_rn(cy, az, -__dmul_rn(cz, ay)), cay = __fma_rn(cz, ax, -__dmul_rn(cx, az)),
+                 caz = __fma_rn(cx, ay, -__dmul_rn(cy, ax));
+    const double abx = __fma_rn(ay, bz, -__dmul_rn(az, by)), aby = __fma_rn(az, bx, -__dmul_rn(ax, bz)),
+                 abz = __fma_rn(ax, by, -__dmul_rn(ay, bx));
+    const double det = __fma_rn(ax, bcx, __fma_rn(ay, bcy, __dmul_rn(az, bcz)));
+    const double inv = __drcp_rn(det);
+    x = __dmul_rn(__fma_rn(ao, bcx, __fma_rn(bo, cax, __dmul_rn(co, abx))), inv);
+    y = __dmul_rn(__fma_rn(ao, bcy, __fma_rn(bo, cay, __dmul_rn(co, aby))), inv);
+    z = __dmul_rn(__fma_rn(ao, bcz, __fma_rn(bo, caz, __dmul_rn(co, abz))), inv);
+}
+
+// The exact-path predicate: is vertex v strictly beyond the plane x.q <= off?
+__device__ __forceinline__ bool beyond64(double qx, double qy, double qz, double off, double x, double y, double z)
+{
+    return __fma_rn(qx, x, __fma_rn(qy, y, __dmul_rn(qz, z))) > off;
+}
+
+__device__ __forceinline__ long long r2_bits64(double x, double y, double z)
+{
+    return __double_as_longlong(__fma_rn(x, x, __fma_rn(y, y, __dmul_rn(z, z))));
+}
+
+// Intersection of planes a, b, c in FP32 with a bound on its distance to the
+// exact intersection.  With P = |q_a||q_b||q_c|, H = P / |det| >= 1 and
+// u = 2^-24, first-order rounding analysis of Cramer's rule (inputs rounded
+// to FP32, cross products, determinant, numerator, scaling) gives
+// |v~ - v| <= u H (5.5 sum|q| + 13 |v|); the bound used is three times that.
+// Ill-conditioned intersections get an infinite bound (always checked in FP64).
+__device__ __forceinline__ void vertex32(const ClipSmem<1> &S, int a, int b, int c, float &x, float &y, float &z,
+                                         float &err)
+{
+    const float ax = S.pfx[a], ay = S.pfy[a], az = S.pfz[a], ao = S.pfo[a];
+    const float bx = S.pfx[b], by = S.pfy[b], bz = S.pfz[b], bo = S.pfo[b];
+    const float cx = S.pfx[c], cy = S.pfy[c], cz = S.pfz[c], co = S.pfo[c];
+    const float bcx = fmaf(by, cz, -bz * cy), bcy = fmaf(bz, cx, -bx * cz), bcz = fmaf(bx, cy, -by * cx);
+    const float cax = fmaf(cy, az, -cz * ay), cay = fmaf(cz, ax, -cx * az), caz = fmaf(cx, ay, -cy * ax);
+    const float abx = fmaf(ay, bz, -az * by), aby = fmaf(az, bx, -ax * bz), abz = fmaf(ax, by, -ay * bx);
+    const float det = fmaf(ax, bcx, fmaf(ay, bcy, az * bcz));
+    const float inv = 1.0f / det;
+    x = fmaf(ao, bcx, fmaf(bo, cax, co * abx)) * inv;
+    y = fmaf(ao, bcy, fmaf(bo, cay, co * aby)) * inv;
+    z = fmaf(ao, bcz, fmaf(bo, caz, co * abz)) * inv;
+    // |q_k| = sqrt(2 o_k)
+    const float la = sqrtf(2.0f * ao), lb = sqrtf(2.0f * bo), lc = sqrtf(2.0f * co);
+    const float H = la * lb * lc / fabsf(det);
+    const float vn = fabsf(x) + fabsf(y) + fabsf(z);
+    const float u = 5.9604645e-8f;
+    err = 3.0f * u * H * (5.5f * (la + lb + lc) + 13.0f * vn);
+    if (!(u * H < 1e-3f) || !(err < 1e30f)) err = __int_as_float(0x7f800000);  // +inf
 }
 
 // Candidate order: (|q|^2, id, image code).
-__device__ __forceinline__ bool cand_less(const ClipSmem &S, int a, int b)
+template <int PREC>
+__device__ __forceinline__ bool cand_less(const ClipSmem<PREC> &S, int a, int b)
 {
-    if (S.cd[a] != S.cd[b]) return S.cd[a] < S.cd[b];
+    if (S.u.c.d2[a] != S.u.c.d2[b]) return S.u.c.d2[a] < S.u.c.d2[b];
     if (S.cid[a] != S.cid[b]) return S.cid[a] < S.cid[b];
     return S.csh[a] < S.csh[b];
 }
 
-__device__ __forceinline__ void cand_swap(ClipSmem &S, int a, int b)
+template <int PREC>
+__device__ __forceinline__ void cand_swap(ClipSmem<PREC> &S, int a, int b)
 {
     double t;
-    t = S.cx[a]; S.cx[a] = S.cx[b]; S.cx[b] = t;
-    t = S.cy[a]; S.cy[a] = S.cy[b]; S.cy[b] = t;
-    t = S.cz[a]; S.cz[a] = S.cz[b]; S.cz[b] = t;
-    t = S.cd[a]; S.cd[a] = S.cd[b]; S.cd[b] = t;
-    int u;
-    u = S.cid[a]; S.cid[a] = S.cid[b]; S.cid[b] = u;
-    u = S.csh[a]; S.csh[a] = S.csh[b]; S.csh[b] = u;
+    t = S.u.c.x[a]; S.u.c.x[a] = S.u.c.x[b]; S.u.c.x[b] = t;
+    t = S.u.c.y[a]; S.u.c.y[a] = S.u.c.y[b]; S.u.c.y[b] = t;
+    t = S.u.c.z[a]; S.u.c.z[a] = S.u.c.z[b]; S.u.c.z[b] = t;
+    long long l = S.u.c.d2[a]; S.u.c.d2[a] = S.u.c.d2[b]; S.u.c.d2[b] = l;
+    int v;
+    v = S.cid[a]; S.cid[a] = S.cid[b]; S.cid[b] = v;
+    v = S.csh[a]; S.csh[a] = S.csh[b]; S.csh[b] = v;
 }
 
 // Warp bitonic sort of the first m candidates (padded to a power of two).
-__device__ void sort_candidates(ClipSmem &S, int m, int lane)
+template <int PREC>
+__device__ void sort_candidates(ClipSmem<PREC> &S, int m, int lane)
 {
     int P = 1;
     while (P < m) P <<= 1;
     for (int t = m + lane; t < P; t += 32) {
-        S.cd[t] = __longlong_as_double(0x7ff0000000000000LL);  // +inf
+        S.u.c.d2[t] = 0x7fffffffffffffffLL;
         S.cid[t] = 0x7fffffff;
         S.csh[t] = 0x7fffffff;
     }
@@ -125,33 +193,65 @@ __device__ void sort_candidates(ClipSmem &S, int m, int lane)
 
 struct CellState {
     int np, nt;
-    double rmax2;
+    long long lim;  // bits of 4 r_max^2: a candidate with |q|^2 above it cannot cut
     int err;
     int cuts;
+    // work counters (warp-uniform), reported when the caller collects stats
+    unsigned pred64, solve64, fan64, tested;
 };
+
+template <int PREC>
+__device__ __forceinline__ void update_limit(ClipSmem<PREC> &S, CellState &C, int lane)
+{
+    long long m = 0;
+    for (int t = lane; t < C.nt; t += 32) m = max(m, S.tr2[t]);
+    m = warp_max_ll(m);
+    C.lim = __double_as_longlong(4.0 * __longlong_as_double(m));
+}
 
 // Clip the cell by candidate k.  Warp-uniform control flow throughout.
 template <int PREC>
-__device__ void clip_by(ClipSmem &S, int k, CellState &C, int lane)
+__device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
 {
-    const double qx = S.cx[k], qy = S.cy[k], qz = S.cz[k], off = 0.5 * S.cd[k];
+    const double qx = S.u.c.x[k], qy = S.u.c.y[k], qz = S.u.c.z[k];
+    const double off = 0.5 * __longlong_as_double(S.u.c.d2[k]);
     const int nchunk = (C.nt + 31) >> 5;
     unsigned outm[TMAX / 32];
     unsigned anyv = 0;
+    C.tested++;
+    if (PREC == 0) C.pred64 += C.nt;
+    float fqx = 0.f, fqy = 0.f, fqz = 0.f, foff = 0.f, fqn = 0.f;
+    if (PREC == 1) {
+        fqx = (float)qx; fqy = (float)qy; fqz = (float)qz; foff = (float)off;
+        fqn = sqrtf(2.0f * foff) * 1.0000005f;
+    }
 #pragma unroll
     for (int c = 0; c < TMAX / 32; ++c) {
         bool o = false;
-        int t = c * 32 + lane;
-        if (c < nchunk && t < C.nt) {
-            if (PREC == 0) {
-                o = qx * S.tx[t] + qy * S.ty[t] + qz * S.tz[t] > off;
-            } else {
-                // FP32 filter with a forward error bound; FP64 only near a tie.
-                float fx = (float)S.tx[t], fy = (float)S.ty[t], fz = (float)S.tz[t];
-                float s = fmaf((float)qx, fx, fmaf((float)qy, fy, fmaf((float)qz, fz, -(float)off)));
-                float mag = fabsf((float)qx * fx) + fabsf((float)qy * fy) + fabsf((float)qz * fz) + (float)off;
-                if (fabsf(s) > 4.0e-6f * mag) o = s > 0.0f;
-                else o = qx * S.tx[t] + qy * S.ty[t] + qz * S.tz[t] > off;
+        const int t = c * 32 + lane;
+        const bool live = c < nchunk && t < C.nt;
+        if constexpr (PREC == 0) {
+            if (live) o = beyond64(qx, qy, qz, off, S.tx[t], S.ty[t], S.tz[t]);
+        } else {
+            bool unsure = false;
+            if (live) {
+                const float vx = S.tfx[t], vy = S.tfy[t], vz = S.tfz[t];
+                const float s = fmaf(fqx, vx, fmaf(fqy, vy, fmaf(fqz, vz, -foff)));
+                const float mag = fabsf(fqx * vx) + fabsf(fqy * vy) + fabsf(fqz * vz) + foff;
+                const float B = fqn * S.terr[t] + 16.0f * 5.9604645e-8f * mag;
+                if (fabsf(s) > B) o = s > 0.0f;
+                else unsure = true;
+            }
+            const unsigned um = __ballot_sync(FULL, unsure);
+            if (um) {
+                C.pred64 += __popc(um);
+                C.solve64 += __popc(um);
+                if (unsure) {
+                    const unsigned v = S.tv[t];
+                    double x, y, z;
+                    vertex64(S, v & 255u, (v >> 8) & 255u, (v >> 16) & 255u, x, y, z);
+                    o = beyond64(qx, qy, qz, off, x, y, z);
+                }
             }
         }
         outm[c] = __ballot_sync(FULL, o);
@@ -163,6 +263,7 @@ __device__ void clip_by(ClipSmem &S, int k, CellState &C, int lane)
     if (lane == 0) {
         S.px[kp] = qx; S.py[kp] = qy; S.pz[kp] = qz; S.po[kp] = off;
         S.pnb[kp] = S.cid[k]; S.psh[kp] = S.csh[k];
+        if constexpr (PREC == 1) { S.pfx[kp] = fqx; S.pfy[kp] = fqy; S.pfz[kp] = fqz; S.pfo[kp] = foff; }
     }
     // mark the directed edges of the removed triangles
 #pragma unroll
@@ -225,45 +326,71 @@ __device__ void clip_by(ClipSmem &S, int k, CellState &C, int lane)
 #pragma unroll
     for (int c = 0; c < TMAX / 32; ++c) {
         if (c >= nchunk) break;
-        int t = c * 32 + lane;
-        bool keep = t < C.nt && !((outm[c] >> lane) & 1u);
-        unsigned km = __ballot_sync(FULL, keep);
+        const int t = c * 32 + lane;
+        const bool keep = t < C.nt && !((outm[c] >> lane) & 1u);
+        const unsigned km = __ballot_sync(FULL, keep);
         unsigned v = 0;
+        long long r2 = 0;
         double x = 0, y = 0, z = 0;
-        if (keep) { v = S.tv[t]; x = S.tx[t]; y = S.ty[t]; z = S.tz[t]; }
+        float fx = 0, fy = 0, fz = 0, fe = 0;
+        if (keep) {
+            v = S.tv[t];
+            r2 = S.tr2[t];
+            if constexpr (PREC == 0) { x = S.tx[t]; y = S.ty[t]; z = S.tz[t]; }
+            else { fx = S.tfx[t]; fy = S.tfy[t]; fz = S.tfz[t]; fe = S.terr[t]; }
+        }
         __syncwarp();
         if (keep) {
-            int d = dst + __popc(km & lanemask_lt());
-            S.tv[d] = v; S.tx[d] = x; S.ty[d] = y; S.tz[d] = z;
+            const int d = dst + __popc(km & lanemask_lt());
+            S.tv[d] = v;
+            S.tr2[d] = r2;
+            if constexpr (PREC == 0) { S.tx[d] = x; S.ty[d] = y; S.tz[d] = z; }
+            else { S.tfx[d] = fx; S.tfy[d] = fy; S.tfz[d] = fz; S.terr[d] = fe; }
         }
         dst += __popc(km);
         __syncwarp();
     }
     // append the new vertices
     for (int e = lane; e < nnew; e += 32) {
-        unsigned v = S.stage[e];
-        int t = nkept + e;
+        const unsigned v = S.stage[e];
+        const int t = nkept + e;
         S.tv[t] = v;
-        double x, y, z;
-        plane_vertex(S, v & 255u, (v >> 8) & 255u, kp, x, y, z);
-        S.tx[t] = x; S.ty[t] = y; S.tz[t] = z;
+        if constexpr (PREC == 0) {
+            double x, y, z;
+            vertex64(S, v & 255u, (v >> 8) & 255u, kp, x, y, z);
+            S.tx[t] = x; S.ty[t] = y; S.tz[t] = z;
+            S.tr2[t] = r2_bits64(x, y, z);
+        } else {
+            float x, y, z, er;
+            vertex32(S, v & 255u, (v >> 8) & 255u, kp, x, y, z, er);
+            if (!(er < 1e30f)) {
+                // ill-conditioned intersection: solve it in FP64 now and keep
+                // its FP32 rounding, whose error is then one rounding per axis
+                double X, Y, Z;
+                vertex64(S, v & 255u, (v >> 8) & 255u, kp, X, Y, Z);
+                x = (float)X; y = (float)Y; z = (float)Z;
+                er = 1.2e-7f * (fabsf(x) + fabsf(y) + fabsf(z)) + 1e-38f;
+            }
+            S.tfx[t] = x; S.tfy[t] = y; S.tfz[t] = z; S.terr[t] = er;
+            const double r = (double)sqrtf(x * x + y * y + z * z) * (1.0 + 1e-6) + (double)er;
+            S.tr2[t] = __double_as_longlong(r * r);
+        }
     }
     __syncwarp();
+    if (PREC == 0) C.solve64 += nnew;
     C.nt = nkept + nnew;
     C.np = kp + 1;
     C.cuts++;
-    double m = 0.0;
-    for (int t = lane; t < C.nt; t += 32) m = fmax(m, S.tx[t] * S.tx[t] + S.ty[t] * S.ty[t] + S.tz[t] * S.tz[t]);
-    C.rmax2 = warp_max(m);
+    update_limit(S, C, lane);
 }
 
 template <int PREC>
-__device__ void flush_batch(ClipSmem &S, int &ncand, CellState &C, int lane)
+__device__ void flush_batch(ClipSmem<PREC> &S, int &ncand, CellState &C, int lane)
 {
     if (ncand == 0) return;
     sort_candidates(S, ncand, lane);
     for (int k = 0; k < ncand; ++k) {
-        if (S.cd[k] > 4.0 * C.rmax2) break;
+        if (S.u.c.d2[k] > C.lim) break;
         clip_by<PREC>(S, k, C, lane);
         if (C.err) break;
     }
@@ -272,15 +399,15 @@ __device__ void flush_batch(ClipSmem &S, int &ncand, CellState &C, int lane)
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(32 * CLIP_WARPS)
+__global__ void __maxnreg__(128)
 k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, int64_t n, Grid g, double amin,
        double *__restrict__ vol, double *__restrict__ cen, Slots sl, DevStatus *st, int collect)
 {
-    __shared__ ClipSmem smem[CLIP_WARPS];
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t w = (int64_t)blockIdx.x * CLIP_WARPS + wid;
     if (w >= n) return;
-    ClipSmem &S = smem[wid];
+    ClipSmem<PREC> &S = reinterpret_cast<ClipSmem<PREC> *>(dyn_smem)[wid];
     const double4_32a me = sorted[w];
     const double px = me.x, py = me.y, pz = me.z;
     const int self = (int)me.w;
@@ -288,9 +415,9 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
 
     // starting box: planes 0..5 = +x,-x,+y,-y,+z,-z self-image bisectors
     if (lane < 6) {
-        int d = lane >> 1;
-        double sg = (lane & 1) ? -1.0 : 1.0;
-        double L = g.box[d];
+        const int d = lane >> 1;
+        const double sg = (lane & 1) ? -1.0 : 1.0;
+        const double L = g.box[d];
         S.px[lane] = d == 0 ? sg * L : 0.0;
         S.py[lane] = d == 1 ? sg * L : 0.0;
         S.pz[lane] = d == 2 ? sg * L : 0.0;
@@ -299,34 +426,39 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
         int s3[3] = {0, 0, 0};
         s3[d] = (lane & 1) ? -1 : 1;
         S.psh[lane] = (s3[0] + 1) + 3 * (s3[1] + 1) + 9 * (s3[2] + 1);
+        if constexpr (PREC == 1) {
+            S.pfx[lane] = (float)S.px[lane]; S.pfy[lane] = (float)S.py[lane]; S.pfz[lane] = (float)S.pz[lane];
+            S.pfo[lane] = (float)S.po[lane];
+        }
     }
     if (lane < 8) {
         // corner (sx, sy, sz): planes chosen by sign, ordered so det > 0
-        int sx = lane & 1, sy = (lane >> 1) & 1, sz = (lane >> 2) & 1;  // 1 means negative
+        const int sx = lane & 1, sy = (lane >> 1) & 1, sz = (lane >> 2) & 1;  // 1 means negative
         unsigned a = sx, b = 2 + sy, c = 4 + sz;
         // det(sign_x e_x, sign_y e_y, sign_z e_z) = product of signs
-        bool neg = (sx ^ sy ^ sz) & 1;
-        if (neg) { unsigned t = b; b = c; c = t; }
+        if ((sx ^ sy ^ sz) & 1) { unsigned t = b; b = c; c = t; }
         S.tv[lane] = a | (b << 8) | (c << 16);
-        S.tx[lane] = sx ? -0.5 * Lx : 0.5 * Lx;
-        S.ty[lane] = sy ? -0.5 * Ly : 0.5 * Ly;
-        S.tz[lane] = sz ? -0.5 * Lz : 0.5 * Lz;
+        const double x = sx ? -0.5 * Lx : 0.5 * Lx, y = sy ? -0.5 * Ly : 0.5 * Ly, z = sz ? -0.5 * Lz : 0.5 * Lz;
+        S.tr2[lane] = r2_bits64(x, y, z);
+        if constexpr (PREC == 0) { S.tx[lane] = x; S.ty[lane] = y; S.tz[lane] = z; }
+        else { S.tfx[lane] = (float)x; S.tfy[lane] = (float)y; S.tfz[lane] = (float)z; S.terr[lane] = 0.0f; }
     }
     for (int r = lane; r < PMAX; r += 32) S.bm[r] = 0ull;
     __syncwarp();
     CellState C;
     C.np = 6;
     C.nt = 8;
-    C.rmax2 = 0.25 * (Lx * Lx + Ly * Ly + Lz * Lz);
+    C.lim = __double_as_longlong(Lx * Lx + Ly * Ly + Lz * Lz);
     C.err = 0;
     C.cuts = 0;
+    C.pred64 = C.solve64 = C.fan64 = C.tested = 0;
 
     int cb[3];
     {
-        double pp[3] = {px, py, pz};
+        const double pp[3] = {px, py, pz};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            int c = (int)floor(pp[d] / g.bs[d]);
+            const int c = (int)floor(pp[d] / g.bs[d]);
             cb[d] = c < 0 ? 0 : (c >= g.g[d] ? g.g[d] - 1 : c);
         }
     }
@@ -338,12 +470,12 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
         const int nb = 2 * rh + 1;
         const int total = nb * nb * nb;
         for (int base = 0; base < total && !C.err; base += 32) {
-            int t = base + lane;
+            const int t = base + lane;
             int cur = 0, end = 0;
             int shx = 0, shy = 0, shz = 0;
             if (t < total) {
-                int ox = t % nb - rh, oy = (t / nb) % nb - rh, oz = t / (nb * nb) - rh;
-                int ch = max(abs(ox), max(abs(oy), abs(oz)));
+                const int ox = t % nb - rh, oy = (t / nb) % nb - rh, oz = t / (nb * nb) - rh;
+                const int ch = max(abs(ox), max(abs(oy), abs(oz)));
                 if (ch >= rl) {
                     int bx = cb[0] + ox, by = cb[1] + oy, bz = cb[2] + oz;
                     shx = (int)floor((double)bx / g.g[0]);
@@ -352,7 +484,7 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
                     bx -= shx * g.g[0];
                     by -= shy * g.g[1];
                     bz -= shz * g.g[2];
-                    int b = bx + g.g[0] * (by + g.g[1] * bz);
+                    const int b = bx + g.g[0] * (by + g.g[1] * bz);
                     cur = start[b];
                     end = start[b + 1];
                     // images two or more boxes away never cut (positions lie in [0, L))
@@ -366,20 +498,21 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
                 if (ncand + 32 > CBATCH) flush_batch<PREC>(S, ncand, C, lane);
                 if (C.err) break;
                 bool keep = false;
-                double qx = 0, qy = 0, qz = 0, d2 = 0;
+                double qx = 0, qy = 0, qz = 0;
+                long long d2b = 0;
                 int j = 0;
                 if (cur < end) {
-                    double4_32a P = sorted[cur];
+                    const double4_32a P = sorted[cur];
                     ++cur;
                     j = (int)P.w;
                     qx = P.x + offx; qy = P.y + offy; qz = P.z + offz;
-                    d2 = qx * qx + qy * qy + qz * qz;
-                    keep = !(j == self && selfimg) && d2 < 4.0 * C.rmax2;
+                    d2b = __double_as_longlong(__fma_rn(qx, qx, __fma_rn(qy, qy, __dmul_rn(qz, qz))));
+                    keep = !(j == self && selfimg) && d2b < C.lim;
                 }
-                unsigned km = __ballot_sync(FULL, keep);
+                const unsigned km = __ballot_sync(FULL, keep);
                 if (keep) {
-                    int s = ncand + __popc(km & lanemask_lt());
-                    S.cx[s] = qx; S.cy[s] = qy; S.cz[s] = qz; S.cd[s] = d2;
+                    const int s = ncand + __popc(km & lanemask_lt());
+                    S.u.c.x[s] = qx; S.u.c.y[s] = qy; S.u.c.z[s] = qz; S.u.c.d2[s] = d2b;
                     S.cid[s] = j; S.csh[s] = code;
                 }
                 ncand += __popc(km);
@@ -392,14 +525,14 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
         // radius the gathered rings are guaranteed to cover
         double R = 1e300;
         {
-            double pp[3] = {px, py, pz};
+            const double pp[3] = {px, py, pz};
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                double lo = (cb[d] - rh) * g.bs[d], hi = (cb[d] + rh + 1) * g.bs[d];
+                const double lo = (cb[d] - rh) * g.bs[d], hi = (cb[d] + rh + 1) * g.bs[d];
                 R = fmin(R, fmin(pp[d] - lo, hi - pp[d]));
             }
         }
-        if (4.0 * C.rmax2 <= R * R) done = true;
+        if (C.lim <= __double_as_longlong(R * R)) done = true;
         else {
             rl = rh + 1;
             rh = rl;
@@ -407,20 +540,31 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
         }
     }
 
-    // ---- finalisation: faces, volume, centroid
+    // ---- finalisation: FP64 vertices, faces, volume, centroid
+    if (PREC == 1 && !C.err) {  // final FP64 vertices from their planes
+        C.solve64 += C.nt;
+        for (int t = lane; t < C.nt; t += 32) {
+            const unsigned v = S.tv[t];
+            double x, y, z;
+            vertex64(S, v & 255u, (v >> 8) & 255u, (v >> 16) & 255u, x, y, z);
+            S.tx[t] = x; S.ty[t] = y; S.tz[t] = z;
+        }
+        __syncwarp();
+    }
     double vl = 0.0, vcx = 0.0, vcy = 0.0, vcz = 0.0;
+    unsigned fan = 0;
     if (!C.err) {
         for (int p = lane; p < C.np; p += 32) {
             int t0 = -1;
             unsigned y = 0;
             for (int t = 0; t < C.nt; ++t) {
-                unsigned v = S.tv[t];
-                unsigned a = v & 255u, b = (v >> 8) & 255u, c = (v >> 16) & 255u;
+                const unsigned v = S.tv[t];
+                const unsigned a = v & 255u, b = (v >> 8) & 255u, c = (v >> 16) & 255u;
                 if (a == (unsigned)p) { t0 = t; y = c; break; }
                 if (b == (unsigned)p) { t0 = t; y = a; break; }
                 if (c == (unsigned)p) { t0 = t; y = b; break; }
             }
-            S.fa[p] = 0.0;
+            S.u.f.a[p] = 0.0;
             if (t0 < 0) continue;  // plane no longer bounds the cell
             const double qx = S.px[p], qy = S.py[p], qz = S.pz[p];
             const double x0 = S.tx[t0], y0 = S.ty[t0], z0 = S.tz[t0];
@@ -433,8 +577,8 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
                 int tn = -1;
                 unsigned z = 0;
                 for (int t = 0; t < C.nt; ++t) {
-                    unsigned v = S.tv[t];
-                    unsigned a = v & 255u, b = (v >> 8) & 255u, c = (v >> 16) & 255u;
+                    const unsigned v = S.tv[t];
+                    const unsigned a = v & 255u, b = (v >> 8) & 255u, c = (v >> 16) & 255u;
                     if (a == (unsigned)p && b == y) { tn = t; z = c; break; }
                     if (b == (unsigned)p && c == y) { tn = t; z = a; break; }
                     if (c == (unsigned)p && a == y) { tn = t; z = b; break; }
@@ -455,14 +599,15 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
                 ++cnt;
                 y = z;
             }
+            fan += cnt;
             if (!ok) { C.err |= ST_EDEGEN; continue; }
             const double ql = sqrt(qx * qx + qy * qy + qz * qz);
             const double area = 0.5 * fabs(A2) / ql;
             const double fx = A2 != 0.0 ? sx / (3.0 * A2) : x0;
             const double fy = A2 != 0.0 ? sy / (3.0 * A2) : y0;
             const double fz = A2 != 0.0 ? sz / (3.0 * A2) : z0;
-            S.fa[p] = area;
-            S.fcx[p] = fx; S.fcy[p] = fy; S.fcz[p] = fz;
+            S.u.f.a[p] = area;
+            S.u.f.x[p] = fx; S.u.f.y[p] = fy; S.u.f.z[p] = fz;
             const double vp = area * ql / 6.0;  // A h / 3 with h = |q| / 2
             vl += vp;
             vcx += 0.75 * vp * fx;
@@ -472,6 +617,8 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
         C.err = __reduce_or_sync(FULL, (unsigned)C.err);
     }
     __syncwarp();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) fan += __shfl_xor_sync(FULL, fan, o);
     vl = warp_sum(vl);
     vcx = warp_sum(vcx);
     vcy = warp_sum(vcy);
@@ -481,20 +628,20 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
     if (!C.err) {
         const int64_t sbase = (int64_t)self * MAXF;
         for (int p0 = 0; p0 < C.np; p0 += 32) {
-            int p = p0 + lane;
-            bool keep = p < C.np && S.fa[p] > amin;
-            unsigned km = __ballot_sync(FULL, keep);
+            const int p = p0 + lane;
+            const bool keep = p < C.np && S.u.f.a[p] > amin;
+            const unsigned km = __ballot_sync(FULL, keep);
             if (keep) {
-                int k = nface + __popc(km & lanemask_lt());
+                const int k = nface + __popc(km & lanemask_lt());
                 if (k < MAXF) {
-                    int64_t s = sbase + k;
+                    const int64_t s = sbase + k;
                     sl.nb[s] = S.pnb[p];
                     sl.sh[s] = (unsigned char)S.psh[p];
-                    sl.area[s] = S.fa[p];
+                    sl.area[s] = S.u.f.a[p];
                     const int64_t ns = n * (int64_t)MAXF;
-                    sl.fc[s] = px + S.fcx[p];
-                    sl.fc[ns + s] = py + S.fcy[p];
-                    sl.fc[2 * ns + s] = pz + S.fcz[p];
+                    sl.fc[s] = px + S.u.f.x[p];
+                    sl.fc[ns + s] = py + S.u.f.y[p];
+                    sl.fc[2 * ns + s] = pz + S.u.f.z[p];
                 }
             }
             nface += __popc(km);
@@ -518,18 +665,33 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
             atomicMax(&st->max_tris, C.nt);
             if (rings > 1) atomicAdd(&st->multi_ring, 1);
             atomicAdd(&st->cuts, (unsigned long long)C.cuts);
+            atomicAdd(&st->pred64, (unsigned long long)C.pred64);
+            atomicAdd(&st->solve64, (unsigned long long)C.solve64);
+            atomicAdd(&st->fan64, (unsigned long long)fan);
+            atomicAdd(&st->tested, (unsigned long long)C.tested);
         }
     }
 }
 
-void launch_clip(const double4_32a *sorted, const int *start, int64_t n, const Grid &g, double amin, int precision,
-                 double *vol, double *cen, Slots sl, DevStatus *st, cudaStream_t s)
+template <int PREC>
+static void launch_clip_t(const double4_32a *sorted, const int *start, int64_t n, const Grid &g, double amin,
+                          double *vol, double *cen, Slots sl, DevStatus *st, int collect, cudaStream_t s)
 {
-    int64_t nb = (n + CLIP_WARPS - 1) / CLIP_WARPS;
-    if (precision == 0)
-        k_clip<0><<<(unsigned)nb, 32 * CLIP_WARPS, 0, s>>>(sorted, start, n, g, amin, vol, cen, sl, st, 1);
-    else
-        k_clip<1><<<(unsigned)nb, 32 * CLIP_WARPS, 0, s>>>(sorted, start, n, g, amin, vol, cen, sl, st, 1);
+    const size_t smem = sizeof(ClipSmem<PREC>) * CLIP_WARPS;
+    static bool configured = false;  // the attribute is per function and process-wide
+    if (!configured) {
+        cudaFuncSetAttribute(k_clip<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        configured = true;
+    }
+    const int64_t nb = (n + CLIP_WARPS - 1) / CLIP_WARPS;
+    k_clip<PREC><<<(unsigned)nb, 32 * CLIP_WARPS, smem, s>>>(sorted, start, n, g, amin, vol, cen, sl, st, collect);
+}
+
+void launch_clip(const double4_32a *sorted, const int *start, int64_t n, const Grid &g, double amin, int precision,
+                 int collect, double *vol, double *cen, Slots sl, DevStatus *st, cudaStream_t s)
+{
+    if (precision == 0) launch_clip_t<0>(sorted, start, n, g, amin, vol, cen, sl, st, collect, s);
+    else launch_clip_t<1>(sorted, start, n, g, amin, vol, cen, sl, st, collect, s);
 }
 
 }  // namespace mm

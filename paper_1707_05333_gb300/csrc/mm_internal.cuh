@@ -36,6 +36,10 @@ struct DevStatus {
     int max_cand, max_planes, max_tris;
     int multi_ring;
     unsigned long long cuts;
+    unsigned long long pred64;   // FP64 plane tests  (q.v > o: 5 flops)
+    unsigned long long solve64;  // FP64 three-plane solves (51 flops)
+    unsigned long long fan64;    // FP64 fan terms of the face geometry (33 flops)
+    unsigned long long tested;   // candidates tested against the cell
 };
 
 struct Grid {
@@ -63,7 +67,7 @@ size_t scan_tmp_size(int64_t n);
 void launch_scan(const int *in, int *out, int64_t n, int *tmp, cudaStream_t s);
 
 void launch_clip(const double4_32a *sorted, const int *start, int64_t n, const Grid &g, double amin,
-                 int precision, double *vol, double *cen, Slots sl, DevStatus *st, cudaStream_t s);
+                 int precision, int collect, double *vol, double *cen, Slots sl, DevStatus *st, cudaStream_t s);
 
 void launch_face_confirm(int64_t n, Slots sl, unsigned long long *emit_mask, unsigned long long *conf_mask,
                          signed char *partner, int *emit_cnt, int *conf_cnt, cudaStream_t s);
