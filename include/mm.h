@@ -158,6 +158,32 @@ mm_status mm_prims_to_charges(mm_ctx *ctx, const mm_mesh *mesh, const double *rh
  * written to the device array totals[5]. */
 mm_status mm_totals(mm_ctx *ctx, const double *U, int64_t n, double *totals);
 
+/* Per-component totals of U[5][n] like mm_totals, for callers that cannot
+ * allocate device memory: code running while a stream is captured into a
+ * CUDA graph (no cudaMalloc there), code that must not synchronise the device
+ * (cudaFree does), and hosts whose own pool owns all device memory.  It needs
+ * no context and allocates nothing: its scratch is a fixed array of 320 KiB
+ * inside this library's device image, placed on a device when the library is
+ * loaded there and held until the process exits.  The paper has no
+ * counterpart; this is a service entry point of the library.
+ *  - U[5][n] and totals[5] are device pointers owned by the caller; work is
+ *    enqueued on cuda_stream (a cudaStream_t, or NULL) without waiting.
+ *  - n must be in [1, MM_TOTALS_NOALLOC_MAX_CELLS]; a larger n returns
+ *    MM_ECAPACITY, n < 1 or a NULL pointer MM_EINVAL.  When err is not NULL,
+ *    a message of at most err_len bytes (NUL-terminated) describes a failure.
+ *  - The first call on a device looks up the scratch array's device address
+ *    (once per device, with that device current); make that first call
+ *    before any stream capture.
+ *  - Every call shares the one scratch array, which keeps the last call's
+ *    partial sums; each call writes every partial it reads, so nothing has to
+ *    start at zero.  Calls whose kernels overlap on the GPU (other streams,
+ *    other threads) race on the scratch and give wrong totals: order them.
+ *  - Results agree with mm_totals to rounding (compensated sums over tiles of
+ *    4096 cells instead of the context's fixed block ranges). */
+#define MM_TOTALS_NOALLOC_MAX_CELLS 16777216LL
+mm_status mm_totals_noalloc(const double *U, int64_t n, double *totals, void *cuda_stream, char *err,
+                            int64_t err_len);
+
 /* Stream-ordered device-to-device copy of `bytes` bytes (a convenience for
  * bindings that read the context-owned mesh arrays into their own buffers). */
 mm_status mm_copy(mm_ctx *ctx, void *dst, const void *src, int64_t bytes);

@@ -55,7 +55,7 @@ class MeshStruct(ctypes.Structure):
 EXPORTS = ["mm_default_config", "mm_create", "mm_destroy", "mm_last_error", "mm_set_config",
            "mm_tessellate", "mm_gradients", "mm_mesh_velocity", "mm_timestep", "mm_flux_step",
            "mm_drift", "mm_step", "mm_prims_to_charges", "mm_totals", "mm_copy", "mm_tess_stats",
-           "mm_set_timing", "mm_stage_times", "mm_kernel_launches"]
+           "mm_set_timing", "mm_stage_times", "mm_kernel_launches", "mm_totals_noalloc"]
 
 STATS = ["max_candidates", "max_planes", "max_vertices", "multi_ring_cells", "cuts", "fp64_plane_tests",
          "fp64_vertex_solves", "fp64_fan_terms", "candidates_tested"]
@@ -99,6 +99,7 @@ def load(path: str | None = None):
     L.mm_tess_stats.argtypes = [_c_p, P(_c_i64)]
     L.mm_set_timing.argtypes = [_c_p, ctypes.c_int]
     L.mm_stage_times.argtypes = [_c_p, P(ctypes.c_double), P(_c_i64)]
+    L.mm_totals_noalloc.argtypes = [_c_p, _c_i64, _c_p, _c_p, ctypes.c_char_p, _c_i64]
     L.mm_kernel_launches.argtypes = [_c_p]
     L.mm_kernel_launches.restype = _c_i64
     for name in EXPORTS:
@@ -106,6 +107,17 @@ def load(path: str | None = None):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
+
+
+def mm_totals_noalloc(U: torch.Tensor, totals: torch.Tensor, stream: torch.cuda.Stream | None = None) -> None:
+    """Totals of U (5, n) into totals (5,) through the allocation-free entry point."""
+    L = load()
+    n = U.shape[1]
+    buf = ctypes.create_string_buffer(256)
+    s = stream or torch.cuda.current_stream()
+    st = L.mm_totals_noalloc(_ptr(U, (5, n)), n, _ptr(totals, (5,)), _c_p(s.cuda_stream), buf, len(buf))
+    if st != 0:
+        raise MMError("mm_totals_noalloc", st, buf.value.decode())
 
 
 def default_config(**kw) -> Config:
