@@ -44,6 +44,9 @@ def parse():
     p.add_argument("--cpu-sample-side", type=int, default=24)
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-variants", action="store_true",
+                   help="skip the mixed-precision and batched-ensemble measurements")
+    p.add_argument("--ensemble-boxes", type=int, default=512)
     return p.parse_args()
 
 
@@ -197,6 +200,90 @@ def algorithmic_bytes(stage, n, F):
     return None
 
 
+def time_steps(torch, stream, fn, steps):
+    """Device time of `steps` calls of fn on `stream`, in ms (CUDA events)."""
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    stream.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def measure_mixed_single(args, w):
+    """The mixed-precision path on the same workload (same bench protocol)."""
+    import torch
+    from paper_1707_05333_gb300 import binding as BD
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = BD.Context(stream=stream, gamma=w.gamma, cfl=w.cfl, limiter=1, precision=1)
+        pos = torch.tensor(w.pos.T.copy(), dtype=torch.float64, device="cuda")
+        mesh = ctx.mm_tessellate(pos, w.box)
+        U = ctx.mm_prims_to_charges(mesh, torch.tensor(w.rho, device="cuda"), torch.tensor(w.vel.T.copy(), device="cuda"),
+                                    torch.tensor(w.pres, device="cuda"))
+        for _ in range(args.warmup):
+            ctx.mm_step(pos, U, w.box)
+        ms = time_steps(torch, stream, lambda: ctx.mm_step(pos, U, w.box), args.steps)
+        ctx.close()
+    return {"value": w.n * args.steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
+            "dtype": "f64+f32", "note": "FP32 gradients/half step/fluxes, FP64 clipping decisions, geometry and update"}
+
+
+def measure_ensemble(args):
+    """Batched ensemble of independent periodic boxes (log-uniform sizes,
+    lognormal GRF density): one CUDA-graph replay per step for all boxes,
+    against one mm_step per box.  Mixed precision."""
+    import numpy as np
+    import torch
+    from paper_1707_05333_gb300 import binding as BD
+    from paper_1707_05333_gb300 import workloads as WL
+    sizes = WL.ensemble_sizes(args.ensemble_boxes)
+    boxes = [WL.ensemble_box(b, int(nb)) for b, nb in enumerate(sizes)]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(off[-1])
+    L = np.ones((len(boxes), 3))
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = BD.Context(stream=stream, gamma=5.0 / 3.0, cfl=0.3, limiter=1, precision=1)
+        # charges from each box's own tessellation
+        Us = []
+        for wb in boxes:
+            pb = torch.tensor(wb.pos.T.copy(), dtype=torch.float64, device="cuda")
+            mb = ctx.mm_tessellate(pb, wb.box)
+            Us.append(ctx.mm_prims_to_charges(mb, torch.tensor(wb.rho, device="cuda"),
+                                              torch.tensor(wb.vel.T.copy(), device="cuda"),
+                                              torch.tensor(wb.pres, device="cuda")))
+        pos0 = torch.tensor(np.concatenate([wb.pos for wb in boxes]).T.copy(), dtype=torch.float64, device="cuda")
+        U0 = torch.cat(Us, dim=1).contiguous()
+        pos, U = pos0.clone(), U0.clone()
+        for _ in range(max(2, args.warmup)):
+            ctx.mm_step_batched(pos, U, off, L)
+        ctx.mm_sync_status()
+        l0 = ctx.mm_kernel_launches()
+        ms_graph = time_steps(torch, stream, lambda: ctx.mm_step_batched(pos, U, off, L), args.steps)
+        launches = (ctx.mm_kernel_launches() - l0) // max(1, args.steps)
+        ctx.mm_sync_status()
+        # one launch sequence per box (each box its own arrays)
+        pb = [pos0[:, off[b]:off[b + 1]].contiguous() for b in range(len(boxes))]
+        ub = [U0[:, off[b]:off[b + 1]].contiguous() for b in range(len(boxes))]
+
+        def per_box():
+            for b in range(len(boxes)):
+                ctx.mm_step(pb[b], ub[b], L[b])
+        per_box()
+        per_steps = 1
+        ms_box = time_steps(torch, stream, per_box, per_steps)
+        ctx.close()
+    graph = n * args.steps / (ms_graph / 1e3)
+    box = n * per_steps / (ms_box / 1e3)
+    return {"workload": f"ensemble of {len(boxes)} periodic unit boxes, {n} cells (2^10..2^16 per box)",
+            "precision": "mixed", "graph_cells_per_s": graph, "graph_ms_per_step": ms_graph / args.steps,
+            "kernels_per_step": launches, "per_box_cells_per_s": box, "per_box_ms_per_step": ms_box / per_steps,
+            "speedup": graph / box}
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_1707_05333_gb300 import build as B
@@ -312,6 +399,10 @@ def run_ours(args, world, rank, local):
                         "algorithmic_bytes_per_launch": byts, "launch_ms": dom_ms}
     stage_ms = {k: v[0] / max(1, v[1]) for k, v in stages.items()}
 
+    variants = None
+    if rank == 0 and not args.no_variants:
+        variants = {"mixed_same_workload": measure_mixed_single(args, w), "batched_ensemble": measure_ensemble(args)}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rate, steps, el, ncpu = oracle_rate(args.cpu_sample_side, args.cpu_seconds)
@@ -328,7 +419,7 @@ def run_ours(args, world, rank, local):
                            "l2": "inputs larger than L2 (state + mesh >> 129 MB), no flush"},
                 "roofline": roofline, "stage_ms": stage_ms, "tess_stats_per_cell": {k: v / n for k, v in tstats.items()
                                                                                    if not k.startswith("max")}, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clocks}
+                "gpu_launches": launches, "clocks": clocks, "variants": variants}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -82,11 +82,15 @@ typedef struct mm_ctx mm_ctx;
  * inc_face[inc_off[k] .. inc_off[k+1]); an entry f >= 0 means k is face_i[f]
  * (outward normal +n), an entry ~f (< 0) means k is face_j[f] (normal -n).
  * cell_centroid is r_k + (centroid relative to r_k): it may lie outside the
- * box near the boundary. */
+ * box near the boundary.  A batched mesh (mm_step_batched) holds nboxes
+ * independent boxes; every dt argument below is then one value per box. */
 typedef struct {
     int64_t n, nfaces, nincident;
     int64_t face_stride; /* row stride of face_normal and face_centroid (>= nfaces) */
-    double box[3];
+    double box[3];       /* size of box 0 (the only box of a single-box mesh) */
+    int64_t nboxes;      /* independent periodic boxes stored back to back */
+    const int32_t *cell_box; /* [n] box of each cell */
+    const double *box_size;  /* [nboxes][3] box sizes */
     const int32_t *face_i, *face_j, *face_shift;
     const double *face_area;     /* [F]    */
     const double *face_normal;   /* [3][face_stride] */
@@ -148,6 +152,30 @@ mm_status mm_drift(mm_ctx *ctx, double *pos, int64_t n, const double *w, const d
  * w_out (device [3][n], may be NULL) receives w. */
 mm_status mm_step(mm_ctx *ctx, double *pos, double *U, int64_t n, const double box[3],
                   const double *dt_fixed, double *dt_out, double *w_out);
+
+/* One whole step (as mm_step, CFL timestep per box) for nboxes independent
+ * periodic boxes stored back to back: box b holds cells
+ * [box_off[b], box_off[b+1]) of pos[3][n] and U[5][n] and has size
+ * boxes[3b..3b+2]; box_off and boxes are HOST arrays, box_off[0] = 0 and
+ * box_off[nboxes] = n.  Every box is an independent problem: its own bins,
+ * face threshold and timestep; results equal mm_step on each box alone.
+ * The first call for a given (pos, U, n, boxes, dt_out, config) reserves
+ * fixed capacities (10 n unique faces), captures the whole step into a CUDA
+ * graph on the context's stream (which must not be the legacy default
+ * stream) and launches it; later identical calls only relaunch the graph,
+ * with no host synchronisation.  dt_out (device [nboxes], may be NULL)
+ * receives each box's dt.  Device-side failures (including a capacity
+ * overflow) are reported by mm_sync_status. */
+mm_status mm_step_batched(mm_ctx *ctx, double *pos, double *U, int64_t n, const int64_t *box_off,
+                          const double *boxes, int nboxes, double *dt_out);
+
+/* Wait for the context's stream and report the device status word of the
+ * last tessellation (mm_step_batched does not wait on its own). */
+mm_status mm_sync_status(mm_ctx *ctx);
+
+/* The mesh of the last tessellation (waits; for a batched step the face and
+ * incidence counts are read back from the device). */
+mm_status mm_current_mesh(mm_ctx *ctx, mm_mesh *out);
 
 /* Charges from per-volume primitives on the current mesh:
  * U = (rho, rho v, P/(gamma-1) + rho |v|^2 / 2) V.  rho[n], vel[3][n], P[n]. */

@@ -46,7 +46,7 @@ class Config(ctypes.Structure):
 
 class MeshStruct(ctypes.Structure):
     _fields_ = [("n", _c_i64), ("nfaces", _c_i64), ("nincident", _c_i64), ("face_stride", _c_i64),
-                ("box", ctypes.c_double * 3),
+                ("box", ctypes.c_double * 3), ("nboxes", _c_i64), ("cell_box", _c_p), ("box_size", _c_p),
                 ("face_i", _c_p), ("face_j", _c_p), ("face_shift", _c_p), ("face_area", _c_p),
                 ("face_normal", _c_p), ("face_centroid", _c_p), ("cell_volume", _c_p),
                 ("cell_centroid", _c_p), ("inc_off", _c_p), ("inc_face", _c_p)]
@@ -55,7 +55,8 @@ class MeshStruct(ctypes.Structure):
 EXPORTS = ["mm_default_config", "mm_create", "mm_destroy", "mm_last_error", "mm_set_config",
            "mm_tessellate", "mm_gradients", "mm_mesh_velocity", "mm_timestep", "mm_flux_step",
            "mm_drift", "mm_step", "mm_prims_to_charges", "mm_totals", "mm_copy", "mm_tess_stats",
-           "mm_set_timing", "mm_stage_times", "mm_kernel_launches", "mm_totals_noalloc"]
+           "mm_set_timing", "mm_stage_times", "mm_kernel_launches", "mm_totals_noalloc", "mm_step_batched",
+           "mm_sync_status", "mm_current_mesh"]
 
 STATS = ["max_candidates", "max_planes", "max_vertices", "multi_ring_cells", "cuts", "fp64_plane_tests",
          "fp64_vertex_solves", "fp64_fan_terms", "candidates_tested"]
@@ -99,6 +100,9 @@ def load(path: str | None = None):
     L.mm_tess_stats.argtypes = [_c_p, P(_c_i64)]
     L.mm_set_timing.argtypes = [_c_p, ctypes.c_int]
     L.mm_stage_times.argtypes = [_c_p, P(ctypes.c_double), P(_c_i64)]
+    L.mm_step_batched.argtypes = [_c_p, _c_p, _c_p, _c_i64, P(_c_i64), P(ctypes.c_double), ctypes.c_int, _c_p]
+    L.mm_sync_status.argtypes = [_c_p]
+    L.mm_current_mesh.argtypes = [_c_p, P(MeshStruct)]
     L.mm_totals_noalloc.argtypes = [_c_p, _c_i64, _c_p, _c_p, ctypes.c_char_p, _c_i64]
     L.mm_kernel_launches.argtypes = [_c_p]
     L.mm_kernel_launches.restype = _c_i64
@@ -266,6 +270,27 @@ class Context:
         b = (ctypes.c_double * 3)(*[float(x) for x in box])
         self._call("mm_step", self.h, _ptr(pos, (3, n)), _ptr(U, (5, n)), n, b,
                    _ptr(dt_fixed, (1,)), _ptr(dt_out, (1,)), _ptr(w_out, (3, n)))
+
+    def mm_step_batched(self, pos, U, box_off, boxes, dt_out=None):
+        """One step of independent periodic boxes stored back to back (replays a
+        captured CUDA graph after the first call with the same arguments)."""
+        import numpy as _np
+        n = pos.shape[1]
+        off = _np.ascontiguousarray(box_off, dtype=_np.int64)
+        bx = _np.ascontiguousarray(boxes, dtype=_np.float64).reshape(-1)
+        nbox = len(off) - 1
+        self._keep = (off, bx)
+        self._call("mm_step_batched", self.h, _ptr(pos, (3, n)), _ptr(U, (5, n)), n,
+                   off.ctypes.data_as(ctypes.POINTER(_c_i64)), bx.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                   nbox, _ptr(dt_out, (nbox,)))
+
+    def mm_sync_status(self) -> None:
+        self._call("mm_sync_status", self.h)
+
+    def mm_current_mesh(self) -> Mesh:
+        s = MeshStruct()
+        self._call("mm_current_mesh", self.h, ctypes.byref(s))
+        return Mesh(self, s)
 
     def mm_prims_to_charges(self, mesh: Mesh, rho, vel, P) -> torch.Tensor:
         U = torch.empty((5, mesh.n), dtype=torch.float64, device=self.device)

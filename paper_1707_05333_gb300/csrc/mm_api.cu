@@ -1,4 +1,10 @@
 // mm_api.cu -- the C ABI: context, device workspace and the call sequence.
+//
+// A mesh is a batch of B independent periodic boxes stored back to back; the
+// single-box calls (mm_tessellate, mm_step, ...) use B = 1.  mm_tessellate
+// waits once for the face count and sizes the face arrays exactly.
+// mm_step_batched instead reserves fixed capacities, so the whole step has no
+// host synchronisation and is captured once into a CUDA graph and replayed.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -17,12 +23,40 @@ struct Buf {
     size_t bytes = 0;
 };
 
+// Identity of a captured batched step: replays are valid while all of it holds.
+struct GraphKey {
+    const void *pos = nullptr, *U = nullptr, *dt_out = nullptr;
+    int64_t n = 0;
+    int64_t tables_gen = 0;
+    int nbox = 0;
+    unsigned long long boxes_hash = 0;
+    mm_config cfg{};
+};
+
+unsigned long long fnv1a(const void *data, size_t bytes, unsigned long long h)
+{
+    const unsigned char *p = static_cast<const unsigned char *>(data);
+    for (size_t k = 0; k < bytes; ++k) {
+        h ^= p[k];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
 }  // namespace
 
 struct mm_ctx {
     mm_config cfg;
     cudaStream_t stream = nullptr;
     char err[512] = {0};
+    // box tables
+    Buf boxes_dev, boxL_dev, box_off_dev, cbox;
+    BoxDev *boxes_host = nullptr;  // pinned staging
+    double *boxL_host = nullptr;
+    long long *box_off_host = nullptr;
+    int nbox_cap = 0, nbox = 0;
+    int64_t nbins = 0, tess_n = 0;
+    int64_t tables_gen = 0;  // bumped whenever the box tables are rewritten
     // binning
     Buf bin_of, bin_count, bin_start, bin_cursor, sorted, scan_tmp;
     // clipping output
@@ -31,27 +65,35 @@ struct mm_ctx {
     Buf emit_mask, conf_mask, partner, emit_cnt, conf_cnt, face_off, inc_off;
     Buf face_i, face_j, face_shift, face_area, face_normal, face_cen, inc_face;
     // hydro scratch
-    Buf Wh, grad, flux, w_int, dt_int, tot_partial;
+    Buf Wh, grad, flux, w_int, dt_int, tot_partial, drift_box, drift_cbox;
+    // mixed-precision records
+    Buf x_fij, x_fa, x_fq, x_ff, x_cw, x_ch, x_grad, x_wv, x_flux;
     DevStatus *st = nullptr;        // device
     DevStatus *st_host = nullptr;   // pinned
     int *cnt_host = nullptr;        // pinned: faces, incidences
+    double *box3_host = nullptr;    // pinned: one box size for mm_drift
     int64_t fcap = 0, icap = 0;
-    int collect_stats = 1;
     MeshDev mesh{};
+    int64_t mesh_ninc = 0;
     bool have_mesh = false;
-    Grid grid{};
     // per-stage timing (events recorded on the stream) and launch counting
     int timing = 0;
+    bool capturing = false;
     std::vector<cudaEvent_t> events;
     std::vector<int> ev_stage;  // stage of each (begin, end) pair
     size_t ev_used = 0;
     int64_t launches = 0;
+    // captured batched step
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    GraphKey gkey;
+    int64_t graph_launches = 0;
 };
 
 // Record the begin (or end) event of a stage when timing is on.
 static void stage_mark(mm_ctx *c, int stage, bool begin)
 {
-    if (!c->timing) return;
+    if (!c->timing || c->capturing) return;
     if (c->ev_used == c->events.size()) {
         cudaEvent_t e;
         if (cudaEventCreate(&e) != cudaSuccess) return;
@@ -94,11 +136,21 @@ static mm_status fail(mm_ctx *c, mm_status s, const char *fmt, ...)
                         __LINE__);                                                                       \
     } while (0)
 
+static void stage_mark_cb(void *arg, int stage, bool begin) { stage_mark(static_cast<mm_ctx *>(arg), stage, begin); }
+
+static void drop_graph(mm_ctx *c);
+
 // Grow a buffer to at least `bytes` (with headroom); contents are not kept.
+// A captured graph holds the old addresses, so growth discards it.
 static mm_status ensure(mm_ctx *c, Buf &b, size_t bytes)
 {
     if (bytes == 0) bytes = 16;
     if (b.bytes >= bytes) return MM_OK;
+    if (c->capturing) return fail(c, MM_ECUDA, "workspace growth during stream capture");
+    if (c->gexec) {
+        CK(cudaStreamSynchronize(c->stream));
+        drop_graph(c);
+    }
     if (b.p) CK(cudaFree(b.p));
     b.p = nullptr;
     b.bytes = 0;
@@ -151,9 +203,12 @@ static mm_status read_status(mm_ctx *c)
     if (s.flags & ST_EDEGEN)
         return fail(c, MM_EDEGENERATE, "cell %d: inconsistent cut (degenerate or coincident generators)",
                     s.bad_cell);
+    if (s.flags & ST_ECAP_MESH)
+        return fail(c, MM_ECAPACITY, "the batch has more faces than its fixed capacity (%lld faces, %lld incidences)",
+                    (long long)c->fcap, (long long)c->icap);
     return fail(c, MM_ECAPACITY,
-                "cell %d exceeded a per-cell capacity (flags 0x%x: 2 candidates, 4 planes (%d), 8 vertices "
-                "(%d), 16 vertices per cut (%d), 32 faces (%d), 64 search rings (%d))",
+                "cell %d exceeded a per-cell capacity (flags 0x%x: 4 planes (%d), 8 vertices (%d), 16 vertices per "
+                "cut (%d), 32 faces (%d), 64 search rings (%d))",
                 s.bad_cell, s.flags, PMAX, TMAX, NSTAGE, MAXF, MAXRING);
 }
 
@@ -162,9 +217,12 @@ static void fill_mesh(const mm_ctx *c, mm_mesh *out)
     const MeshDev &m = c->mesh;
     out->n = m.n;
     out->nfaces = m.nf;
-    out->nincident = c->cnt_host[1];
+    out->nincident = c->mesh_ninc;
     out->face_stride = m.fs;
-    for (int d = 0; d < 3; ++d) out->box[d] = m.box[d];
+    out->nboxes = c->nbox;
+    for (int d = 0; d < 3; ++d) out->box[d] = c->boxL_host[d];
+    out->cell_box = m.cbox;
+    out->box_size = m.boxL;
     out->face_i = m.face_i;
     out->face_j = m.face_j;
     out->face_shift = m.face_shift;
@@ -183,7 +241,9 @@ static MeshDev mesh_from(const mm_mesh *mm)
     m.n = mm->n;
     m.nf = mm->nfaces;
     m.fs = mm->face_stride;
-    for (int d = 0; d < 3; ++d) m.box[d] = mm->box[d];
+    m.nf_dev = nullptr;
+    m.cbox = mm->cell_box;
+    m.boxL = mm->box_size;
     m.face_i = mm->face_i;
     m.face_j = mm->face_j;
     m.face_shift = mm->face_shift;
@@ -195,6 +255,286 @@ static MeshDev mesh_from(const mm_mesh *mm)
     m.inc_off = mm->inc_off;
     m.inc_face = mm->inc_face;
     return m;
+}
+
+// Per-box tables: bins about one generator wide, bin ranges, face thresholds;
+// uploaded through pinned staging, plus the cell -> box map.
+static mm_status setup_boxes(mm_ctx *c, int64_t n, const int64_t *box_off, const double *boxL, int B)
+{
+    if (B < 1) return fail(c, MM_EINVAL, "need at least one box");
+    if (n < 1 || n > MM_MAX_CELLS) return fail(c, MM_EINVAL, "n = %lld outside [1, %lld]", (long long)n, MM_MAX_CELLS);
+    if (box_off[0] != 0 || box_off[B] != n) return fail(c, MM_EINVAL, "box offsets must run from 0 to n");
+    if (B > c->nbox_cap) {
+        CK(cudaStreamSynchronize(c->stream));
+        if (c->boxes_host) cudaFreeHost(c->boxes_host);
+        if (c->boxL_host) cudaFreeHost(c->boxL_host);
+        if (c->box_off_host) cudaFreeHost(c->box_off_host);
+        c->boxes_host = nullptr;
+        c->boxL_host = nullptr;
+        c->box_off_host = nullptr;
+        c->nbox_cap = 0;
+        CK(cudaMallocHost(&c->boxes_host, sizeof(BoxDev) * B));
+        CK(cudaMallocHost(&c->boxL_host, sizeof(double) * 3 * B));
+        CK(cudaMallocHost(&c->box_off_host, sizeof(long long) * (B + 1)));
+        c->nbox_cap = B;
+    } else {
+        CK(cudaStreamSynchronize(c->stream));  // the staging may still feed an earlier copy
+    }
+    int64_t nbins = 0;
+    for (int b = 0; b < B; ++b) {
+        const int64_t nb = box_off[b + 1] - box_off[b];
+        if (nb < 1) return fail(c, MM_EINVAL, "box %d holds no generator", b);
+        const double *L = boxL + 3 * b;
+        for (int d = 0; d < 3; ++d)
+            if (!(L[d] > 0.0) || !std::isfinite(L[d])) return fail(c, MM_EINVAL, "box %d size must be finite and > 0", b);
+        BoxDev &g = c->boxes_host[b];
+        const double vcell = L[0] * L[1] * L[2] / (double)nb;
+        const double spacing = std::cbrt(vcell);
+        int64_t nbb = 1;
+        for (int d = 0; d < 3; ++d) {
+            int64_t gd = (int64_t)std::floor(L[d] / spacing);
+            if (gd < 1) gd = 1;
+            if (gd > 4096) gd = 4096;
+            g.g[d] = (int)gd;
+            g.bs[d] = L[d] / (double)gd;
+            g.L[d] = L[d];
+            c->boxL_host[3 * b + d] = L[d];
+            nbb *= gd;
+        }
+        g.bin_off = (int)nbins;
+        g.amin = c->cfg.area_rel * std::pow(vcell, 2.0 / 3.0);
+        nbins += nbb;
+        if (nbins > ((int64_t)1 << 30)) return fail(c, MM_EINVAL, "too many bins");
+    }
+    for (int b = 0; b <= B; ++b) c->box_off_host[b] = (long long)box_off[b];
+    mm_status r;
+    if ((r = ensure(c, c->boxes_dev, sizeof(BoxDev) * B)) || (r = ensure(c, c->boxL_dev, sizeof(double) * 3 * B)) ||
+        (r = ensure(c, c->box_off_dev, sizeof(long long) * (B + 1))) || (r = ensure(c, c->cbox, sizeof(int) * n)))
+        return r;
+    cudaStream_t s = c->stream;
+    CK(cudaMemcpyAsync(c->boxes_dev.p, c->boxes_host, sizeof(BoxDev) * B, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->boxL_dev.p, c->boxL_host, sizeof(double) * 3 * B, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->box_off_dev.p, c->box_off_host, sizeof(long long) * (B + 1), cudaMemcpyHostToDevice, s));
+    if (B == 1) {
+        CK(cudaMemsetAsync(c->cbox.p, 0, sizeof(int) * n, s));
+    } else {
+        launch_fill_cbox(P<long long>(c->box_off_dev), B, n, P<int>(c->cbox), s);
+        CKLAUNCH();
+        c->launches += 1;
+    }
+    c->nbox = B;
+    c->nbins = nbins;
+    c->tess_n = n;
+    c->tables_gen++;
+    return MM_OK;
+}
+
+// Face arrays at capacity: exact (with headroom) after a counted pass, or
+// fixed upfront in graph mode.
+static mm_status ensure_faces(mm_ctx *c, int64_t nf, int64_t ni)
+{
+    mm_status r;
+    if (nf > c->fcap) {
+        const int64_t cap = nf + nf / 8 + 64;
+        if ((r = ensure(c, c->face_i, cap * sizeof(int))) || (r = ensure(c, c->face_j, cap * sizeof(int))) ||
+            (r = ensure(c, c->face_shift, cap * sizeof(int))) || (r = ensure(c, c->face_area, cap * sizeof(double))) ||
+            (r = ensure(c, c->face_normal, 3 * cap * sizeof(double))) ||
+            (r = ensure(c, c->face_cen, 3 * cap * sizeof(double))))
+            return r;
+        c->fcap = cap;
+    }
+    if (ni > c->icap) {
+        const int64_t cap = ni + ni / 8 + 64;
+        if ((r = ensure(c, c->inc_face, cap * sizeof(int)))) return r;
+        c->icap = cap;
+    }
+    return MM_OK;
+}
+
+static mm_status ensure_tess_buffers(mm_ctx *c, int64_t n)
+{
+    mm_status r;
+    const int64_t nbins = c->nbins;
+    const int64_t ns = n * (int64_t)MAXF;
+    const size_t scan_n = (size_t)((nbins > n ? nbins : n) + 1);
+    if ((r = ensure(c, c->bin_of, n * sizeof(int))) || (r = ensure(c, c->bin_count, (nbins + 1) * sizeof(int))) ||
+        (r = ensure(c, c->bin_start, (nbins + 1) * sizeof(int))) || (r = ensure(c, c->bin_cursor, nbins * sizeof(int))) ||
+        (r = ensure(c, c->sorted, n * sizeof(double4_32a))) ||
+        (r = ensure(c, c->scan_tmp, scan_tmp_size(scan_n) * sizeof(int))) || (r = ensure(c, c->vol, n * sizeof(double))) ||
+        (r = ensure(c, c->cen, 3 * n * sizeof(double))) || (r = ensure(c, c->s_cnt, n * sizeof(int))) ||
+        (r = ensure(c, c->s_nb, ns * sizeof(int))) || (r = ensure(c, c->s_sh, ns)) ||
+        (r = ensure(c, c->s_area, ns * sizeof(double))) || (r = ensure(c, c->s_fc, 3 * ns * sizeof(double))) ||
+        (r = ensure(c, c->emit_mask, n * 8)) || (r = ensure(c, c->conf_mask, n * 8)) || (r = ensure(c, c->partner, ns)) ||
+        (r = ensure(c, c->emit_cnt, n * sizeof(int))) || (r = ensure(c, c->conf_cnt, n * sizeof(int))) ||
+        (r = ensure(c, c->face_off, (n + 1) * sizeof(int))) || (r = ensure(c, c->inc_off, (n + 1) * sizeof(int))))
+        return r;
+    return MM_OK;
+}
+
+// Enqueue the tessellation of the boxes set up last.  fixed: the face arrays
+// already have their capacities and the face count stays on the device.
+static mm_status tess_enqueue(mm_ctx *c, const double *pos, bool fixed)
+{
+    const int64_t n = c->tess_n, nbins = c->nbins;
+    cudaStream_t s = c->stream;
+    mm_status r;
+    stage_mark(c, MM_STAGE_BIN, true);
+    CK(cudaMemsetAsync(c->st, 0, sizeof(DevStatus), s));
+    CK(cudaMemsetAsync(c->bin_count.p, 0, (nbins + 1) * sizeof(int), s));
+    CK(cudaMemsetAsync(c->bin_cursor.p, 0, nbins * sizeof(int), s));
+    const BoxDev *boxes = P<BoxDev>(c->boxes_dev);
+    const int *cbox = P<int>(c->cbox);
+    launch_bin_count(pos, n, boxes, cbox, P<int>(c->bin_of), P<int>(c->bin_count), c->st, s);
+    launch_scan(P<int>(c->bin_count), P<int>(c->bin_start), nbins, P<int>(c->scan_tmp), s);
+    launch_bin_scatter(pos, n, P<int>(c->bin_of), P<int>(c->bin_start), P<int>(c->bin_cursor), P<double4_32a>(c->sorted), s);
+    launch_bin_sort(P<int>(c->bin_start), nbins, P<double4_32a>(c->sorted), s);
+    CKLAUNCH();
+    stage_mark(c, MM_STAGE_BIN, false);
+    c->launches += 6;
+
+    Slots sl{P<int>(c->s_cnt), P<int>(c->s_nb), P<unsigned char>(c->s_sh), P<double>(c->s_area), P<double>(c->s_fc)};
+    stage_mark(c, MM_STAGE_CLIP, true);
+    launch_clip(P<double4_32a>(c->sorted), P<int>(c->bin_start), n, boxes, cbox, c->cfg.precision, c->cfg.collect_stats,
+                P<double>(c->vol), P<double>(c->cen), sl, c->st, s);
+    CKLAUNCH();
+    stage_mark(c, MM_STAGE_CLIP, false);
+    c->launches += 1;
+    stage_mark(c, MM_STAGE_FACES, true);
+    launch_face_confirm(n, sl, P<unsigned long long>(c->emit_mask), P<unsigned long long>(c->conf_mask),
+                        P<signed char>(c->partner), P<int>(c->emit_cnt), P<int>(c->conf_cnt), s);
+    launch_scan(P<int>(c->emit_cnt), P<int>(c->face_off), n, P<int>(c->scan_tmp), s);
+    launch_scan(P<int>(c->conf_cnt), P<int>(c->inc_off), n, P<int>(c->scan_tmp), s);
+    CKLAUNCH();
+    c->launches += 7;
+    int64_t nf = 0, ni = 0;
+    if (!fixed) {
+        stage_mark(c, MM_STAGE_FACES, false);
+        CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&c->cnt_host[0], P<int>(c->face_off) + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&c->cnt_host[1], P<int>(c->inc_off) + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if ((r = read_status(c))) return r;
+        nf = c->cnt_host[0];
+        ni = c->cnt_host[1];
+        if ((r = ensure_faces(c, nf, ni))) return r;
+        stage_mark(c, MM_STAGE_FACES, true);
+    }
+    launch_face_write(n, pos, boxes, cbox, sl, P<unsigned long long>(c->emit_mask), P<unsigned long long>(c->conf_mask),
+                      P<signed char>(c->partner), P<int>(c->face_off), P<int>(c->inc_off), P<int>(c->face_i),
+                      P<int>(c->face_j), P<int>(c->face_shift), P<double>(c->face_area), P<double>(c->face_normal),
+                      P<double>(c->face_cen), c->fcap, P<int>(c->inc_face), c->icap, c->st, s);
+    CKLAUNCH();
+    stage_mark(c, MM_STAGE_FACES, false);
+    c->launches += 1;
+
+    MeshDev &m = c->mesh;
+    m.n = n;
+    m.nf = fixed ? 0 : nf;
+    m.fs = c->fcap;
+    m.nf_dev = fixed ? P<int>(c->face_off) + n : nullptr;
+    m.cbox = cbox;
+    m.boxL = P<double>(c->boxL_dev);
+    m.face_i = P<int>(c->face_i);
+    m.face_j = P<int>(c->face_j);
+    m.face_shift = P<int>(c->face_shift);
+    m.area = P<double>(c->face_area);
+    m.normal = P<double>(c->face_normal);
+    m.fcen = P<double>(c->face_cen);
+    m.vol = P<double>(c->vol);
+    m.cen = P<double>(c->cen);
+    m.inc_off = P<int>(c->inc_off);
+    m.inc_face = P<int>(c->inc_face);
+    c->mesh_ninc = fixed ? 0 : ni;
+    c->have_mesh = true;
+    return MM_OK;
+}
+
+// Hydro workspace for a mesh with n cells and face capacity fs.
+static mm_status ensure_hydro(mm_ctx *c, int64_t n, int64_t fs)
+{
+    mm_status r;
+    const int64_t F = fs > 0 ? fs : 1;
+    if (c->cfg.precision == 1) {
+        if ((r = ensure(c, c->x_fij, F * sizeof(int2))) || (r = ensure(c, c->x_fa, F * sizeof(float4))) ||
+            (r = ensure(c, c->x_fq, F * sizeof(float4))) || (r = ensure(c, c->x_ff, F * sizeof(float2))) ||
+            (r = ensure(c, c->x_flux, 2 * F * sizeof(float4))) || (r = ensure(c, c->x_cw, 2 * n * sizeof(float4))) ||
+            (r = ensure(c, c->x_ch, 2 * n * sizeof(float4))) || (r = ensure(c, c->x_grad, 4 * n * sizeof(float4))) ||
+            (r = ensure(c, c->x_wv, n * sizeof(float4))))
+            return r;
+    } else {
+        if ((r = ensure(c, c->Wh, 5 * n * sizeof(double))) || (r = ensure(c, c->grad, 15 * n * sizeof(double))) ||
+            (r = ensure(c, c->flux, 5 * F * sizeof(double))))
+            return r;
+    }
+    return MM_OK;
+}
+
+// The hydro stages on mesh m (workspace already ensured).
+static mm_status hydro_enqueue(mm_ctx *c, const MeshDev &m, const double *pos, const double *w, const double *dt,
+                               double *U)
+{
+    HydroCfg h = hydro_cfg(c->cfg);
+    cudaStream_t s = c->stream;
+    if (c->cfg.precision == 1) {
+        Mixed x{P<int2>(c->x_fij), P<float4>(c->x_fa), P<float4>(c->x_fq), P<float2>(c->x_ff), P<float4>(c->x_cw),
+                P<float4>(c->x_ch), P<float4>(c->x_grad), P<float4>(c->x_wv), P<float4>(c->x_flux)};
+        launch_mixed_step(m, h, pos, w, dt, x, U, s, stage_mark_cb, c);
+        CKLAUNCH();
+        c->launches += 6;
+        return MM_OK;
+    }
+    stage_mark(c, MM_STAGE_GRADIENT_HALF, true);
+    launch_gradient(m, h, U, true, nullptr, P<double>(c->Wh), dt, s);
+    stage_mark(c, MM_STAGE_GRADIENT_HALF, false);
+    stage_mark(c, MM_STAGE_GRADIENT, true);
+    launch_gradient(m, h, P<double>(c->Wh), false, P<double>(c->grad), nullptr, nullptr, s);
+    stage_mark(c, MM_STAGE_GRADIENT, false);
+    stage_mark(c, MM_STAGE_FACE_FLUX, true);
+    launch_face_flux(m, h, pos, w, P<double>(c->Wh), P<double>(c->grad), P<double>(c->flux), s);
+    stage_mark(c, MM_STAGE_FACE_FLUX, false);
+    stage_mark(c, MM_STAGE_UPDATE, true);
+    launch_update(m, h, P<double>(c->flux), dt, U, s);
+    stage_mark(c, MM_STAGE_UPDATE, false);
+    CKLAUNCH();
+    c->launches += 4;
+    return MM_OK;
+}
+
+// Mesh velocity + per-box CFL timestep (or a copy of the fixed dt), the flux
+// step and the drift, on the mesh of the last tessellation.
+static mm_status step_rest(mm_ctx *c, double *pos, double *U, const double *dt_fixed, double *w, double *dt)
+{
+    const MeshDev m = c->mesh;
+    HydroCfg h = hydro_cfg(c->cfg);
+    cudaStream_t s = c->stream;
+    mm_status r;
+    stage_mark(c, MM_STAGE_MESH_VELOCITY, true);
+    if (dt_fixed) {
+        launch_mesh_velocity(m, h, pos, U, w, nullptr, s);
+        CK(cudaMemcpyAsync(dt, dt_fixed, sizeof(double) * c->nbox, cudaMemcpyDeviceToDevice, s));
+        c->launches += 1;
+    } else {
+        launch_dt_init(dt, c->nbox, s);
+        launch_mesh_velocity(m, h, pos, U, w, dt, s);
+        c->launches += 2;
+    }
+    stage_mark(c, MM_STAGE_MESH_VELOCITY, false);
+    CKLAUNCH();
+    if ((r = hydro_enqueue(c, m, pos, w, dt, U))) return r;
+    stage_mark(c, MM_STAGE_DRIFT, true);
+    launch_drift(pos, m.n, w, dt, m.cbox, m.boxL, s);
+    stage_mark(c, MM_STAGE_DRIFT, false);
+    CKLAUNCH();
+    c->launches += 1;
+    return MM_OK;
+}
+
+static void drop_graph(mm_ctx *c)
+{
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->gexec = nullptr;
+    c->graph = nullptr;
 }
 
 extern "C" {
@@ -233,6 +573,7 @@ mm_status mm_create(mm_ctx **out, const mm_config *cfg, void *cuda_stream)
     cudaError_t e = cudaMalloc(&c->st, sizeof(DevStatus));
     if (e == cudaSuccess) e = cudaMallocHost(&c->st_host, sizeof(DevStatus));
     if (e == cudaSuccess) e = cudaMallocHost(&c->cnt_host, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->box3_host, 3 * sizeof(double));
     if (e != cudaSuccess) {
         mm_destroy(c);
         return e == cudaErrorMemoryAllocation ? MM_ENOMEM : MM_ECUDA;
@@ -244,17 +585,25 @@ mm_status mm_create(mm_ctx **out, const mm_config *cfg, void *cuda_stream)
 void mm_destroy(mm_ctx *c)
 {
     if (!c) return;
-    Buf *bufs[] = {&c->bin_of, &c->bin_count, &c->bin_start, &c->bin_cursor, &c->sorted, &c->scan_tmp,
-                   &c->vol, &c->cen, &c->s_cnt, &c->s_nb, &c->s_sh, &c->s_area, &c->s_fc, &c->emit_mask,
-                   &c->conf_mask, &c->partner, &c->emit_cnt, &c->conf_cnt, &c->face_off, &c->inc_off,
-                   &c->face_i, &c->face_j, &c->face_shift, &c->face_area, &c->face_normal, &c->face_cen,
-                   &c->inc_face, &c->Wh, &c->grad, &c->flux, &c->w_int, &c->dt_int, &c->tot_partial};
+    cudaStreamSynchronize(c->stream);
+    drop_graph(c);
+    Buf *bufs[] = {&c->boxes_dev, &c->boxL_dev, &c->box_off_dev, &c->cbox, &c->bin_of, &c->bin_count, &c->bin_start,
+                   &c->bin_cursor, &c->sorted, &c->scan_tmp, &c->vol, &c->cen, &c->s_cnt, &c->s_nb, &c->s_sh,
+                   &c->s_area, &c->s_fc, &c->emit_mask, &c->conf_mask, &c->partner, &c->emit_cnt, &c->conf_cnt,
+                   &c->face_off, &c->inc_off, &c->face_i, &c->face_j, &c->face_shift, &c->face_area,
+                   &c->face_normal, &c->face_cen, &c->inc_face, &c->Wh, &c->grad, &c->flux, &c->w_int, &c->dt_int,
+                   &c->tot_partial, &c->drift_box, &c->drift_cbox, &c->x_fij, &c->x_fa, &c->x_fq, &c->x_ff,
+                   &c->x_cw, &c->x_ch, &c->x_grad, &c->x_wv, &c->x_flux};
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     if (c->st) cudaFree(c->st);
     if (c->st_host) cudaFreeHost(c->st_host);
     if (c->cnt_host) cudaFreeHost(c->cnt_host);
+    if (c->box3_host) cudaFreeHost(c->box3_host);
+    if (c->boxes_host) cudaFreeHost(c->boxes_host);
+    if (c->boxL_host) cudaFreeHost(c->boxL_host);
+    if (c->box_off_host) cudaFreeHost(c->box_off_host);
     delete c;
 }
 
@@ -273,115 +622,10 @@ mm_status mm_tessellate(mm_ctx *c, const double *pos, int64_t n, const double bo
     if (!c) return MM_EINVAL;
     c->have_mesh = false;
     if (!pos || !box) return fail(c, MM_EINVAL, "null pointer argument");
-    if (n < 1 || n > MM_MAX_CELLS) return fail(c, MM_EINVAL, "n = %lld outside [1, %lld]", (long long)n, MM_MAX_CELLS);
-    for (int d = 0; d < 3; ++d)
-        if (!(box[d] > 0.0) || !std::isfinite(box[d])) return fail(c, MM_EINVAL, "box[%d] must be finite and > 0", d);
-    cudaStream_t s = c->stream;
-
-    // grid of bins about one generator wide
-    Grid g{};
-    const double spacing = std::cbrt(box[0] * box[1] * box[2] / (double)n);
-    int64_t nbins = 1;
-    for (int d = 0; d < 3; ++d) {
-        int64_t gd = (int64_t)std::floor(box[d] / spacing);
-        if (gd < 1) gd = 1;
-        if (gd > 4096) gd = 4096;
-        g.g[d] = (int)gd;
-        g.bs[d] = box[d] / (double)gd;
-        g.box[d] = box[d];
-        nbins *= gd;
-    }
-    if (nbins > (int64_t)1 << 30) return fail(c, MM_EINVAL, "too many bins");
-    c->grid = g;
+    const int64_t off[2] = {0, n};
     mm_status r;
-    const int64_t ns = n * (int64_t)MAXF;
-    const size_t scan_n = (size_t)((nbins > n ? nbins : n) + 1);
-    if ((r = ensure(c, c->bin_of, n * sizeof(int))) || (r = ensure(c, c->bin_count, (nbins + 1) * sizeof(int))) ||
-        (r = ensure(c, c->bin_start, (nbins + 1) * sizeof(int))) || (r = ensure(c, c->bin_cursor, nbins * sizeof(int))) ||
-        (r = ensure(c, c->sorted, n * sizeof(double4_32a))) || (r = ensure(c, c->scan_tmp, scan_tmp_size(scan_n) * sizeof(int))) ||
-        (r = ensure(c, c->vol, n * sizeof(double))) || (r = ensure(c, c->cen, 3 * n * sizeof(double))) ||
-        (r = ensure(c, c->s_cnt, n * sizeof(int))) || (r = ensure(c, c->s_nb, ns * sizeof(int))) ||
-        (r = ensure(c, c->s_sh, ns)) || (r = ensure(c, c->s_area, ns * sizeof(double))) ||
-        (r = ensure(c, c->s_fc, 3 * ns * sizeof(double))) || (r = ensure(c, c->emit_mask, n * 8)) ||
-        (r = ensure(c, c->conf_mask, n * 8)) || (r = ensure(c, c->partner, ns)) ||
-        (r = ensure(c, c->emit_cnt, n * sizeof(int))) || (r = ensure(c, c->conf_cnt, n * sizeof(int))) ||
-        (r = ensure(c, c->face_off, (n + 1) * sizeof(int))) || (r = ensure(c, c->inc_off, (n + 1) * sizeof(int))))
+    if ((r = setup_boxes(c, n, off, box, 1)) || (r = ensure_tess_buffers(c, n)) || (r = tess_enqueue(c, pos, false)))
         return r;
-
-    stage_mark(c, MM_STAGE_BIN, true);
-    CK(cudaMemsetAsync(c->st, 0, sizeof(DevStatus), s));
-    CK(cudaMemsetAsync(c->bin_count.p, 0, (nbins + 1) * sizeof(int), s));
-    CK(cudaMemsetAsync(c->bin_cursor.p, 0, nbins * sizeof(int), s));
-    launch_bin_count(pos, n, g, P<int>(c->bin_of), P<int>(c->bin_count), c->st, s);
-    launch_scan(P<int>(c->bin_count), P<int>(c->bin_start), nbins, P<int>(c->scan_tmp), s);
-    launch_bin_scatter(pos, n, P<int>(c->bin_of), P<int>(c->bin_start), P<int>(c->bin_cursor), P<double4_32a>(c->sorted), s);
-    launch_bin_sort(P<int>(c->bin_start), nbins, P<double4_32a>(c->sorted), s);
-    CKLAUNCH();
-    stage_mark(c, MM_STAGE_BIN, false);
-    c->launches += 6;
-
-    Slots sl{P<int>(c->s_cnt), P<int>(c->s_nb), P<unsigned char>(c->s_sh), P<double>(c->s_area), P<double>(c->s_fc)};
-    const double amin = c->cfg.area_rel * std::pow(box[0] * box[1] * box[2] / (double)n, 2.0 / 3.0);
-    stage_mark(c, MM_STAGE_CLIP, true);
-    launch_clip(P<double4_32a>(c->sorted), P<int>(c->bin_start), n, g, amin, c->cfg.precision, c->cfg.collect_stats,
-                P<double>(c->vol),
-                P<double>(c->cen), sl, c->st, s);
-    CKLAUNCH();
-    stage_mark(c, MM_STAGE_CLIP, false);
-    c->launches += 1;
-    stage_mark(c, MM_STAGE_FACES, true);
-    launch_face_confirm(n, sl, P<unsigned long long>(c->emit_mask), P<unsigned long long>(c->conf_mask),
-                        P<signed char>(c->partner), P<int>(c->emit_cnt), P<int>(c->conf_cnt), s);
-    launch_scan(P<int>(c->emit_cnt), P<int>(c->face_off), n, P<int>(c->scan_tmp), s);
-    launch_scan(P<int>(c->conf_cnt), P<int>(c->inc_off), n, P<int>(c->scan_tmp), s);
-    CKLAUNCH();
-    stage_mark(c, MM_STAGE_FACES, false);
-    c->launches += 7;
-    CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(&c->cnt_host[0], P<int>(c->face_off) + n, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(&c->cnt_host[1], P<int>(c->inc_off) + n, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    if ((r = read_status(c))) return r;
-    const int64_t nf = c->cnt_host[0], ni = c->cnt_host[1];
-    if (nf > c->fcap) {
-        const int64_t cap = nf + nf / 8 + 64;
-        if ((r = ensure(c, c->face_i, cap * sizeof(int))) || (r = ensure(c, c->face_j, cap * sizeof(int))) ||
-            (r = ensure(c, c->face_shift, cap * sizeof(int))) || (r = ensure(c, c->face_area, cap * sizeof(double))) ||
-            (r = ensure(c, c->face_normal, 3 * cap * sizeof(double))) ||
-            (r = ensure(c, c->face_cen, 3 * cap * sizeof(double))) || (r = ensure(c, c->flux, 5 * cap * sizeof(double))))
-            return r;
-        c->fcap = cap;
-    }
-    if (ni > c->icap) {
-        const int64_t cap = ni + ni / 8 + 64;
-        if ((r = ensure(c, c->inc_face, cap * sizeof(int)))) return r;
-        c->icap = cap;
-    }
-    stage_mark(c, MM_STAGE_FACES, true);
-    launch_face_write(n, pos, g, sl, P<unsigned long long>(c->emit_mask), P<unsigned long long>(c->conf_mask),
-                      P<signed char>(c->partner), P<int>(c->face_off), P<int>(c->inc_off), P<int>(c->face_i),
-                      P<int>(c->face_j), P<int>(c->face_shift), P<double>(c->face_area), P<double>(c->face_normal),
-                      P<double>(c->face_cen), c->fcap, P<int>(c->inc_face), s);
-    CKLAUNCH();
-    stage_mark(c, MM_STAGE_FACES, false);
-    c->launches += 1;
-
-    MeshDev &m = c->mesh;
-    m.n = n;
-    m.nf = nf;
-    m.fs = c->fcap;
-    for (int d = 0; d < 3; ++d) m.box[d] = box[d];
-    m.face_i = P<int>(c->face_i);
-    m.face_j = P<int>(c->face_j);
-    m.face_shift = P<int>(c->face_shift);
-    m.area = P<double>(c->face_area);
-    m.normal = P<double>(c->face_normal);
-    m.fcen = P<double>(c->face_cen);
-    m.vol = P<double>(c->vol);
-    m.cen = P<double>(c->cen);
-    m.inc_off = P<int>(c->inc_off);
-    m.inc_face = P<int>(c->inc_face);
-    c->have_mesh = true;
     if (out) fill_mesh(c, out);
     return MM_OK;
 }
@@ -389,7 +633,8 @@ mm_status mm_tessellate(mm_ctx *c, const double *pos, int64_t n, const double bo
 static mm_status check_mesh(mm_ctx *c, const mm_mesh *mesh)
 {
     if (!mesh) return fail(c, MM_EINVAL, "mesh is NULL");
-    if (mesh->n < 1 || !mesh->cell_volume || !mesh->inc_off) return fail(c, MM_EINVAL, "mesh is not initialised");
+    if (mesh->n < 1 || !mesh->cell_volume || !mesh->inc_off || !mesh->cell_box || !mesh->box_size || mesh->nboxes < 1)
+        return fail(c, MM_EINVAL, "mesh is not initialised");
     return MM_OK;
 }
 
@@ -425,7 +670,7 @@ mm_status mm_timestep(mm_ctx *c, const mm_mesh *mesh, const double *U, const dou
     if ((r = check_mesh(c, mesh))) return r;
     if (!U || !w || !dt) return fail(c, MM_EINVAL, "null pointer argument");
     // the timestep of Sec. 4.2 measures |v - w| against the given w
-    launch_dt_init(dt, c->stream);
+    launch_dt_init(dt, (int)mesh->nboxes, c->stream);
     launch_timestep(mesh_from(mesh), hydro_cfg(c->cfg), U, w, dt, c->stream);
     CKLAUNCH();
     c->launches += 2;
@@ -440,26 +685,8 @@ mm_status mm_flux_step(mm_ctx *c, const mm_mesh *mesh, const double *pos, const 
     if ((r = check_mesh(c, mesh))) return r;
     if (!pos || !w || !dt || !U) return fail(c, MM_EINVAL, "null pointer argument");
     MeshDev m = mesh_from(mesh);
-    HydroCfg h = hydro_cfg(c->cfg);
-    if ((r = ensure(c, c->Wh, 5 * m.n * sizeof(double))) || (r = ensure(c, c->grad, 15 * m.n * sizeof(double))) ||
-        (r = ensure(c, c->flux, 5 * (m.nf > 0 ? m.nf : 1) * sizeof(double))))
-        return r;
-    cudaStream_t s = c->stream;
-    stage_mark(c, MM_STAGE_GRADIENT_HALF, true);
-    launch_gradient(m, h, U, true, nullptr, P<double>(c->Wh), dt, s);
-    stage_mark(c, MM_STAGE_GRADIENT_HALF, false);
-    stage_mark(c, MM_STAGE_GRADIENT, true);
-    launch_gradient(m, h, P<double>(c->Wh), false, P<double>(c->grad), nullptr, nullptr, s);
-    stage_mark(c, MM_STAGE_GRADIENT, false);
-    stage_mark(c, MM_STAGE_FACE_FLUX, true);
-    launch_face_flux(m, h, pos, w, P<double>(c->Wh), P<double>(c->grad), P<double>(c->flux), s);
-    stage_mark(c, MM_STAGE_FACE_FLUX, false);
-    stage_mark(c, MM_STAGE_UPDATE, true);
-    launch_update(m, h, P<double>(c->flux), dt, U, s);
-    stage_mark(c, MM_STAGE_UPDATE, false);
-    CKLAUNCH();
-    c->launches += 4;
-    return MM_OK;
+    if ((r = ensure_hydro(c, m.n, m.fs))) return r;
+    return hydro_enqueue(c, m, pos, w, dt, U);
 }
 
 mm_status mm_drift(mm_ctx *c, double *pos, int64_t n, const double *w, const double *dt, const double box[3])
@@ -467,8 +694,17 @@ mm_status mm_drift(mm_ctx *c, double *pos, int64_t n, const double *w, const dou
     if (!c) return MM_EINVAL;
     if (!pos || !w || !dt || !box) return fail(c, MM_EINVAL, "null pointer argument");
     if (n < 1 || n > MM_MAX_CELLS) return fail(c, MM_EINVAL, "bad n");
+    for (int d = 0; d < 3; ++d)
+        if (!(box[d] > 0.0) || !std::isfinite(box[d])) return fail(c, MM_EINVAL, "box[%d] must be finite and > 0", d);
+    mm_status r;
+    // one box: its own size table and an all-zero cell -> box map
+    if ((r = ensure(c, c->drift_box, 3 * sizeof(double))) || (r = ensure(c, c->drift_cbox, n * sizeof(int)))) return r;
+    CK(cudaStreamSynchronize(c->stream));  // the pinned staging may still feed an earlier copy
+    for (int d = 0; d < 3; ++d) c->box3_host[d] = box[d];
+    CK(cudaMemcpyAsync(c->drift_box.p, c->box3_host, 3 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(c->drift_cbox.p, 0, n * sizeof(int), c->stream));
     stage_mark(c, MM_STAGE_DRIFT, true);
-    launch_drift(pos, n, w, dt, box, c->stream);
+    launch_drift(pos, n, w, dt, P<int>(c->drift_cbox), P<double>(c->drift_box), c->stream);
     stage_mark(c, MM_STAGE_DRIFT, false);
     CKLAUNCH();
     c->launches += 1;
@@ -481,28 +717,106 @@ mm_status mm_step(mm_ctx *c, double *pos, double *U, int64_t n, const double box
     if (!c) return MM_EINVAL;
     if (!pos || !U) return fail(c, MM_EINVAL, "null pointer argument");
     mm_status r;
-    mm_mesh mesh;
-    if ((r = mm_tessellate(c, pos, n, box, &mesh))) return r;
-    if ((r = ensure(c, c->w_int, 3 * n * sizeof(double))) || (r = ensure(c, c->dt_int, sizeof(double)))) return r;
+    if ((r = mm_tessellate(c, pos, n, box, nullptr))) return r;
+    if ((r = ensure(c, c->w_int, 3 * n * sizeof(double))) || (r = ensure(c, c->dt_int, sizeof(double))) ||
+        (r = ensure_hydro(c, n, c->mesh.fs)))
+        return r;
     double *w = w_out ? w_out : P<double>(c->w_int);
     double *dt = dt_out ? dt_out : P<double>(c->dt_int);
-    cudaStream_t s = c->stream;
-    MeshDev m = c->mesh;
-    HydroCfg h = hydro_cfg(c->cfg);
-    stage_mark(c, MM_STAGE_MESH_VELOCITY, true);
-    if (dt_fixed) {
-        launch_mesh_velocity(m, h, pos, U, w, nullptr, s);
-        CK(cudaMemcpyAsync(dt, dt_fixed, sizeof(double), cudaMemcpyDeviceToDevice, s));
-        c->launches += 1;
-    } else {
-        launch_dt_init(dt, s);
-        launch_mesh_velocity(m, h, pos, U, w, dt, s);
-        c->launches += 2;
+    return step_rest(c, pos, U, dt_fixed, w, dt);
+}
+
+mm_status mm_step_batched(mm_ctx *c, double *pos, double *U, int64_t n, const int64_t *box_off, const double *boxes,
+                          int nbox, double *dt_out)
+{
+    if (!c) return MM_EINVAL;
+    if (!pos || !U || !box_off || !boxes) return fail(c, MM_EINVAL, "null pointer argument");
+    if (!c->stream)
+        return fail(c, MM_EINVAL, "a batched step is captured into a CUDA graph: give the context a non-default stream");
+    if (nbox < 1) return fail(c, MM_EINVAL, "need at least one box");
+    GraphKey key;
+    key.pos = pos;
+    key.U = U;
+    key.dt_out = dt_out;
+    key.n = n;
+    key.nbox = nbox;
+    key.boxes_hash = fnv1a(box_off, sizeof(int64_t) * (nbox + 1), 1469598103934665603ull);
+    key.boxes_hash = fnv1a(boxes, sizeof(double) * 3 * nbox, key.boxes_hash);
+    key.cfg = c->cfg;
+    key.tables_gen = c->gkey.tables_gen;
+    // the tables must still be the ones the graph was captured with
+    const bool same = c->gexec && c->tables_gen == c->gkey.tables_gen && key.pos == c->gkey.pos &&
+                      key.U == c->gkey.U && key.dt_out == c->gkey.dt_out &&
+                      key.n == c->gkey.n && key.nbox == c->gkey.nbox && key.boxes_hash == c->gkey.boxes_hash &&
+                      std::memcmp(&key.cfg, &c->gkey.cfg, sizeof(mm_config)) == 0;
+    if (!same) {
+        drop_graph(c);
+        mm_status r;
+        if ((r = setup_boxes(c, n, box_off, boxes, nbox)) || (r = ensure_tess_buffers(c, n))) return r;
+        // fixed capacities: Voronoi cells of points in a box have < 8 unique faces on average
+        const int64_t fcap = 10 * n + 1024, icap = 2 * fcap;
+        if ((r = ensure_faces(c, fcap, icap)) || (r = ensure_hydro(c, n, c->fcap)) ||
+            (r = ensure(c, c->w_int, 3 * n * sizeof(double))) || (r = ensure(c, c->dt_int, sizeof(double) * nbox)))
+            return r;
+        CK(cudaStreamSynchronize(c->stream));
+        const int64_t l0 = c->launches;
+        c->capturing = true;
+        cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            c->capturing = false;
+            return fail(c, MM_ECUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
+        }
+        double *dt = P<double>(c->dt_int);
+        r = tess_enqueue(c, pos, true);
+        if (r == MM_OK) r = step_rest(c, pos, U, nullptr, P<double>(c->w_int), dt);
+        if (r == MM_OK && dt_out) {
+            e = cudaMemcpyAsync(dt_out, dt, sizeof(double) * nbox, cudaMemcpyDeviceToDevice, c->stream);
+            if (e != cudaSuccess) r = fail(c, MM_ECUDA, "dt copy: %s", cudaGetErrorString(e));
+        }
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(c->stream, &g);
+        c->capturing = false;
+        if (r != MM_OK) {
+            if (g) cudaGraphDestroy(g);
+            return r;
+        }
+        if (e != cudaSuccess) return fail(c, MM_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+        c->graph = g;
+        e = cudaGraphInstantiate(&c->gexec, g, 0);
+        if (e != cudaSuccess) {
+            drop_graph(c);
+            return fail(c, MM_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+        }
+        c->gkey = key;
+        c->gkey.tables_gen = c->tables_gen;
+        c->graph_launches = c->launches - l0;
+        c->launches = l0;
     }
-    stage_mark(c, MM_STAGE_MESH_VELOCITY, false);
-    CKLAUNCH();
-    if ((r = mm_flux_step(c, &mesh, pos, w, dt, U))) return r;
-    return mm_drift(c, pos, n, w, dt, box);
+    CK(cudaGraphLaunch(c->gexec, c->stream));
+    c->launches += c->graph_launches;
+    return MM_OK;
+}
+
+mm_status mm_sync_status(mm_ctx *c)
+{
+    if (!c) return MM_EINVAL;
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(c->st_host, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost));
+    return read_status(c);
+}
+
+mm_status mm_current_mesh(mm_ctx *c, mm_mesh *out)
+{
+    if (!c || !out) return MM_EINVAL;
+    if (!c->have_mesh) return fail(c, MM_EINVAL, "no mesh yet");
+    CK(cudaStreamSynchronize(c->stream));
+    const int64_t n = c->mesh.n;
+    CK(cudaMemcpy(&c->cnt_host[0], P<int>(c->face_off) + n, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&c->cnt_host[1], P<int>(c->inc_off) + n, sizeof(int), cudaMemcpyDeviceToHost));
+    fill_mesh(c, out);
+    out->nfaces = c->cnt_host[0];
+    out->nincident = c->cnt_host[1];
+    return MM_OK;
 }
 
 mm_status mm_prims_to_charges(mm_ctx *c, const mm_mesh *mesh, const double *rho, const double *vel,

@@ -16,19 +16,42 @@ __device__ __forceinline__ int bin_coord(double x, double bs, int g)
     return c < 0 ? 0 : (c >= g ? g - 1 : c);
 }
 
-__global__ void k_bin_count(const double *__restrict__ pos, int64_t n, Grid g, int *__restrict__ bin_of,
-                            int *__restrict__ count, DevStatus *st)
+// Box of every cell from the box offsets (binary search; cells of a box are contiguous).
+__global__ void k_fill_cbox(const long long *__restrict__ box_off, int nbox, int64_t n, int *__restrict__ cbox)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
+    int lo = 0, hi = nbox - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (box_off[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    cbox[i] = lo;
+}
+
+void launch_fill_cbox(const long long *box_off, int nbox, int64_t n, int *cbox, cudaStream_t s)
+{
+    int nb = (int)((n + 255) / 256);
+    k_fill_cbox<<<nb, 256, 0, s>>>(box_off, nbox, n, cbox);
+}
+
+__global__ void k_bin_count(const double *__restrict__ pos, int64_t n, const BoxDev *__restrict__ boxes,
+                            const int *__restrict__ cbox, int *__restrict__ bin_of, int *__restrict__ count,
+                            DevStatus *st)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const BoxDev g = boxes[cbox[i]];
     double x = pos[i], y = pos[n + i], z = pos[2 * n + i];
-    bool ok = (x >= 0.0 && x < g.box[0]) && (y >= 0.0 && y < g.box[1]) && (z >= 0.0 && z < g.box[2]);
+    bool ok = (x >= 0.0 && x < g.L[0]) && (y >= 0.0 && y < g.L[1]) && (z >= 0.0 && z < g.L[2]);
     if (!ok) {
         atomicOr(&st->flags, ST_EINVAL);
         atomicExch(&st->bad_cell, (int)i);
         x = y = z = 0.0;
     }
-    int b = bin_coord(x, g.bs[0], g.g[0]) + g.g[0] * (bin_coord(y, g.bs[1], g.g[1]) + g.g[1] * bin_coord(z, g.bs[2], g.g[2]));
+    int b = g.bin_off + bin_coord(x, g.bs[0], g.g[0]) +
+            g.g[0] * (bin_coord(y, g.bs[1], g.g[1]) + g.g[1] * bin_coord(z, g.bs[2], g.g[2]));
     bin_of[i] = b;
     atomicAdd(&count[b], 1);
 }
@@ -40,7 +63,8 @@ __global__ void k_bin_scatter(const double *__restrict__ pos, int64_t n, const i
     if (i >= n) return;
     int b = bin_of[i];
     int slot = start[b] + atomicAdd(&cursor[b], 1);
-    sorted[slot] = make_double4_32a(pos[i], pos[n + i], pos[2 * n + i], (double)i);
+    // the generator index rides in .w as a bit pattern (no FP64 conversion to read it back)
+    sorted[slot] = make_double4_32a(pos[i], pos[n + i], pos[2 * n + i], __longlong_as_double((long long)i));
 }
 
 // Order each bin's generators by index, so that everything downstream (the
@@ -54,7 +78,7 @@ __global__ void k_bin_sort(const int *__restrict__ start, int64_t nbins, double4
     for (int k = lo + 1; k < hi; ++k) {
         double4_32a v = sorted[k];
         int m = k - 1;
-        while (m >= lo && sorted[m].w > v.w) {
+        while (m >= lo && __double_as_longlong(sorted[m].w) > __double_as_longlong(v.w)) {
             sorted[m + 1] = sorted[m];
             --m;
         }
@@ -68,11 +92,11 @@ void launch_bin_sort(const int *start, int64_t nbins, double4_32a *sorted, cudaS
     k_bin_sort<<<nb, 256, 0, s>>>(start, nbins, sorted);
 }
 
-void launch_bin_count(const double *pos, int64_t n, const Grid &g, int *bin_of, int *count, DevStatus *st,
-                      cudaStream_t s)
+void launch_bin_count(const double *pos, int64_t n, const BoxDev *boxes, const int *cbox, int *bin_of, int *count,
+                      DevStatus *st, cudaStream_t s)
 {
     int nb = (int)((n + 255) / 256);
-    k_bin_count<<<nb, 256, 0, s>>>(pos, n, g, bin_of, count, st);
+    k_bin_count<<<nb, 256, 0, s>>>(pos, n, boxes, cbox, bin_of, count, st);
 }
 
 void launch_bin_scatter(const double *pos, int64_t n, const int *bin_of, const int *start, int *cursor,

@@ -18,9 +18,10 @@
 //    with a warp bitonic sort, and clipped in that order.  The cell is
 //    complete once 2 r_max is inside the radius the gathered rings cover.
 //  * Geometry: a face's polygon is walked around its plane in the dual, its
-//    area and centroid come from a fan, and the cell volume and centroid
-//    from the pyramids (apex p) over the faces: V_f = A h / 3 with h = |q|/2,
-//    centroid 3/4 of the way from p to the face centroid.
+//    area and centroid come from a fan about its first vertex, and the cell
+//    volume and centroid from the pyramids (apex p)
+//    over the faces: V_f = A h / 3 with h = |q|/2, centroid 3/4 of the way
+//    from p to the face centroid.
 //
 // Precision.  GB300 issues FP64 at 1/64 of the FP32 rate, and the warp-wide
 // FP64 instruction count bounds this kernel.  PREC 0 solves every vertex in
@@ -60,6 +61,9 @@ struct ClipSmem {
     float pfx[PREC ? PMAX : 1], pfy[PREC ? PMAX : 1], pfz[PREC ? PMAX : 1], pfo[PREC ? PMAX : 1];
     float tfx[PREC ? TMAX : 1], tfy[PREC ? TMAX : 1], tfz[PREC ? TMAX : 1], terr[PREC ? TMAX : 1];
 };
+
+// floor(a / b) for b > 0 in integer arithmetic
+__device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
 __device__ __forceinline__ unsigned lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
 
@@ -206,7 +210,8 @@ __device__ __forceinline__ void update_limit(ClipSmem<PREC> &S, CellState &C, in
     long long m = 0;
     for (int t = lane; t < C.nt; t += 32) m = max(m, S.tr2[t]);
     m = warp_max_ll(m);
-    C.lim = __double_as_longlong(4.0 * __longlong_as_double(m));
+    if constexpr (PREC == 0) C.lim = __double_as_longlong(4.0 * __longlong_as_double(m));
+    else C.lim = __double_as_longlong(4.0 * (double)__int_as_float((int)m));
 }
 
 // Clip the cell by candidate k.  Warp-uniform control flow throughout.
@@ -226,10 +231,13 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
         fqn = sqrtf(2.0f * foff) * 1.0000005f;
     }
 #pragma unroll
+    for (int c = 0; c < TMAX / 32; ++c) outm[c] = 0u;
+#pragma unroll
     for (int c = 0; c < TMAX / 32; ++c) {
+        if (c >= nchunk) break;
         bool o = false;
         const int t = c * 32 + lane;
-        const bool live = c < nchunk && t < C.nt;
+        const bool live = t < C.nt;
         if constexpr (PREC == 0) {
             if (live) o = beyond64(qx, qy, qz, off, S.tx[t], S.ty[t], S.tz[t]);
         } else {
@@ -268,6 +276,7 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
     // mark the directed edges of the removed triangles
 #pragma unroll
     for (int c = 0; c < TMAX / 32; ++c) {
+        if (c >= nchunk) break;
         if ((outm[c] >> lane) & 1u) {
             unsigned v = S.tv[c * 32 + lane];
             unsigned a = v & 255u, b = (v >> 8) & 255u, cc = (v >> 16) & 255u;
@@ -282,6 +291,7 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
     unsigned long long xs = 0, ys = 0;
 #pragma unroll
     for (int c = 0; c < TMAX / 32; ++c) {
+        if (c >= nchunk) break;
         if (outm[c] == 0) continue;  // warp-uniform
         unsigned e[3];
         int cnt = 0;
@@ -372,8 +382,9 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
                 er = 1.2e-7f * (fabsf(x) + fabsf(y) + fabsf(z)) + 1e-38f;
             }
             S.tfx[t] = x; S.tfy[t] = y; S.tfz[t] = z; S.terr[t] = er;
-            const double r = (double)sqrtf(x * x + y * y + z * z) * (1.0 + 1e-6) + (double)er;
-            S.tr2[t] = __double_as_longlong(r * r);
+            // an FP32 upper bound of |v|^2, kept as the bit pattern of a positive float
+            const float r = sqrtf(x * x + y * y + z * z) * 1.000001f + er;
+            S.tr2[t] = (long long)__float_as_int(r * r * 1.000001f);
         }
     }
     __syncwarp();
@@ -400,8 +411,9 @@ __device__ void flush_batch(ClipSmem<PREC> &S, int &ncand, CellState &C, int lan
 
 template <int PREC>
 __global__ void __maxnreg__(128)
-k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, int64_t n, Grid g, double amin,
-       double *__restrict__ vol, double *__restrict__ cen, Slots sl, DevStatus *st, int collect)
+k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, int64_t n,
+       const BoxDev *__restrict__ boxes, const int *__restrict__ cbox, double *__restrict__ vol,
+       double *__restrict__ cen, Slots sl, DevStatus *st, int collect)
 {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -410,14 +422,16 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
     ClipSmem<PREC> &S = reinterpret_cast<ClipSmem<PREC> *>(dyn_smem)[wid];
     const double4_32a me = sorted[w];
     const double px = me.x, py = me.y, pz = me.z;
-    const int self = (int)me.w;
-    const double Lx = g.box[0], Ly = g.box[1], Lz = g.box[2];
+    const int self = (int)__double_as_longlong(me.w);
+    const BoxDev g = boxes[cbox[self]];
+    const double amin = g.amin;
+    const double Lx = g.L[0], Ly = g.L[1], Lz = g.L[2];
 
     // starting box: planes 0..5 = +x,-x,+y,-y,+z,-z self-image bisectors
     if (lane < 6) {
         const int d = lane >> 1;
         const double sg = (lane & 1) ? -1.0 : 1.0;
-        const double L = g.box[d];
+        const double L = g.L[d];
         S.px[lane] = d == 0 ? sg * L : 0.0;
         S.py[lane] = d == 1 ? sg * L : 0.0;
         S.pz[lane] = d == 2 ? sg * L : 0.0;
@@ -439,7 +453,8 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
         if ((sx ^ sy ^ sz) & 1) { unsigned t = b; b = c; c = t; }
         S.tv[lane] = a | (b << 8) | (c << 16);
         const double x = sx ? -0.5 * Lx : 0.5 * Lx, y = sy ? -0.5 * Ly : 0.5 * Ly, z = sz ? -0.5 * Lz : 0.5 * Lz;
-        S.tr2[lane] = r2_bits64(x, y, z);
+        if constexpr (PREC == 0) S.tr2[lane] = r2_bits64(x, y, z);
+        else S.tr2[lane] = (long long)__float_as_int((float)(x * x + y * y + z * z) * 1.000001f);
         if constexpr (PREC == 0) { S.tx[lane] = x; S.ty[lane] = y; S.tz[lane] = z; }
         else { S.tfx[lane] = (float)x; S.tfy[lane] = (float)y; S.tfz[lane] = (float)z; S.terr[lane] = 0.0f; }
     }
@@ -462,6 +477,18 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
             cb[d] = c < 0 ? 0 : (c >= g.g[d] ? g.g[d] - 1 : c);
         }
     }
+    // image offsets s L - p for s = -1, 0, +1 (selected, not recomputed, per bin)
+    const double omx = -Lx - px, o0x = -px, opx = Lx - px;
+    const double omy = -Ly - py, o0y = -py, opy = Ly - py;
+    const double omz = -Lz - pz, o0z = -pz, opz = Lz - pz;
+    // distance from p to the nearer wall of its own bin, per axis: the block of
+    // rings 0..r then covers the radius min_d (edge_d + r bs_d)
+    double edge[3];
+    {
+        const double pp[3] = {px, py, pz};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) edge[d] = fmin(pp[d] - cb[d] * g.bs[d], (cb[d] + 1) * g.bs[d] - pp[d]);
+    }
     int ncand = 0, maxcand = 0;
     int rl = 0, rh = 1;
     bool done = false;
@@ -478,20 +505,22 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
                 const int ch = max(abs(ox), max(abs(oy), abs(oz)));
                 if (ch >= rl) {
                     int bx = cb[0] + ox, by = cb[1] + oy, bz = cb[2] + oz;
-                    shx = (int)floor((double)bx / g.g[0]);
-                    shy = (int)floor((double)by / g.g[1]);
-                    shz = (int)floor((double)bz / g.g[2]);
+                    shx = floordiv(bx, g.g[0]);
+                    shy = floordiv(by, g.g[1]);
+                    shz = floordiv(bz, g.g[2]);
                     bx -= shx * g.g[0];
                     by -= shy * g.g[1];
                     bz -= shz * g.g[2];
-                    const int b = bx + g.g[0] * (by + g.g[1] * bz);
+                    const int b = g.bin_off + bx + g.g[0] * (by + g.g[1] * bz);
                     cur = start[b];
                     end = start[b + 1];
                     // images two or more boxes away never cut (positions lie in [0, L))
                     if (abs(shx) > 1 || abs(shy) > 1 || abs(shz) > 1) end = cur;
                 }
             }
-            const double offx = shx * Lx - px, offy = shy * Ly - py, offz = shz * Lz - pz;
+            const double offx = shx < 0 ? omx : (shx > 0 ? opx : o0x);
+            const double offy = shy < 0 ? omy : (shy > 0 ? opy : o0y);
+            const double offz = shz < 0 ? omz : (shz > 0 ? opz : o0z);
             const int code = (shx + 1) + 3 * (shy + 1) + 9 * (shz + 1);
             const bool selfimg = (abs(shx) + abs(shy) + abs(shz)) <= 1;
             while (__any_sync(FULL, cur < end)) {
@@ -504,7 +533,7 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
                 if (cur < end) {
                     const double4_32a P = sorted[cur];
                     ++cur;
-                    j = (int)P.w;
+                    j = (int)__double_as_longlong(P.w);
                     qx = P.x + offx; qy = P.y + offy; qz = P.z + offz;
                     d2b = __double_as_longlong(__fma_rn(qx, qx, __fma_rn(qy, qy, __dmul_rn(qz, qz))));
                     keep = !(j == self && selfimg) && d2b < C.lim;
@@ -523,15 +552,8 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
         flush_batch<PREC>(S, ncand, C, lane);
         ++rings;
         // radius the gathered rings are guaranteed to cover
-        double R = 1e300;
-        {
-            const double pp[3] = {px, py, pz};
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const double lo = (cb[d] - rh) * g.bs[d], hi = (cb[d] + rh + 1) * g.bs[d];
-                R = fmin(R, fmin(pp[d] - lo, hi - pp[d]));
-            }
-        }
+        const double rr = (double)rh;
+        const double R = fmin(fmin(fma(rr, g.bs[0], edge[0]), fma(rr, g.bs[1], edge[1])), fma(rr, g.bs[2], edge[2]));
         if (C.lim <= __double_as_longlong(R * R)) done = true;
         else {
             rl = rh + 1;
@@ -552,7 +574,7 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
         __syncwarp();
     }
     double vl = 0.0, vcx = 0.0, vcy = 0.0, vcz = 0.0;
-    unsigned fan = 0;
+    unsigned fan = 0;  // polygon edges summed (work counter)
     if (!C.err) {
         for (int p = lane; p < C.np; p += 32) {
             int t0 = -1;
@@ -566,11 +588,17 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
             }
             S.u.f.a[p] = 0.0;
             if (t0 < 0) continue;  // plane no longer bounds the cell
+            // Fan about the polygon's first vertex v0 with offsets d = v - v0
+            // formed once per vertex: edge (a, b) spans the triangle (v0, a, b)
+            // with w = q . (d_a x d_b) = 2 |q| times its signed area, so
+            // area = |sum w| / (2|q|), pyramid volume A |q| / 6 = |sum w| / 12,
+            // centroid = v0 + sum w (d_a + d_b) / (3 sum w).  Offsets from v0
+            // keep the rounding relative to the face's own size.
             const double qx = S.px[p], qy = S.py[p], qz = S.pz[p];
             const double x0 = S.tx[t0], y0 = S.ty[t0], z0 = S.tz[t0];
-            double ax = 0, ay = 0, az = 0;  // previous vertex
-            double A2 = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
-            int cnt = 1;
+            double ax = 0.0, ay = 0.0, az = 0.0;  // offset of the current vertex
+            double W = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+            int cnt = 0;
             bool ok = false;
             for (int guard = 0; guard < TMAX; ++guard) {
                 // next vertex around p: the triangle containing p -> y
@@ -584,31 +612,28 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
                     if (c == (unsigned)p && a == y) { tn = t; z = b; break; }
                 }
                 if (tn < 0) break;
-                if (tn == t0) { ok = true; break; }
-                const double bx = S.tx[tn], by = S.ty[tn], bz = S.tz[tn];
-                if (cnt >= 2) {
-                    const double ux = ax - x0, uy = ay - y0, uz = az - z0;
-                    const double vx = bx - x0, vy = by - y0, vz = bz - z0;
-                    const double w = qx * (uy * vz - uz * vy) + qy * (uz * vx - ux * vz) + qz * (ux * vy - uy * vx);
-                    A2 += w;
-                    sx += w * (x0 + ax + bx);
-                    sy += w * (y0 + ay + by);
-                    sz += w * (z0 + az + bz);
-                }
-                ax = bx; ay = by; az = bz;
                 ++cnt;
+                if (tn == t0) { ok = true; break; }
+                const double bx = S.tx[tn] - x0, by = S.ty[tn] - y0, bz = S.tz[tn] - z0;
+                const double w = qx * (ay * bz - az * by) + qy * (az * bx - ax * bz) + qz * (ax * by - ay * bx);
+                W += w;
+                sx += w * (ax + bx);
+                sy += w * (ay + by);
+                sz += w * (az + bz);
+                ax = bx; ay = by; az = bz;
                 y = z;
             }
             fan += cnt;
             if (!ok) { C.err |= ST_EDEGEN; continue; }
-            const double ql = sqrt(qx * qx + qy * qy + qz * qz);
-            const double area = 0.5 * fabs(A2) / ql;
-            const double fx = A2 != 0.0 ? sx / (3.0 * A2) : x0;
-            const double fy = A2 != 0.0 ? sy / (3.0 * A2) : y0;
-            const double fz = A2 != 0.0 ? sz / (3.0 * A2) : z0;
+            const double aw = fabs(W);
+            const double area = 0.5 * aw / sqrt(2.0 * S.po[p]);
+            const double i3w = W != 0.0 ? 1.0 / (3.0 * W) : 0.0;
+            const double fx = x0 + sx * i3w;
+            const double fy = y0 + sy * i3w;
+            const double fz = z0 + sz * i3w;
             S.u.f.a[p] = area;
             S.u.f.x[p] = fx; S.u.f.y[p] = fy; S.u.f.z[p] = fz;
-            const double vp = area * ql / 6.0;  // A h / 3 with h = |q| / 2
+            const double vp = aw * (1.0 / 12.0);
             vl += vp;
             vcx += 0.75 * vp * fx;
             vcy += 0.75 * vp * fy;
@@ -674,8 +699,9 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
 }
 
 template <int PREC>
-static void launch_clip_t(const double4_32a *sorted, const int *start, int64_t n, const Grid &g, double amin,
-                          double *vol, double *cen, Slots sl, DevStatus *st, int collect, cudaStream_t s)
+static void launch_clip_t(const double4_32a *sorted, const int *start, int64_t n, const BoxDev *boxes,
+                          const int *cbox, double *vol, double *cen, Slots sl, DevStatus *st, int collect,
+                          cudaStream_t s)
 {
     const size_t smem = sizeof(ClipSmem<PREC>) * CLIP_WARPS;
     static bool configured = false;  // the attribute is per function and process-wide
@@ -684,14 +710,14 @@ static void launch_clip_t(const double4_32a *sorted, const int *start, int64_t n
         configured = true;
     }
     const int64_t nb = (n + CLIP_WARPS - 1) / CLIP_WARPS;
-    k_clip<PREC><<<(unsigned)nb, 32 * CLIP_WARPS, smem, s>>>(sorted, start, n, g, amin, vol, cen, sl, st, collect);
+    k_clip<PREC><<<(unsigned)nb, 32 * CLIP_WARPS, smem, s>>>(sorted, start, n, boxes, cbox, vol, cen, sl, st, collect);
 }
 
-void launch_clip(const double4_32a *sorted, const int *start, int64_t n, const Grid &g, double amin, int precision,
-                 int collect, double *vol, double *cen, Slots sl, DevStatus *st, cudaStream_t s)
+void launch_clip(const double4_32a *sorted, const int *start, int64_t n, const BoxDev *boxes, const int *cbox,
+                 int precision, int collect, double *vol, double *cen, Slots sl, DevStatus *st, cudaStream_t s)
 {
-    if (precision == 0) launch_clip_t<0>(sorted, start, n, g, amin, vol, cen, sl, st, collect, s);
-    else launch_clip_t<1>(sorted, start, n, g, amin, vol, cen, sl, st, collect, s);
+    if (precision == 0) launch_clip_t<0>(sorted, start, n, boxes, cbox, vol, cen, sl, st, collect, s);
+    else launch_clip_t<1>(sorted, start, n, boxes, cbox, vol, cen, sl, st, collect, s);
 }
 
 }  // namespace mm

@@ -44,17 +44,24 @@ __global__ void k_face_confirm(int64_t n, Slots sl, unsigned long long *__restri
     conf_cnt[i] = __popcll(cm);
 }
 
-__global__ void k_face_write(int64_t n, const double *__restrict__ pos, Grid g, Slots sl,
+__global__ void k_face_write(int64_t n, const double *__restrict__ pos, const BoxDev *__restrict__ boxes,
+                             const int *__restrict__ cbox, Slots sl,
                              const unsigned long long *__restrict__ emit_mask,
                              const unsigned long long *__restrict__ conf_mask,
                              const signed char *__restrict__ partner, const int *__restrict__ face_off,
                              const int *__restrict__ inc_off, int *__restrict__ face_i, int *__restrict__ face_j,
                              int *__restrict__ face_shift, double *__restrict__ face_area,
                              double *__restrict__ face_normal, double *__restrict__ face_cen, int64_t fcap,
-                             int *__restrict__ inc_face)
+                             int *__restrict__ inc_face, int64_t icap, DevStatus *st)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const double *L = boxes[cbox[i]].L;
+    // a fixed capacity (graph mode) that is too small is reported, never overrun
+    if ((int64_t)face_off[i + 1] > fcap || (int64_t)inc_off[i + 1] > icap) {
+        atomicOr(&st->flags, ST_ECAP_MESH);
+        return;
+    }
     const unsigned long long em = emit_mask[i], cm = conf_mask[i];
     const int fbase = face_off[i];
     int e = inc_off[i];
@@ -70,9 +77,9 @@ __global__ void k_face_write(int64_t n, const double *__restrict__ pos, Grid g, 
             const int f = fbase + __popcll(em & ((1ull << k) - 1ull));
             if (f < fcap) {
                 const int sx = code % 3 - 1, sy = (code / 3) % 3 - 1, sz = code / 9 - 1;
-                const double qx = pos[j] + sx * g.box[0] - pos[i];
-                const double qy = pos[n + j] + sy * g.box[1] - pos[n + i];
-                const double qz = pos[2 * n + j] + sz * g.box[2] - pos[2 * n + i];
+                const double qx = pos[j] + sx * L[0] - pos[i];
+                const double qy = pos[n + j] + sy * L[1] - pos[n + i];
+                const double qz = pos[2 * n + j] + sz * L[2] - pos[2 * n + i];
                 const double inv = 1.0 / sqrt(qx * qx + qy * qy + qz * qz);
                 face_i[f] = (int)i;
                 face_j[f] = j;
@@ -102,14 +109,16 @@ void launch_face_confirm(int64_t n, Slots sl, unsigned long long *emit_mask, uns
     k_face_confirm<<<nb, 128, 0, s>>>(n, sl, emit_mask, conf_mask, partner, emit_cnt, conf_cnt);
 }
 
-void launch_face_write(int64_t n, const double *pos, const Grid &g, Slots sl, const unsigned long long *emit_mask,
-                       const unsigned long long *conf_mask, const signed char *partner, const int *face_off,
-                       const int *inc_off, int *face_i, int *face_j, int *face_shift, double *face_area,
-                       double *face_normal, double *face_cen, int64_t fcap, int *inc_face, cudaStream_t s)
+void launch_face_write(int64_t n, const double *pos, const BoxDev *boxes, const int *cbox, Slots sl,
+                       const unsigned long long *emit_mask, const unsigned long long *conf_mask,
+                       const signed char *partner, const int *face_off, const int *inc_off, int *face_i,
+                       int *face_j, int *face_shift, double *face_area, double *face_normal, double *face_cen,
+                       int64_t fcap, int *inc_face, int64_t icap, DevStatus *st, cudaStream_t s)
 {
     int nb = (int)((n + 127) / 128);
-    k_face_write<<<nb, 128, 0, s>>>(n, pos, g, sl, emit_mask, conf_mask, partner, face_off, inc_off, face_i,
-                                    face_j, face_shift, face_area, face_normal, face_cen, fcap, inc_face);
+    k_face_write<<<nb, 128, 0, s>>>(n, pos, boxes, cbox, sl, emit_mask, conf_mask, partner, face_off, inc_off,
+                                    face_i, face_j, face_shift, face_area, face_normal, face_cen, fcap, inc_face,
+                                    icap, st);
 }
 
 }  // namespace mm

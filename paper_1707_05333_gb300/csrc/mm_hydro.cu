@@ -3,14 +3,11 @@
 // lists (gradients, update) or face-centric over unique faces (fluxes); no
 // atomics touch the conserved data, so results are bitwise reproducible.
 #include "mm_internal.cuh"
+#include "mm_riemann.cuh"
 
 namespace mm {
 
 constexpr unsigned FULL_MASK_HYDRO = 0xffffffffu;
-
-struct Box3 {
-    double L[3];
-};
 
 __device__ __forceinline__ void decode_shift(int code, double &sx, double &sy, double &sz)
 {
@@ -27,7 +24,7 @@ struct Nbr {
     double ox, oy, oz;
 };
 
-__device__ __forceinline__ Nbr neighbour(const MeshDev &m, int e)
+__device__ __forceinline__ Nbr neighbour(const MeshDev &m, int e, const double *L)
 {
     Nbr r;
     int f = m.inc_face[e];
@@ -38,9 +35,9 @@ __device__ __forceinline__ Nbr neighbour(const MeshDev &m, int e)
     r.sg = fwd ? 1.0 : -1.0;
     double sx, sy, sz;
     decode_shift(m.face_shift[f], sx, sy, sz);
-    r.ox = r.sg * sx * m.box[0];
-    r.oy = r.sg * sy * m.box[1];
-    r.oz = r.sg * sz * m.box[2];
+    r.ox = r.sg * sx * L[0];
+    r.oy = r.sg * sy * L[1];
+    r.oz = r.sg * sz * L[2];
     return r;
 }
 
@@ -50,24 +47,9 @@ __device__ __forceinline__ void load5(const double *S, int64_t n, int64_t i, dou
     for (int k = 0; k < 5; ++k) w[k] = S[k * n + i] * inv_v;
 }
 
-// Floors on density and specific internal energy (Sec. 4.1).  A state below
-// the density floor is reset to the floor density at rest with the floor
-// internal energy; otherwise only the internal energy is raised if needed.
-// Returns true if the state changed (an untouched state is left bit for bit).
 __device__ __forceinline__ bool apply_floor(double W[5], double rho_floor, double eps_floor)
 {
-    if (!(W[0] >= rho_floor)) {
-        W[0] = rho_floor;
-        W[1] = W[2] = W[3] = 0.0;
-        W[4] = rho_floor * eps_floor;
-        return true;
-    }
-    const double ke = 0.5 * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]) / W[0];
-    if (!(W[4] - ke >= W[0] * eps_floor)) {
-        W[4] = W[0] * eps_floor + ke;
-        return true;
-    }
-    return false;
+    return apply_floor_t<double>(W, rho_floor, eps_floor);
 }
 
 // ---------------------------------------------------------------------------
@@ -86,6 +68,7 @@ __global__ void __launch_bounds__(128) k_gradient(MeshDev m, HydroCfg c, const d
     load5(S, n, i, ivi, Wi);
     const double cix = m.cen[i], ciy = m.cen[n + i], ciz = m.cen[2 * n + i];
     const int e0 = m.inc_off[i], e1 = m.inc_off[i + 1];
+    const double *L = m.boxL + 3 * m.cbox[i];
 
     // M = 1/2 sum A n (x) d,  b_k = 1/2 sum A (W_o - W_i)_k n
     double M[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -96,7 +79,7 @@ __global__ void __launch_bounds__(128) k_gradient(MeshDev m, HydroCfg c, const d
 #pragma unroll
     for (int k = 0; k < 15; ++k) b[k] = 0.0;
     for (int e = e0; e < e1; ++e) {
-        const Nbr q = neighbour(m, e);
+        const Nbr q = neighbour(m, e, L);
         const double ha = 0.5 * m.area[q.f];
         const double nx = q.sg * m.normal[q.f], ny = q.sg * m.normal[m.fs + q.f], nz = q.sg * m.normal[2 * m.fs + q.f];
         const double dx = m.cen[q.o] + q.ox - cix, dy = m.cen[n + q.o] + q.oy - ciy, dz = m.cen[2 * n + q.o] + q.oz - ciz;
@@ -139,7 +122,7 @@ __global__ void __launch_bounds__(128) k_gradient(MeshDev m, HydroCfg c, const d
 #pragma unroll
         for (int k = 0; k < 5; ++k) { dmax[k] = 0.0; dmin[k] = 0.0; rn[k] = 1.0; rd[k] = 1.0; }
         for (int e = e0; e < e1; ++e) {
-            const Nbr q = neighbour(m, e);
+            const Nbr q = neighbour(m, e, L);
             const double dx = m.cen[q.o] + q.ox - cix, dy = m.cen[n + q.o] + q.oy - ciy, dz = m.cen[2 * n + q.o] + q.oz - ciz;
             const double ivo = FROM_CHARGES ? 1.0 / m.vol[q.o] : 1.0;
 #pragma unroll
@@ -207,7 +190,7 @@ __global__ void __launch_bounds__(128) k_gradient(MeshDev m, HydroCfg c, const d
         for (int d = 0; d < 3; ++d) s += u[d] * (g[12 + d] + dP[d]);
         rate[4] = -(s + (Wi[4] + P) * divu);
     }
-    const double hdt = 0.5 * (*dtp);
+    const double hdt = 0.5 * dtp[m.cbox[i]];
 #pragma unroll
     for (int k = 0; k < 5; ++k) Wh[k * n + i] = Wi[k] + hdt * rate[k];
 }
@@ -228,64 +211,20 @@ void launch_gradient(const MeshDev &m, const HydroCfg &c, const double *S, bool 
 // ---------------------------------------------------------------------------
 // Face fluxes: reconstruct, floor, boost into the face frame, HLLC, boost back
 // ---------------------------------------------------------------------------
-struct FaceState {
-    double rho, vx, vy, vz, P;  // velocity already in the face frame
-};
-
-// HLLC in vector form along unit normal (nx,ny,nz): the tangential velocity
-// rides along with the normal mass flux, so no explicit tangent basis is
-// needed.  Davis wave speeds; contact speed from the jump conditions.
-__device__ __forceinline__ void hllc(const FaceState &L, const FaceState &R, double nx, double ny, double nz,
-                                     double gamma, double F[5])
-{
-    const double gm1 = gamma - 1.0;
-    const double ul = L.vx * nx + L.vy * ny + L.vz * nz;
-    const double ur = R.vx * nx + R.vy * ny + R.vz * nz;
-    const double cl = sqrt(gamma * L.P / L.rho), cr = sqrt(gamma * R.P / R.rho);
-    const double El = L.P / gm1 + 0.5 * L.rho * (L.vx * L.vx + L.vy * L.vy + L.vz * L.vz);
-    const double Er = R.P / gm1 + 0.5 * R.rho * (R.vx * R.vx + R.vy * R.vy + R.vz * R.vz);
-    const double sl = fmin(ul - cl, ur - cr);
-    const double sr = fmax(ul + cl, ur + cr);
-    const double ml = L.rho * (sl - ul), mr = R.rho * (sr - ur);
-    const double ss = (R.P - L.P + ul * ml - ur * mr) / (ml - mr);
-    // branch order: S_L >= 0 -> F_L; S* >= 0 -> F*_L; S_R > 0 -> F*_R; else F_R
-    const bool left = (sl >= 0.0) || (ss >= 0.0);
-    const bool star = (sl < 0.0) && (left || sr > 0.0);
-    const FaceState &K = left ? L : R;
-    const double uk = left ? ul : ur;
-    const double Ek = left ? El : Er;
-    const double sk = left ? sl : sr;
-    const double mk = K.rho * uk;
-    // physical flux of side K
-    F[0] = mk;
-    F[1] = mk * K.vx + K.P * nx;
-    F[2] = mk * K.vy + K.P * ny;
-    F[3] = mk * K.vz + K.P * nz;
-    F[4] = (Ek + K.P) * uk;
-    if (star) {
-        // U*_K = rho_K (S_K - u_K)/(S_K - S*) (1, v_K + (S* - u_K) n, E_K/rho_K + (S* - u_K)(S* + P_K/(rho_K (S_K - u_K))))
-        const double f = K.rho * (sk - uk) / (sk - ss);
-        const double du = ss - uk;
-        const double es = f * (Ek / K.rho + du * (ss + K.P / (K.rho * (sk - uk))));
-        F[0] += sk * (f - K.rho);
-        F[1] += sk * (f * (K.vx + du * nx) - K.rho * K.vx);
-        F[2] += sk * (f * (K.vy + du * ny) - K.rho * K.vy);
-        F[3] += sk * (f * (K.vz + du * nz) - K.rho * K.vz);
-        F[4] += sk * (es - Ek);
-    }
-}
+using FaceState = FaceStateT<double>;
 
 __global__ void __launch_bounds__(128) k_face_flux(MeshDev m, HydroCfg c, const double *__restrict__ pos,
                                                    const double *__restrict__ w, const double *__restrict__ Wh,
                                                    const double *__restrict__ grad, double *__restrict__ flux)
 {
     const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (f >= m.nf) return;
+    if (f >= face_count(m)) return;
     const int64_t n = m.n, fs = m.fs;
     const int i = m.face_i[f], j = m.face_j[f];
     double sx, sy, sz;
     decode_shift(m.face_shift[f], sx, sy, sz);
-    const double ox = sx * m.box[0], oy = sy * m.box[1], oz = sz * m.box[2];
+    const double *Lb = m.boxL + 3 * m.cbox[i];
+    const double ox = sx * Lb[0], oy = sy * Lb[1], oz = sz * Lb[2];
     const double fx = m.fcen[f], fy = m.fcen[fs + f], fz = m.fcen[2 * fs + f];
     const double nx = m.normal[f], ny = m.normal[fs + f], nz = m.normal[2 * fs + f];
     // reconstruction to the face centroid: W_face = W_half + (x_f - c) . grad
@@ -328,24 +267,24 @@ __global__ void __launch_bounds__(128) k_face_flux(MeshDev m, HydroCfg c, const 
         R.vx = WR[1] * ir - wfx; R.vy = WR[2] * ir - wfy; R.vz = WR[3] * ir - wfz;
     }
     double F[5];
-    hllc(L, R, nx, ny, nz, c.gamma, F);
+    hllc_t<double>(L, R, nx, ny, nz, c.gamma, F);
     // back to the lab frame: p -> p + m w, E -> E + p.w + |w|^2/2 m
     const double A = m.area[f];
     const double fm = F[0];
     const double fe = F[4] + F[1] * wfx + F[2] * wfy + F[3] * wfz + 0.5 * (wfx * wfx + wfy * wfy + wfz * wfz) * fm;
-    const int64_t nf = m.nf;
     flux[f] = A * fm;
-    flux[nf + f] = A * (F[1] + fm * wfx);
-    flux[2 * nf + f] = A * (F[2] + fm * wfy);
-    flux[3 * nf + f] = A * (F[3] + fm * wfz);
-    flux[4 * nf + f] = A * fe;
+    flux[fs + f] = A * (F[1] + fm * wfx);
+    flux[2 * fs + f] = A * (F[2] + fm * wfy);
+    flux[3 * fs + f] = A * (F[3] + fm * wfz);
+    flux[4 * fs + f] = A * fe;
 }
 
 void launch_face_flux(const MeshDev &m, const HydroCfg &c, const double *pos, const double *w, const double *Wh,
                       const double *grad, double *flux, cudaStream_t s)
 {
-    if (m.nf == 0) return;
-    int nb = (int)((m.nf + 127) / 128);
+    const int64_t nfl = face_launch_count(m);
+    if (nfl == 0) return;
+    int nb = (int)((nfl + 127) / 128);
     k_face_flux<<<nb, 128, 0, s>>>(m, c, pos, w, Wh, grad, flux);
 }
 
@@ -356,7 +295,7 @@ __global__ void __launch_bounds__(256) k_update(MeshDev m, HydroCfg c, const dou
                                                 const double *__restrict__ dtp, double *__restrict__ U)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t n = m.n, nf = m.nf;
+    const int64_t n = m.n, nf = m.fs;  // flux rows are face-capacity apart
     if (i >= n) return;
     double acc[5] = {0, 0, 0, 0, 0};
     for (int e = m.inc_off[i]; e < m.inc_off[i + 1]; ++e) {
@@ -370,7 +309,7 @@ __global__ void __launch_bounds__(256) k_update(MeshDev m, HydroCfg c, const dou
             for (int k = 0; k < 5; ++k) acc[k] -= flux[k * nf + f];
         }
     }
-    const double dt = *dtp;
+    const double dt = dtp[m.cbox[i]];
     double Un[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) Un[k] = U[k * n + i] - dt * acc[k];
@@ -395,9 +334,22 @@ void launch_update(const MeshDev &m, const HydroCfg &c, const double *flux, cons
 
 // ---------------------------------------------------------------------------
 // Mesh velocity (Sec. 4.2) fused with the per-cell CFL timestep and its
-// global minimum.  Positive doubles order like their bit patterns, so the
-// minimum is an unsigned 64-bit atomicMin: exact and order independent.
+// minimum over each box.  Positive doubles order like their bit patterns, so
+// the minimum is an unsigned 64-bit atomicMin: exact and order independent.
 // ---------------------------------------------------------------------------
+// Minimum of v over the lanes of each box: one atomic per warp when the warp
+// lies in one box (cells of a box are contiguous), one per lane otherwise.
+__device__ __forceinline__ void box_min(unsigned long long *bits, int box, double v)
+{
+    const int b0 = __shfl_sync(FULL_MASK_HYDRO, box, 0);
+    if (__all_sync(FULL_MASK_HYDRO, box == b0 || box < 0)) {
+        for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(FULL_MASK_HYDRO, v, o));
+        if ((threadIdx.x & 31) == 0 && b0 >= 0 && v > 0.0)
+            atomicMin(bits + b0, (unsigned long long)__double_as_longlong(v));
+    } else if (box >= 0 && v > 0.0) {
+        atomicMin(bits + box, (unsigned long long)__double_as_longlong(v));
+    }
+}
 __device__ __forceinline__ double sound_speed(const double W[5], double gamma)
 {
     const double ke = 0.5 * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]) / W[0];
@@ -437,16 +389,7 @@ __global__ void __launch_bounds__(256) k_mesh_velocity(MeshDev m, HydroCfg c, co
         const double rx = vx - wx, ry = vy - wy, rz = vz - wz;
         dti = c.cfl * R / (cs + sqrt(rx * rx + ry * ry + rz * rz));
     }
-    // block minimum, then one atomic per block
-    __shared__ double sm[8];
-    for (int o = 16; o > 0; o >>= 1) dti = fmin(dti, __shfl_xor_sync(FULL_MASK_HYDRO, dti, o));
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = dti;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double v = sm[0];
-        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) v = fmin(v, sm[k]);
-        if (dt_bits && v > 0.0) atomicMin(dt_bits, (unsigned long long)__double_as_longlong(v));
-    }
+    if (dt_bits) box_min(dt_bits, i < n ? m.cbox[i] : -1, dti);
 }
 
 // CFL timestep for a given generator velocity w (Sec. 4.2).
@@ -464,15 +407,7 @@ __global__ void __launch_bounds__(256) k_timestep(MeshDev m, HydroCfg c, const d
         const double R = cbrt(3.0 * V / (4.0 * 3.14159265358979323846));
         dti = c.cfl * R / (sound_speed(W, c.gamma) + sqrt(rx * rx + ry * ry + rz * rz));
     }
-    __shared__ double sm[8];
-    for (int o = 16; o > 0; o >>= 1) dti = fmin(dti, __shfl_xor_sync(FULL_MASK_HYDRO, dti, o));
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = dti;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double v = sm[0];
-        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) v = fmin(v, sm[k]);
-        if (v > 0.0) atomicMin(dt_bits, (unsigned long long)__double_as_longlong(v));
-    }
+    box_min(dt_bits, i < n ? m.cbox[i] : -1, dti);
 }
 
 void launch_timestep(const MeshDev &m, const HydroCfg &c, const double *U, const double *w, double *dt_min,
@@ -482,9 +417,13 @@ void launch_timestep(const MeshDev &m, const HydroCfg &c, const double *U, const
     k_timestep<<<nb, 256, 0, s>>>(m, c, U, w, reinterpret_cast<unsigned long long *>(dt_min));
 }
 
-__global__ void k_dt_init(double *dt) { *dt = __longlong_as_double(0x7ff0000000000000LL); }
+__global__ void k_dt_init(double *dt, int nbox)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nbox) dt[b] = __longlong_as_double(0x7ff0000000000000LL);
+}
 
-void launch_dt_init(double *dt, cudaStream_t s) { k_dt_init<<<1, 1, 0, s>>>(dt); }
+void launch_dt_init(double *dt, int nbox, cudaStream_t s) { k_dt_init<<<(nbox + 255) / 256, 256, 0, s>>>(dt, nbox); }
 
 void launch_mesh_velocity(const MeshDev &m, const HydroCfg &c, const double *pos, const double *U, double *w,
                           double *dt_min, cudaStream_t s)
@@ -497,14 +436,15 @@ void launch_mesh_velocity(const MeshDev &m, const HydroCfg &c, const double *pos
 // Drift: r += w dt wrapped into [0, L)
 // ---------------------------------------------------------------------------
 __global__ void k_drift(double *__restrict__ pos, int64_t n, const double *__restrict__ w,
-                        const double *__restrict__ dtp, Box3 b)
+                        const double *__restrict__ dtp, const int *__restrict__ cbox, const double *__restrict__ boxL)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double dt = *dtp;
+    const int b = cbox[i];
+    const double dt = dtp[b];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        const double L = b.L[d];
+        const double L = boxL[3 * b + d];
         double x = fmod(pos[d * n + i] + w[d * n + i] * dt, L);
         if (x < 0.0) x += L;
         if (x >= L) x -= L;
@@ -512,11 +452,11 @@ __global__ void k_drift(double *__restrict__ pos, int64_t n, const double *__res
     }
 }
 
-void launch_drift(double *pos, int64_t n, const double *w, const double *dt, const double *box3, cudaStream_t s)
+void launch_drift(double *pos, int64_t n, const double *w, const double *dt, const int *cbox, const double *boxL,
+                  cudaStream_t s)
 {
-    Box3 b{{box3[0], box3[1], box3[2]}};
     int nb = (int)((n + 255) / 256);
-    k_drift<<<nb, 256, 0, s>>>(pos, n, w, dt, b);
+    k_drift<<<nb, 256, 0, s>>>(pos, n, w, dt, cbox, boxL);
 }
 
 // ---------------------------------------------------------------------------

@@ -1,4 +1,9 @@
 // mm_internal.cuh -- shared declarations of the CUDA moving-mesh library.
+//
+// Every mesh is a set of B independent periodic boxes stored back to back
+// (a single box is B = 1): cell c belongs to box cbox[c]; box b has its own
+// grid of bins (a contiguous range of the global bin array), size, face-area
+// threshold and timestep dt[b].
 #pragma once
 
 #include <cstdint>
@@ -10,7 +15,6 @@ namespace mm {
 
 // Per-cell fixed capacities of the clipping kernel (Sec. 3).  A cell that
 // exceeds one reports MM_ECAPACITY for the tessellation.
-constexpr int CMAX = 128;   // candidates gathered per search ring
 constexpr int PMAX = 64;    // planes that ever cut the cell (6 box planes included)
 constexpr int TMAX = 128;   // vertices (triangles of the dual) alive at once
 constexpr int NSTAGE = 32;  // vertices created by one cut
@@ -28,6 +32,7 @@ enum : int {
     ST_ECAP_FACE = 32,
     ST_ECAP_RING = 64,
     ST_EDEGEN = 128,
+    ST_ECAP_MESH = 256,  // more unique faces or incidences than a fixed capacity (graph mode)
 };
 
 struct DevStatus {
@@ -38,14 +43,17 @@ struct DevStatus {
     unsigned long long cuts;
     unsigned long long pred64;   // FP64 plane tests  (q.v > o: 5 flops)
     unsigned long long solve64;  // FP64 three-plane solves (51 flops)
-    unsigned long long fan64;    // FP64 fan terms of the face geometry (33 flops)
+    unsigned long long fan64;    // FP64 fan terms of the face geometry
     unsigned long long tested;   // candidates tested against the cell
 };
 
-struct Grid {
-    int g[3];
+// One periodic box of a batch.
+struct BoxDev {
+    int g[3];      // bins per axis
+    int bin_off;   // first bin of this box in the global bin array
     double bs[3];  // bin edge per axis
-    double box[3];
+    double L[3];   // box size
+    double amin;   // faces with area <= amin are dropped
 };
 
 struct Slots {         // per-cell face slots written by the clipper
@@ -57,7 +65,8 @@ struct Slots {         // per-cell face slots written by the clipper
 };
 
 // kernels' host launchers (stream-ordered, no syncs)
-void launch_bin_count(const double *pos, int64_t n, const Grid &g, int *bin_of, int *count,
+void launch_fill_cbox(const long long *box_off, int nbox, int64_t n, int *cbox, cudaStream_t s);
+void launch_bin_count(const double *pos, int64_t n, const BoxDev *boxes, const int *cbox, int *bin_of, int *count,
                       DevStatus *st, cudaStream_t s);
 void launch_bin_scatter(const double *pos, int64_t n, const int *bin_of, const int *start, int *cursor,
                         double4_32a *sorted, cudaStream_t s);
@@ -66,20 +75,24 @@ void launch_bin_sort(const int *start, int64_t nbins, double4_32a *sorted, cudaS
 size_t scan_tmp_size(int64_t n);
 void launch_scan(const int *in, int *out, int64_t n, int *tmp, cudaStream_t s);
 
-void launch_clip(const double4_32a *sorted, const int *start, int64_t n, const Grid &g, double amin,
+void launch_clip(const double4_32a *sorted, const int *start, int64_t n, const BoxDev *boxes, const int *cbox,
                  int precision, int collect, double *vol, double *cen, Slots sl, DevStatus *st, cudaStream_t s);
 
 void launch_face_confirm(int64_t n, Slots sl, unsigned long long *emit_mask, unsigned long long *conf_mask,
                          signed char *partner, int *emit_cnt, int *conf_cnt, cudaStream_t s);
-void launch_face_write(int64_t n, const double *pos, const Grid &g, Slots sl,
+void launch_face_write(int64_t n, const double *pos, const BoxDev *boxes, const int *cbox, Slots sl,
                        const unsigned long long *emit_mask, const unsigned long long *conf_mask,
                        const signed char *partner, const int *face_off, const int *inc_off,
                        int *face_i, int *face_j, int *face_shift, double *face_area, double *face_normal,
-                       double *face_cen, int64_t fcap, int *inc_face, cudaStream_t s);
+                       double *face_cen, int64_t fcap, int *inc_face, int64_t icap, DevStatus *st, cudaStream_t s);
 
 struct MeshDev {
-    int64_t n, nf, fs;  // cells, faces, row stride of the [3][.] face arrays
-    double box[3];
+    int64_t n;           // cells
+    int64_t nf;          // unique faces (host value; see nf_dev)
+    int64_t fs;          // face capacity: row stride of the [3][.] face arrays and of the flux rows
+    const int *nf_dev;   // if set, the face count is read from here on the device (graph mode)
+    const int *cbox;     // [n] box of each cell
+    const double *boxL;  // [B][3] box sizes
     const int *face_i, *face_j, *face_shift;
     const double *area, *normal, *fcen;
     const double *vol, *cen;
@@ -91,6 +104,24 @@ struct HydroCfg {
     int limiter, regularize;
 };
 
+// FP32 records of the mixed-precision hydro path (see mm_hydro32.cu).
+struct Mixed {
+    int2 *fij;     // [F]
+    float4 *fa;    // [F]   area, normal
+    float4 *fq;    // [F]   r_j' - r_i, (x_f - r_i).x
+    float2 *ff;    // [F]   (x_f - r_i).y, .z
+    float4 *cw;    // [2n]  W^n, c - r
+    float4 *ch;    // [2n]  W^(n+1/2), c - r
+    float4 *grad;  // [4n]  limited gradient of W^(n+1/2)
+    float4 *wv;    // [n]   mesh velocity
+    float4 *flux;  // [2F]  A F
+};
+
+// dt arguments are per-box arrays [B] indexed through cbox.  Launchers over
+// faces size their grid by the face capacity when the count lives on the
+// device (graph mode).
+void launch_mixed_step(const MeshDev &m, const HydroCfg &c, const double *pos, const double *w, const double *dt,
+                       Mixed x, double *U, cudaStream_t s, void (*mark)(void *, int, bool), void *mark_arg);
 void launch_gradient(const MeshDev &m, const HydroCfg &c, const double *U_or_W, bool from_charges,
                      double *grad, double *W_half, const double *dt, cudaStream_t s);
 void launch_face_flux(const MeshDev &m, const HydroCfg &c, const double *pos, const double *w,
@@ -99,13 +130,19 @@ void launch_update(const MeshDev &m, const HydroCfg &c, const double *flux, cons
                    cudaStream_t s);
 void launch_mesh_velocity(const MeshDev &m, const HydroCfg &c, const double *pos, const double *U,
                           double *w, double *dt_min, cudaStream_t s);
-void launch_dt_init(double *dt, cudaStream_t s);
+void launch_dt_init(double *dt, int nbox, cudaStream_t s);
 void launch_timestep(const MeshDev &m, const HydroCfg &c, const double *U, const double *w, double *dt_min,
                      cudaStream_t s);
-void launch_drift(double *pos, int64_t n, const double *w, const double *dt, const double *box3,
+void launch_drift(double *pos, int64_t n, const double *w, const double *dt, const int *cbox, const double *boxL,
                   cudaStream_t s);
 void launch_prims_to_charges(const MeshDev &m, const HydroCfg &c, const double *rho, const double *vel,
                              const double *P, double *U, cudaStream_t s);
 void launch_totals(const double *U, int64_t n, double *partial, int nblocks, double *totals, cudaStream_t s);
+
+// The face count a kernel over faces must honour.
+__device__ __forceinline__ int64_t face_count(const MeshDev &m) { return m.nf_dev ? (int64_t)*m.nf_dev : m.nf; }
+
+// Grid size of a launch over faces.
+inline int64_t face_launch_count(const MeshDev &m) { return m.nf_dev ? m.fs : m.nf; }
 
 }  // namespace mm

@@ -1,0 +1,85 @@
+// mm_riemann.cuh -- the face-frame Riemann solver and floors shared by the
+// FP64 and the mixed-precision hydro kernels (Sec. 4, Sec. 4.1).
+#pragma once
+
+namespace mm {
+
+template <class T>
+struct FaceStateT {
+    T rho, vx, vy, vz, P;  // velocity already in the face frame
+};
+
+__device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
+__device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
+__device__ __forceinline__ double min_t(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float min_t(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double max_t(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float max_t(float a, float b) { return fmaxf(a, b); }
+
+// HLLC in vector form along the unit normal (nx,ny,nz): the tangential
+// velocity rides along with the normal mass flux, so no explicit tangent
+// basis is needed.  Davis wave speeds; contact speed from the jump conditions
+// across the two outer waves.  Branch order: S_L >= 0 -> F_L; S* >= 0 -> F*_L;
+// S_R > 0 -> F*_R; else F_R.
+template <class T>
+__device__ __forceinline__ void hllc_t(const FaceStateT<T> &L, const FaceStateT<T> &R, T nx, T ny, T nz, T gamma,
+                                       T F[5])
+{
+    const T gm1 = gamma - T(1);
+    const T ul = L.vx * nx + L.vy * ny + L.vz * nz;
+    const T ur = R.vx * nx + R.vy * ny + R.vz * nz;
+    const T cl = sqrt_t(gamma * L.P / L.rho), cr = sqrt_t(gamma * R.P / R.rho);
+    const T El = L.P / gm1 + T(0.5) * L.rho * (L.vx * L.vx + L.vy * L.vy + L.vz * L.vz);
+    const T Er = R.P / gm1 + T(0.5) * R.rho * (R.vx * R.vx + R.vy * R.vy + R.vz * R.vz);
+    const T sl = min_t(ul - cl, ur - cr);
+    const T sr = max_t(ul + cl, ur + cr);
+    const T ml = L.rho * (sl - ul), mr = R.rho * (sr - ur);
+    const T ss = (R.P - L.P + ul * ml - ur * mr) / (ml - mr);
+    const bool left = (sl >= T(0)) || (ss >= T(0));
+    const bool star = (sl < T(0)) && (left || sr > T(0));
+    const FaceStateT<T> &K = left ? L : R;
+    const T uk = left ? ul : ur;
+    const T Ek = left ? El : Er;
+    const T sk = left ? sl : sr;
+    const T mk = K.rho * uk;
+    // physical flux of side K
+    F[0] = mk;
+    F[1] = mk * K.vx + K.P * nx;
+    F[2] = mk * K.vy + K.P * ny;
+    F[3] = mk * K.vz + K.P * nz;
+    F[4] = (Ek + K.P) * uk;
+    if (star) {
+        // U*_K = rho_K (S_K - u_K)/(S_K - S*) (1, v_K + (S* - u_K) n, E_K/rho_K + (S* - u_K)(S* + P_K/(rho_K (S_K - u_K))))
+        const T f = K.rho * (sk - uk) / (sk - ss);
+        const T du = ss - uk;
+        const T es = f * (Ek / K.rho + du * (ss + K.P / (K.rho * (sk - uk))));
+        F[0] += sk * (f - K.rho);
+        F[1] += sk * (f * (K.vx + du * nx) - K.rho * K.vx);
+        F[2] += sk * (f * (K.vy + du * ny) - K.rho * K.vy);
+        F[3] += sk * (f * (K.vz + du * nz) - K.rho * K.vz);
+        F[4] += sk * (es - Ek);
+    }
+}
+
+// Floors on density and specific internal energy (Sec. 4.1).  A state below
+// the density floor is reset to the floor density at rest with the floor
+// internal energy; otherwise only the internal energy is raised if needed.
+// Returns true if the state changed (an untouched state is left bit for bit).
+template <class T>
+__device__ __forceinline__ bool apply_floor_t(T W[5], T rho_floor, T eps_floor)
+{
+    if (!(W[0] >= rho_floor)) {
+        W[0] = rho_floor;
+        W[1] = W[2] = W[3] = T(0);
+        W[4] = rho_floor * eps_floor;
+        return true;
+    }
+    const T ke = T(0.5) * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]) / W[0];
+    if (!(W[4] - ke >= W[0] * eps_floor)) {
+        W[4] = W[0] * eps_floor + ke;
+        return true;
+    }
+    return false;
+}
+
+}  // namespace mm

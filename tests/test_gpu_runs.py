@@ -1,0 +1,86 @@
+"""Run-level checks of the CUDA path on the paper's test problems (Sec. 5):
+the Sod shock tube against the exact Riemann solution, and the point blast
+against the Sedov-Taylor similarity law."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import exact_riemann as ER
+from paper_1707_05333_gb300 import workloads as WL
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+def run_to(ctx, torch, w, t_end, U):
+    pos = H.to_dev(torch, w.pos.T)
+    t = 0.0
+    dt = torch.empty(1, dtype=torch.float64, device="cuda")
+    steps = 0
+    while t < t_end - 1e-12:
+        mesh = ctx.mm_tessellate(pos, w.box)
+        wv = ctx.mm_mesh_velocity(mesh, pos, U)
+        dtc = ctx.mm_timestep(mesh, U, wv)
+        step = min(float(dtc.item()), t_end - t)
+        dt.fill_(step)
+        ctx.mm_flux_step(mesh, pos, wv, dt, U)
+        ctx.mm_drift(pos, wv, dt, w.box)
+        t += step
+        steps += 1
+    mesh = ctx.mm_tessellate(pos, w.box)
+    G = {k: v.cpu().numpy() for k, v in mesh.to_torch().items()}
+    return G, U.cpu().numpy(), steps
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sod_tube_full_size_matches_exact_solution(oracle, precision):
+    """128x16x16 generators in the 8x1x1 box (gamma 1.4) to t = 0.2: the
+    density profile follows the exact solution of both interfaces."""
+    import torch
+    from paper_1707_05333_gb300 import binding
+    w = WL.shock_tube(128, 16, 16)
+    ctx = binding.Context(gamma=1.4, cfl=0.3, limiter=1, precision=precision)
+    P = H.to_dev(torch, w.pos.T)
+    mesh = ctx.mm_tessellate(P, w.box)
+    U = ctx.mm_prims_to_charges(mesh, H.to_dev(torch, w.rho), H.to_dev(torch, w.vel.T), H.to_dev(torch, w.pres))
+    G, Uh, steps = run_to(ctx, torch, w, 0.2, U)
+    rho = Uh[0] / G["cell_volume"]
+    x = G["cell_centroid"][0] % 8.0
+    # interfaces at x=4 (left state on the left) and x=0==8 (mirror)
+    exact = np.where(x < 2.0, ER.profile(0.125, 0, 0.1, 1.0, 0, 1.0, 1.4, x + 8.0, 8.0, 0.2)[0],
+                     ER.profile(1.0, 0, 1.0, 0.125, 0, 0.1, 1.4, x, 4.0, 0.2)[0])
+    sel = (x > 1.0) & (x < 7.0)
+    l1 = np.mean(np.abs(rho[sel] - exact[sel]))
+    print(f"Sod precision={precision}: {steps} steps, density L1 vs exact = {l1:.4f}")
+    assert 10 < steps < 200
+    assert l1 < 0.02
+    ctx.close()
+
+
+def test_point_blast_shock_radius_follows_sedov_taylor(oracle):
+    """64^3 point blast (E = 1, rho = 1, gamma 5/3): the radius of the density
+    peak grows like xi0 (E t^2 / rho)^(1/5), xi0 = 1.15 for gamma = 5/3."""
+    import torch
+    from paper_1707_05333_gb300 import binding
+    w = WL.point_blast(48)
+    ctx = binding.Context(gamma=w.gamma, cfl=0.3, limiter=1, precision=1)
+    P = H.to_dev(torch, w.pos.T)
+    mesh = ctx.mm_tessellate(P, w.box)
+    U = ctx.mm_prims_to_charges(mesh, H.to_dev(torch, w.rho), H.to_dev(torch, w.vel.T), H.to_dev(torch, w.pres))
+    e_add = H.to_dev(torch, w.e_add)
+    U[4] += e_add
+    t_end = 0.02
+    G, Uh, steps = run_to(ctx, torch, w, t_end, U)
+    rho = Uh[0] / G["cell_volume"]
+    r = np.linalg.norm(G["cell_centroid"].T % 1.0 - 0.5, axis=1)
+    # radius of the density peak: mass-weighted radius of the densest shell
+    bins = np.linspace(0, 0.4, 41)
+    idx = np.digitize(r, bins)
+    prof = np.array([rho[idx == k].mean() if np.any(idx == k) else 0 for k in range(1, len(bins))])
+    r_peak = 0.5 * (bins[np.argmax(prof)] + bins[np.argmax(prof) + 1])
+    r_st = 1.15 * (1.0 * t_end ** 2 / 1.0) ** 0.2
+    print(f"Sedov: {steps} steps, peak radius {r_peak:.3f} vs similarity {r_st:.3f}, peak density {prof.max():.2f}")
+    assert abs(r_peak - r_st) < 0.15 * r_st
+    assert prof.max() > 1.5
+    ctx.close()

@@ -181,3 +181,45 @@ def test_full_size_shear_layer_step_properties(gpu):
     assert np.all(np.abs(t1 - t0) <= 1e-13 * scale)
     assert bool(torch.isfinite(U).all()) and bool((U[0] > 0).all())
     assert 0 < float(dt.item()) < 1e-2
+
+
+MIXED_CASES = {
+    "smooth_wave_16^3": lambda: WL.smooth_wave(16),
+    "shear_layer_32^3": lambda: WL.shear_layer(32),
+    "shock_tube_64x8x8": lambda: WL.shock_tube(64, 8, 8),
+    "point_blast_16^3": lambda: WL.point_blast(16),
+}
+
+
+@pytest.mark.parametrize("case", list(MIXED_CASES))
+def test_mixed_step_l1_error_and_conservation(oracle, gpu, case):
+    """precision=1: FP32 gradients, half step, reconstruction and fluxes, FP64
+    update.  One step against the FP64 oracle: relative L1 error of density,
+    momentum and energy <= 1e-5, and totals conserved to 1e-12."""
+    c, torch = gpu
+    w = MIXED_CASES[case]()
+    T, U = setup(oracle, w)
+    ocfg, gcfg = cfg_pair(oracle, w.gamma, cfl=w.cfl, limiter=1)
+    S = oracle.step(w.pos, U, w.box, ocfg, tess=T)
+    gcfg.precision = 1
+    c.set_config(**{f: getattr(gcfg, f) for f, _ in gcfg._fields_})
+    try:
+        pos = H.to_dev(torch, w.pos.T)
+        Ud = H.to_dev(torch, U.T)
+        t0 = c.mm_totals(Ud).cpu().numpy()
+        dt = torch.tensor([S["dt"]], dtype=torch.float64, device="cuda")
+        c.mm_step(pos, Ud, w.box, dt_fixed=dt)
+        t1 = c.mm_totals(Ud).cpu().numpy()
+    finally:
+        c.set_config(precision=0)
+    G = Ud.cpu().numpy().T
+    O = S["U"]
+    l1 = {}
+    for name, cols in (("density", [0]), ("momentum", [1, 2, 3]), ("energy", [4])):
+        l1[name] = np.abs(G[:, cols] - O[:, cols]).sum() / np.abs(O[:, cols]).sum()
+    print(case, "relative L1 vs FP64 oracle:", {k: f"{v:.2e}" for k, v in l1.items()})
+    assert l1["density"] <= 1e-5 and l1["energy"] <= 1e-5 and l1["momentum"] <= 1e-5, l1
+    scale = np.abs(U).sum(0)
+    # momentum scale sqrt(M E) (the momentum may start exactly at zero)
+    scale[1:4] = max(scale[1:4].max(), np.sqrt(scale[0] * scale[4]))
+    assert np.all(np.abs(t1 - t0) <= 1e-12 * scale), (t1 - t0) / scale
