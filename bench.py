@@ -40,6 +40,8 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n-side", type=int, default=256, help="shear layer generators per axis")
     p.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    p.add_argument("--clip-filter", type=int, choices=[0, 1], default=1,
+                   help="1: FP32-filtered clipping with exact FP64 fallback (same mesh bit for bit)")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--cpu-sample-side", type=int, default=24)
     p.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -117,6 +119,34 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # determinant, the reciprocal and the scaled numerators -> 51 flops), and a
 # face-fan term of the area/centroid sums (33 flops).
 FLOPS_PLANE_TEST, FLOPS_SOLVE, FLOPS_FAN = 5, 51, 33
+# FP32 lanes: 128 per SM per clock, so one FP32 flop costs 1/64 of an FP64
+# flop of issue time on this part.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def clip_roofline(direct, filtered, ms, n, clip_filter):
+    """ALU roofline of the clipping kernel.  `direct` holds the counters of a
+    tessellation with every vertex solved and tested in FP64 (so they count
+    all algorithmic plane tests and vertex solves); `filtered` those of the
+    same tessellation with the FP32 filter (tests and solves in FP32, then the
+    FP64 tests near ties, the final FP64 vertices and the FP64 face fans).
+    Work is expressed in FP64-equivalent flops: an FP32 flop weighs
+    FP64/FP32 peak, so frac = (F64/P64 + F32/P32) / time."""
+    if clip_filter:
+        f32 = FLOPS_PLANE_TEST * direct["fp64_plane_tests"] + FLOPS_SOLVE * direct["fp64_vertex_solves"]
+        f64 = (FLOPS_PLANE_TEST * filtered["fp64_plane_tests"] + FLOPS_SOLVE * filtered["fp64_vertex_solves"] +
+               FLOPS_FAN * filtered["fp64_fan_terms"])
+    else:
+        f32 = 0
+        f64 = (FLOPS_PLANE_TEST * direct["fp64_plane_tests"] + FLOPS_SOLVE * direct["fp64_vertex_solves"] +
+               FLOPS_FAN * direct["fp64_fan_terms"])
+    eq = f64 + f32 * FP64_PEAK_TFLOPS / FP32_PEAK_TFLOPS
+    ach = eq / (ms / 1e3) / 1e12
+    return {"kernel": "k_clip", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s (FP64-equivalent)", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz (FP64 ALU); FP32 flops weighted 1/64",
+            "fp64_flops_per_launch": f64, "fp32_flops_per_launch": f32, "fp64_equiv_flops_per_cell": eq / n,
+            "launch_ms": ms}
 
 
 def measured_peaks():
@@ -200,6 +230,20 @@ def algorithmic_bytes(stage, n, F):
     return None
 
 
+def aggregate(ms, cells_per_rank, steps, world):
+    """Whole-job throughput across ranks: every rank advanced its own replica,
+    so value = world * cells * steps / (slowest rank's time).  Returns
+    (value, slowest ms); the maximum is an all-reduce when world > 1."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return world * cells_per_rank * steps / (ms / 1e3), ms
+
+
 def time_steps(torch, stream, fn, steps):
     """Device time of `steps` calls of fn on `stream`, in ms (CUDA events)."""
     torch.cuda.synchronize()
@@ -229,6 +273,27 @@ def measure_mixed_single(args, w):
         ctx.close()
     return {"value": w.n * args.steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
             "dtype": "f64+f32", "note": "FP32 gradients/half step/fluxes, FP64 clipping decisions, geometry and update"}
+
+
+def measure_direct_clip(args, w):
+    """FP64 hydro with the direct FP64 clipper (every vertex solved and tested
+    in FP64): the same mesh bit for bit as the filtered clipper, slower."""
+    import torch
+    from paper_1707_05333_gb300 import binding as BD
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = BD.Context(stream=stream, gamma=w.gamma, cfl=w.cfl, limiter=1, precision=0, clip_filter=0)
+        pos = torch.tensor(w.pos.T.copy(), dtype=torch.float64, device="cuda")
+        mesh = ctx.mm_tessellate(pos, w.box)
+        U = ctx.mm_prims_to_charges(mesh, torch.tensor(w.rho, device="cuda"), torch.tensor(w.vel.T.copy(), device="cuda"),
+                                    torch.tensor(w.pres, device="cuda"))
+        for _ in range(args.warmup):
+            ctx.mm_step(pos, U, w.box)
+        steps = max(2, args.steps // 2)
+        ms = time_steps(torch, stream, lambda: ctx.mm_step(pos, U, w.box), steps)
+        ctx.close()
+    return {"value": w.n * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "dtype": "f64",
+            "note": "clip_filter=0: every clipping vertex solved and tested in FP64 as it appears"}
 
 
 def measure_ensemble(args):
@@ -299,7 +364,8 @@ def run_ours(args, world, rank, local):
     prec = 0 if args.precision == "fp64" else 1
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        ctx = BD.Context(stream=stream, gamma=w.gamma, cfl=w.cfl, limiter=1, precision=prec)
+        ctx = BD.Context(stream=stream, gamma=w.gamma, cfl=w.cfl, limiter=1, precision=prec,
+                         clip_filter=args.clip_filter)
         pos0 = torch.tensor(w.pos.T.copy(), dtype=torch.float64, device="cuda")
         mesh = ctx.mm_tessellate(pos0, w.box)
         U0 = ctx.mm_prims_to_charges(mesh, torch.tensor(w.rho, device="cuda"),
@@ -308,8 +374,12 @@ def run_ours(args, world, rank, local):
         pos, U = pos0.clone(), U0.clone()
         for _ in range(args.warmup):
             ctx.mm_step(pos, U, w.box)
-        # one counted tessellation of the current state (outside the timed region)
-        ctx.set_config(collect_stats=1)
+        # counted tessellations of the current state (outside the timed region):
+        # the direct FP64 clipper counts every algorithmic test and solve
+        ctx.set_config(collect_stats=1, clip_filter=0)
+        ctx.mm_tessellate(pos, w.box)
+        tdirect = ctx.mm_tess_stats()
+        ctx.set_config(clip_filter=args.clip_filter)
         ctx.mm_tessellate(pos, w.box)
         tstats = ctx.mm_tess_stats()
         ctx.set_config(collect_stats=0)
@@ -341,13 +411,8 @@ def run_ours(args, world, rank, local):
         stages = ctx.mm_stage_times()
         ctx.mm_set_timing(False)
         nf = ctx.mm_tessellate(pos, w.box).nfaces  # faces of the current mesh, for the byte counts
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
         n = w.n
-        value = world * n * args.steps / (ms / 1e3)
+        value, ms = aggregate(ms, n, args.steps, world)
 
         # ---- end to end through the ABI with host buffers
         pos_h = torch.empty_like(pos, device="cpu").pin_memory()
@@ -368,12 +433,8 @@ def run_ours(args, world, rank, local):
         f1.record(stream)
         stream.synchronize()
         e2e_ms = f0.elapsed_time(f1)
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        e2e = {"value": world * n * args.e2e_steps / (e2e_ms / 1e3), "unit": UNIT,
+        e2e_value, e2e_ms = aggregate(e2e_ms, n, args.e2e_steps, world)
+        e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": int(pos.numel() * 8 + U.numel() * 8),
                "d2h_bytes_per_step": int(pos.numel() * 8 + U.numel() * 8)}
 
@@ -383,13 +444,7 @@ def run_ours(args, world, rank, local):
     peak, peak_kind = measured_peaks()
     roofline = None
     if dom == "clip":
-        flops = (FLOPS_PLANE_TEST * tstats["fp64_plane_tests"] + FLOPS_SOLVE * tstats["fp64_vertex_solves"] +
-                 FLOPS_FAN * tstats["fp64_fan_terms"])
-        ach = flops / (dom_ms / 1e3) / 1e12
-        roofline = {"kernel": "k_clip", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz (FP64 ALU)",
-                    "algorithmic_flops_per_launch": flops, "flops_per_cell": flops / n, "launch_ms": dom_ms}
+        roofline = clip_roofline(tdirect, tstats, dom_ms, n, args.clip_filter)
     else:
         byts = algorithmic_bytes(dom, n, nf)
         if byts is not None:
@@ -401,7 +456,9 @@ def run_ours(args, world, rank, local):
 
     variants = None
     if rank == 0 and not args.no_variants:
-        variants = {"mixed_same_workload": measure_mixed_single(args, w), "batched_ensemble": measure_ensemble(args)}
+        variants = {"mixed_same_workload": measure_mixed_single(args, w),
+                    "direct_fp64_clip_same_workload": measure_direct_clip(args, w),
+                    "batched_ensemble": measure_ensemble(args)}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -415,7 +472,8 @@ def run_ours(args, world, rank, local):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f64+f32",
                 "data": "synthetic",
                 "config": {"workload": f"shear_layer_{args.n_side}^3", "cells": n, "faces": nf,
-                           "precision": args.precision, "parallelism": f"replicas x{world}",
+                           "precision": args.precision, "clip_filter": args.clip_filter,
+                           "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (state + mesh >> 129 MB), no flush"},
                 "roofline": roofline, "stage_ms": stage_ms, "tess_stats_per_cell": {k: v / n for k, v in tstats.items()
                                                                                    if not k.startswith("max")}, "cpu_baseline": cpu, "e2e": e2e,

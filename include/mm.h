@@ -57,16 +57,26 @@ typedef struct {
     double rho_floor; /* density floor (Sec. 4.1)                                           */
     double eps_floor; /* specific internal energy floor (Sec. 4.1)                          */
     double area_rel;  /* faces with area <= area_rel (V_box/n)^(2/3) are dropped            */
-    int limiter;      /* 0 none, 1 S10, 2 S10 times Duffell-MacFadyen (Sec. 4.1)            */
+    int limiter;      /* 0 none, 1 S10, 2 S10 times Duffell-MacFadyen, 3 S10 measured to   */
+                      /*    face centroids (Sec. 4.1)                                       */
     int regularize;   /* 1: add the roundness correction to w (Sec. 4.2)                    */
-    int precision;    /* 0: plain FP64 throughout; 1: mixed (FP32 clipping filter with      */
-                      /*    exact FP64 fallback, FP32 gradients and fluxes, FP64 update)      */
+    int precision;    /* 0: FP64 hydro; 1: mixed (FP32 gradients, half step and fluxes,     */
+                      /*    FP64 update); the mesh is FP64-exact either way (clip_filter)   */
     int collect_stats;/* 1: the clipper records the counters read by mm_tess_stats          */
+    int riemann;      /* 0 HLLC (the paper's default), 1 HLL (Sec. 4)                        */
+    int clip_warps;   /* cells (warps) per block of the clipping kernel, 1..8 (tunable)      */
+    int cand_cap;     /* candidates per sorted batch of the clipper, 32..64 (tunable)        */
+    int clip_filter;  /* 1: clip with FP32 vertices, an error-bounded FP32 plane test and    */
+                      /*    an exact FP64 test near ties, then FP64 vertices (same mesh, bit */
+                      /*    for bit); 0: solve and test every vertex in FP64 as it appears  */
+    double bin_scale; /* neighbour-search bin edge in mean generator spacings (tunable)       */
 } mm_config;
 
 /* Fill a config with the defaults: gamma 5/3, cfl 0.3, eta 1, chi 1, zeta
  * 0.25, theta 0.49, floors 1e-10, area_rel 1e-10, S10 limiter, no
- * roundness correction, FP64, no counters. */
+ * roundness correction, FP64 hydro, filtered clipping, no counters, HLLC,
+ * 4 clip warps per block, batches of 64 candidates, bins one mean spacing
+ * wide. */
 void mm_default_config(mm_config *cfg);
 
 typedef struct mm_ctx mm_ctx;
@@ -168,6 +178,16 @@ mm_status mm_step(mm_ctx *ctx, double *pos, double *U, int64_t n, const double b
  * overflow) are reported by mm_sync_status. */
 mm_status mm_step_batched(mm_ctx *ctx, double *pos, double *U, int64_t n, const int64_t *box_off,
                           const double *boxes, int nboxes, double *dt_out);
+
+/* The context's current configuration. */
+mm_status mm_get_config(const mm_ctx *ctx, mm_config *cfg);
+
+/* Pick clip_warps, cand_cap and bin_scale for generators like pos[3][n] in
+ * box: every combination of {2,4,8} x {32,64} x {0.8,1,1.25,1.5} is timed on
+ * `reps` tessellations (after one warm-up each) and the fastest is kept in
+ * the context's configuration; *best_ms (may be NULL) receives its time.
+ * The mesh of the last timed tessellation is left in the context. */
+mm_status mm_autotune(mm_ctx *ctx, const double *pos, int64_t n, const double box[3], int reps, double *best_ms);
 
 /* Wait for the context's stream and report the device status word of the
  * last tessellation (mm_step_batched does not wait on its own). */

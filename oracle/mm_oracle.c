@@ -676,9 +676,10 @@ static void solve3(const double *M, const double *B /* [3][5] */, double *X /* [
  * linear fields.  Then the S10 factor min(1, psi_ij) over the neighbours
  * (psi from the neighbourhood max/min and Delta_ij = grad . (c_j - c_i)), and
  * optionally the Duffell-MacFadyen factor min(1, max(0, theta (W_j - W_i) /
- * Delta_ij)). */
+ * Delta_ij)).  limiter 3 is S10 with Delta_ij measured to the face centroid,
+ * grad . (x_f - c_i), as in the original S10 scheme. */
 void orc_gradient(int64_t n, int64_t nf, const int32_t *fi, const int32_t *fj, const int32_t *fshift,
-                  const double *farea, const double *fnormal, const double *centroid,
+                  const double *farea, const double *fnormal, const double *fcentroid, const double *centroid,
                   const double *box, const double *W, const orc_cfg *cfg, double *grad)
 {
     double *M = (double *)calloc(9 * n, sizeof(double));
@@ -729,14 +730,24 @@ void orc_gradient(int64_t n, int64_t nf, const int32_t *fi, const int32_t *fj, c
             for (int side = 0; side < 2; ++side) {
                 int32_t c = side ? j : i, o = side ? i : j;
                 double sg = side ? -1.0 : 1.0;
+                double dv[3];
+                for (int a = 0; a < 3; ++a) {
+                    if (cfg->limiter == 3) {
+                        /* face centroid in this cell's frame minus the cell centroid */
+                        double xf = fcentroid[3 * f + a] - (side ? fshift[3 * f + a] * box[a] : 0.0);
+                        dv[a] = xf - centroid[3 * c + a];
+                    } else {
+                        dv[a] = sg * d[a];
+                    }
+                }
                 for (int k = 0; k < 5; ++k) {
                     const double *g = grad + 15 * c + 3 * k;
-                    double del = sg * (g[0] * d[0] + g[1] * d[1] + g[2] * d[2]);
+                    double del = g[0] * dv[0] + g[1] * dv[1] + g[2] * dv[2];
                     double p = 1.0;
                     if (del > 0.0) p = (wmax[5 * c + k] - W[5 * c + k]) / del;
                     else if (del < 0.0) p = (wmin[5 * c + k] - W[5 * c + k]) / del;
                     if (p < psi[5 * c + k]) psi[5 * c + k] = p;
-                    if (cfg->limiter >= 2 && del != 0.0) {
+                    if (cfg->limiter == 2 && del != 0.0) {
                         double pd = cfg->theta * (W[5 * o + k] - W[5 * c + k]) / del;
                         if (pd < 0.0) pd = 0.0;
                         if (pd < psidm[5 * c + k]) psidm[5 * c + k] = pd;
@@ -747,7 +758,7 @@ void orc_gradient(int64_t n, int64_t nf, const int32_t *fi, const int32_t *fj, c
         for (int64_t i = 0; i < n; ++i)
             for (int k = 0; k < 5; ++k) {
                 double alpha = psi[5 * i + k] < 1.0 ? psi[5 * i + k] : 1.0;
-                if (cfg->limiter >= 2) alpha *= (psidm[5 * i + k] < 1.0 ? psidm[5 * i + k] : 1.0);
+                if (cfg->limiter == 2) alpha *= (psidm[5 * i + k] < 1.0 ? psidm[5 * i + k] : 1.0);
                 for (int a = 0; a < 3; ++a) grad[15 * i + 3 * k + a] *= alpha;
             }
     }
@@ -814,6 +825,26 @@ void orc_hllc_1d(const double *L, const double *R, double gamma, double *F)
     memcpy(F, Fr, sizeof(Fr));
 }
 
+/* HLL flux of the same 1-D problem: the single intermediate state between
+ * the Davis wave speeds, from the integral form of the conservation laws. */
+void orc_hll_1d(const double *L, const double *R, double gamma, double *F)
+{
+    double rl = L[0], ul = L[1], pl = L[4];
+    double rr = R[0], ur = R[1], pr = R[4];
+    double cl = sqrt(gamma * pl / rl), cr = sqrt(gamma * pr / rr);
+    double El = pl / (gamma - 1.0) + 0.5 * rl * (ul * ul + L[2] * L[2] + L[3] * L[3]);
+    double Er = pr / (gamma - 1.0) + 0.5 * rr * (ur * ur + R[2] * R[2] + R[3] * R[3]);
+    double sl = fmin(ul - cl, ur - cr);
+    double sr = fmax(ul + cl, ur + cr);
+    double Fl[5] = {rl * ul, rl * ul * ul + pl, rl * ul * L[2], rl * ul * L[3], (El + pl) * ul};
+    double Fr[5] = {rr * ur, rr * ur * ur + pr, rr * ur * R[2], rr * ur * R[3], (Er + pr) * ur};
+    if (sl >= 0.0) { memcpy(F, Fl, sizeof(Fl)); return; }
+    if (sr <= 0.0) { memcpy(F, Fr, sizeof(Fr)); return; }
+    double Ul[5] = {rl, rl * ul, rl * L[2], rl * L[3], El};
+    double Ur[5] = {rr, rr * ur, rr * R[2], rr * R[3], Er};
+    for (int k = 0; k < 5; ++k) F[k] = (sr * Fl[k] - sl * Fr[k] + sl * sr * (Ur[k] - Ul[k])) / (sr - sl);
+}
+
 /* Orthonormal basis (n, t1, t2) with t1 perpendicular to n. */
 static void face_basis(const double *n, double *t1, double *t2)
 {
@@ -852,7 +883,8 @@ void orc_riemann_lab(const double *WL, const double *WR, const double *nrm, cons
         ps[s][4] = P;
     }
     double Fp[5];
-    orc_hllc_1d(pl, pr, g, Fp);
+    if (cfg->riemann == 1) orc_hll_1d(pl, pr, g, Fp);
+    else orc_hllc_1d(pl, pr, g, Fp);
     double fm = Fp[0];
     double fp[3];
     for (int d = 0; d < 3; ++d) fp[d] = Fp[1] * nrm[d] + Fp[2] * t1[d] + Fp[3] * t2[d];

@@ -21,8 +21,10 @@ typedef struct {
     double theta;      /* Duffell-MacFadyen limiter parameter (Sec. 4.1)                  */
     double rho_floor;  /* density floor (Sec. 4.1, value not given in the paper)          */
     double eps_floor;  /* specific internal energy ("temperature") floor (Sec. 4.1)       */
-    int limiter;       /* 0 none, 1 S10, 2 S10 then Duffell-MacFadyen                    */
+    int limiter;       /* 0 none, 1 S10, 2 S10 then Duffell-MacFadyen, 3 S10 to face centroids */
     int regularize;    /* 1: add the roundness correction to the mesh velocity            */
+    int riemann;       /* 0 HLLC, 1 HLL (Sec. 4)                                         */
+    int pad;
 } orc_cfg;
 
 /* Voronoi tessellation of the periodic box by clipping (Sec. 3).
@@ -47,7 +49,7 @@ int orc_tessellate_subset(int64_t n, const double *pos, const double *box, doubl
 /* Limited cell-centred gradient of a per-volume field W[n][5] (Sec. 4.1).
  * Unique faces.  grad[n][5][3]. */
 void orc_gradient(int64_t n, int64_t nf, const int32_t *fi, const int32_t *fj, const int32_t *fshift,
-                  const double *farea, const double *fnormal, const double *centroid,
+                  const double *farea, const double *fnormal, const double *fcentroid, const double *centroid,
                   const double *box, const double *W, const orc_cfg *cfg, double *grad);
 
 /* Half-step predictor (Sec. 4.1): Wh = W - dt/2 sum_d A_d(W) dW/dx_d. */
@@ -87,5 +89,7 @@ void orc_riemann_lab(const double *WL, const double *WR, const double *nrm, cons
                      const orc_cfg *cfg, double *F);
 /* One-dimensional HLLC flux in the face frame: prim = (rho, u, v1, v2, P). */
 void orc_hllc_1d(const double *primL, const double *primR, double gamma, double *F);
+/* One-dimensional HLL flux with the same wave speeds. */
+void orc_hll_1d(const double *primL, const double *primR, double gamma, double *F);
 
 #endif

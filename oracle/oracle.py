@@ -45,12 +45,13 @@ class Cfg(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("cfl", ctypes.c_double), ("eta", ctypes.c_double),
                 ("chi", ctypes.c_double), ("zeta", ctypes.c_double), ("theta", ctypes.c_double),
                 ("rho_floor", ctypes.c_double), ("eps_floor", ctypes.c_double),
-                ("limiter", ctypes.c_int), ("regularize", ctypes.c_int)]
+                ("limiter", ctypes.c_int), ("regularize", ctypes.c_int), ("riemann", ctypes.c_int),
+                ("pad", ctypes.c_int)]
 
 
 def make_cfg(gamma=5.0 / 3.0, cfl=0.3, eta=1.0, chi=1.0, zeta=0.25, theta=0.49,
-             rho_floor=1e-10, eps_floor=1e-10, limiter=1, regularize=0) -> Cfg:
-    return Cfg(gamma, cfl, eta, chi, zeta, theta, rho_floor, eps_floor, limiter, regularize)
+             rho_floor=1e-10, eps_floor=1e-10, limiter=1, regularize=0, riemann=0) -> Cfg:
+    return Cfg(gamma, cfl, eta, chi, zeta, theta, rho_floor, eps_floor, limiter, regularize, riemann, 0)
 
 
 _P = ctypes.c_void_p
@@ -68,7 +69,7 @@ def lib():
             L.orc_tessellate_subset.argtypes = [_I64, _P, _P, ctypes.c_double, _I64, _P, _P, _P, _I64,
                                                 _P, _P, _P, _P, _P, _P, _P]
             L.orc_tessellate_subset.restype = ctypes.c_int
-            L.orc_gradient.argtypes = [_I64, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
+            L.orc_gradient.argtypes = [_I64, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
             L.orc_half_step.argtypes = [_I64, _P, _P, _P, ctypes.c_double, _P]
             L.orc_face_flux.argtypes = [_I64, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                                         _P, _P]
@@ -82,6 +83,7 @@ def lib():
             L.orc_flux_jacobian.argtypes = [_P, ctypes.c_int, ctypes.c_double, _P]
             L.orc_riemann_lab.argtypes = [_P, _P, _P, _P, _P, _P]
             L.orc_hllc_1d.argtypes = [_P, _P, ctypes.c_double, _P]
+            L.orc_hll_1d.argtypes = [_P, _P, ctypes.c_double, _P]
             _lib = L
     return _lib
 
@@ -167,9 +169,9 @@ def gradient(F, volume, centroid, box, W, cfg):
     n = W.shape[0]
     grad = np.zeros((n, 5, 3))
     fi, fj, sh = _c(F["i"], np.int32), _c(F["j"], np.int32), _c(F["shift"], np.int32)
-    area, nrm = _c(F["area"]), _c(F["normal"])
+    area, nrm, fc = _c(F["area"]), _c(F["normal"]), _c(F["centroid"])
     cen, box, W = _c(centroid), _c(box), _c(W)
-    lib().orc_gradient(n, fi.shape[0], _p(fi), _p(fj), _p(sh), _p(area), _p(nrm), _p(cen), _p(box),
+    lib().orc_gradient(n, fi.shape[0], _p(fi), _p(fj), _p(sh), _p(area), _p(nrm), _p(fc), _p(cen), _p(box),
                        _p(W), ctypes.byref(cfg), _p(grad))
     return grad
 
@@ -246,6 +248,13 @@ def riemann_lab(WL, WR, nrm, wface, cfg):
     WL, WR, nrm, wface = _c(WL), _c(WR), _c(nrm), _c(wface)
     F = np.zeros(5)
     lib().orc_riemann_lab(_p(WL), _p(WR), _p(nrm), _p(wface), ctypes.byref(cfg), _p(F))
+    return F
+
+
+def hll_1d(primL, primR, gamma):
+    L, R = _c(primL), _c(primR)
+    F = np.zeros(5)
+    lib().orc_hll_1d(_p(L), _p(R), float(gamma), _p(F))
     return F
 
 

@@ -41,7 +41,9 @@ class Config(ctypes.Structure):
                 ("chi", ctypes.c_double), ("zeta", ctypes.c_double), ("theta", ctypes.c_double),
                 ("rho_floor", ctypes.c_double), ("eps_floor", ctypes.c_double),
                 ("area_rel", ctypes.c_double), ("limiter", ctypes.c_int), ("regularize", ctypes.c_int),
-                ("precision", ctypes.c_int), ("collect_stats", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("collect_stats", ctypes.c_int),
+                ("riemann", ctypes.c_int), ("clip_warps", ctypes.c_int), ("cand_cap", ctypes.c_int),
+                ("clip_filter", ctypes.c_int), ("bin_scale", ctypes.c_double)]
 
 
 class MeshStruct(ctypes.Structure):
@@ -56,7 +58,7 @@ EXPORTS = ["mm_default_config", "mm_create", "mm_destroy", "mm_last_error", "mm_
            "mm_tessellate", "mm_gradients", "mm_mesh_velocity", "mm_timestep", "mm_flux_step",
            "mm_drift", "mm_step", "mm_prims_to_charges", "mm_totals", "mm_copy", "mm_tess_stats",
            "mm_set_timing", "mm_stage_times", "mm_kernel_launches", "mm_totals_noalloc", "mm_step_batched",
-           "mm_sync_status", "mm_current_mesh"]
+           "mm_sync_status", "mm_current_mesh", "mm_get_config", "mm_autotune"]
 
 STATS = ["max_candidates", "max_planes", "max_vertices", "multi_ring_cells", "cuts", "fp64_plane_tests",
          "fp64_vertex_solves", "fp64_fan_terms", "candidates_tested"]
@@ -102,6 +104,8 @@ def load(path: str | None = None):
     L.mm_stage_times.argtypes = [_c_p, P(ctypes.c_double), P(_c_i64)]
     L.mm_step_batched.argtypes = [_c_p, _c_p, _c_p, _c_i64, P(_c_i64), P(ctypes.c_double), ctypes.c_int, _c_p]
     L.mm_sync_status.argtypes = [_c_p]
+    L.mm_get_config.argtypes = [_c_p, P(Config)]
+    L.mm_autotune.argtypes = [_c_p, _c_p, _c_i64, P(ctypes.c_double), ctypes.c_int, P(ctypes.c_double)]
     L.mm_current_mesh.argtypes = [_c_p, P(MeshStruct)]
     L.mm_totals_noalloc.argtypes = [_c_p, _c_i64, _c_p, _c_p, ctypes.c_char_p, _c_i64]
     L.mm_kernel_launches.argtypes = [_c_p]
@@ -283,6 +287,22 @@ class Context:
         self._call("mm_step_batched", self.h, _ptr(pos, (3, n)), _ptr(U, (5, n)), n,
                    off.ctypes.data_as(ctypes.POINTER(_c_i64)), bx.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                    nbox, _ptr(dt_out, (nbox,)))
+
+    def mm_get_config(self) -> Config:
+        cfg = Config()
+        self._call("mm_get_config", self.h, ctypes.byref(cfg))
+        return cfg
+
+    def mm_autotune(self, pos, box, reps: int = 1) -> dict:
+        """Time the clipper over its tunable settings and keep the fastest."""
+        n = pos.shape[1]
+        b = (ctypes.c_double * 3)(*[float(x) for x in box])
+        best = ctypes.c_double(0.0)
+        self._call("mm_autotune", self.h, _ptr(pos, (3, n)), n, b, int(reps), ctypes.byref(best))
+        cfg = self.mm_get_config()
+        self.config = cfg
+        return {"clip_warps": cfg.clip_warps, "cand_cap": cfg.cand_cap, "bin_scale": cfg.bin_scale,
+                "tessellate_ms": best.value}
 
     def mm_sync_status(self) -> None:
         self._call("mm_sync_status", self.h)

@@ -179,6 +179,7 @@ static HydroCfg hydro_cfg(const mm_config &g)
     h.eps_floor = g.eps_floor;
     h.limiter = g.limiter;
     h.regularize = g.regularize;
+    h.riemann = g.riemann;
     return h;
 }
 
@@ -187,10 +188,14 @@ static mm_status check_cfg(mm_ctx *c, const mm_config *g)
     if (!g) return fail(c, MM_EINVAL, "config is NULL");
     if (!(g->gamma > 1.0) || !std::isfinite(g->gamma)) return fail(c, MM_EINVAL, "gamma must be > 1");
     if (!(g->cfl > 0.0)) return fail(c, MM_EINVAL, "cfl must be > 0");
-    if (g->limiter < 0 || g->limiter > 2) return fail(c, MM_EINVAL, "limiter must be 0, 1 or 2");
+    if (g->limiter < 0 || g->limiter > 3) return fail(c, MM_EINVAL, "limiter must be 0, 1, 2 or 3");
+    if (g->riemann < 0 || g->riemann > 1) return fail(c, MM_EINVAL, "riemann must be 0 (HLLC) or 1 (HLL)");
     if (g->precision < 0 || g->precision > 1) return fail(c, MM_EINVAL, "precision must be 0 or 1");
     if (!(g->rho_floor > 0.0) || !(g->eps_floor >= 0.0)) return fail(c, MM_EINVAL, "floors must be positive");
     if (!(g->area_rel >= 0.0)) return fail(c, MM_EINVAL, "area_rel must be >= 0");
+    if (g->clip_warps < 1 || g->clip_warps > CLIP_MAX_WARPS) return fail(c, MM_EINVAL, "clip_warps must be in [1, 8]");
+    if (g->cand_cap < 32 || g->cand_cap > 64) return fail(c, MM_EINVAL, "cand_cap must be in [32, 64]");
+    if (!(g->bin_scale >= 0.25 && g->bin_scale <= 4.0)) return fail(c, MM_EINVAL, "bin_scale must be in [0.25, 4]");
     return MM_OK;
 }
 
@@ -289,7 +294,7 @@ static mm_status setup_boxes(mm_ctx *c, int64_t n, const int64_t *box_off, const
             if (!(L[d] > 0.0) || !std::isfinite(L[d])) return fail(c, MM_EINVAL, "box %d size must be finite and > 0", b);
         BoxDev &g = c->boxes_host[b];
         const double vcell = L[0] * L[1] * L[2] / (double)nb;
-        const double spacing = std::cbrt(vcell);
+        const double spacing = std::cbrt(vcell) * c->cfg.bin_scale;
         int64_t nbb = 1;
         for (int d = 0; d < 3; ++d) {
             int64_t gd = (int64_t)std::floor(L[d] / spacing);
@@ -297,6 +302,7 @@ static mm_status setup_boxes(mm_ctx *c, int64_t n, const int64_t *box_off, const
             if (gd > 4096) gd = 4096;
             g.g[d] = (int)gd;
             g.bs[d] = L[d] / (double)gd;
+            g.ibs[d] = (double)gd / L[d];
             g.L[d] = L[d];
             c->boxL_host[3 * b + d] = L[d];
             nbb *= gd;
@@ -394,8 +400,9 @@ static mm_status tess_enqueue(mm_ctx *c, const double *pos, bool fixed)
 
     Slots sl{P<int>(c->s_cnt), P<int>(c->s_nb), P<unsigned char>(c->s_sh), P<double>(c->s_area), P<double>(c->s_fc)};
     stage_mark(c, MM_STAGE_CLIP, true);
-    launch_clip(P<double4_32a>(c->sorted), P<int>(c->bin_start), n, boxes, cbox, c->cfg.precision, c->cfg.collect_stats,
-                P<double>(c->vol), P<double>(c->cen), sl, c->st, s);
+    launch_clip(P<double4_32a>(c->sorted), P<int>(c->bin_start), n, boxes, cbox, c->cfg.clip_filter ? 1 : 0,
+                c->cfg.collect_stats,
+                c->cfg.clip_warps, c->cfg.cand_cap, P<double>(c->vol), P<double>(c->cen), sl, c->st, s);
     CKLAUNCH();
     stage_mark(c, MM_STAGE_CLIP, false);
     c->launches += 1;
@@ -555,6 +562,11 @@ void mm_default_config(mm_config *g)
     g->limiter = 1;
     g->regularize = 0;
     g->precision = 0;
+    g->riemann = 0;
+    g->clip_warps = 4;
+    g->cand_cap = 64;
+    g->clip_filter = 1;
+    g->bin_scale = 1.0;
 }
 
 mm_status mm_create(mm_ctx **out, const mm_config *cfg, void *cuda_stream)
@@ -794,6 +806,65 @@ mm_status mm_step_batched(mm_ctx *c, double *pos, double *U, int64_t n, const in
     }
     CK(cudaGraphLaunch(c->gexec, c->stream));
     c->launches += c->graph_launches;
+    return MM_OK;
+}
+
+mm_status mm_get_config(const mm_ctx *c, mm_config *cfg)
+{
+    if (!c || !cfg) return MM_EINVAL;
+    *cfg = c->cfg;
+    return MM_OK;
+}
+
+mm_status mm_autotune(mm_ctx *c, const double *pos, int64_t n, const double box[3], int reps, double *best_ms)
+{
+    if (!c) return MM_EINVAL;
+    if (!pos || !box) return fail(c, MM_EINVAL, "null pointer argument");
+    if (reps < 1) reps = 1;
+    static const int warps_opt[] = {2, 4, 8};
+    static const int cap_opt[] = {32, 64};
+    static const double scale_opt[] = {0.8, 1.0, 1.25, 1.5};
+    const mm_config keep = c->cfg;
+    const int keep_timing = c->timing;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double best = 1e300;
+    mm_config best_cfg = keep;
+    mm_status r = MM_OK;
+    c->timing = 0;
+    for (double sc : scale_opt)
+        for (int wp : warps_opt)
+            for (int cap : cap_opt) {
+                c->cfg = keep;
+                c->cfg.bin_scale = sc;
+                c->cfg.clip_warps = wp;
+                c->cfg.cand_cap = cap;
+                double tot = 0.0;
+                for (int k = 0; k < reps + 1 && r == MM_OK; ++k) {
+                    cudaEventRecord(e0, c->stream);
+                    r = mm_tessellate(c, pos, n, box, nullptr);
+                    cudaEventRecord(e1, c->stream);
+                    cudaEventSynchronize(e1);
+                    float ms = 0.0f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (k > 0) tot += ms;  // the first run of each setting only warms up
+                }
+                if (r != MM_OK) break;
+                if (tot / reps < best) {
+                    best = tot / reps;
+                    best_cfg = c->cfg;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->timing = keep_timing;
+    c->cfg = keep;
+    if (r != MM_OK) return r;
+    c->cfg.bin_scale = best_cfg.bin_scale;
+    c->cfg.clip_warps = best_cfg.clip_warps;
+    c->cfg.cand_cap = best_cfg.cand_cap;
+    if (best_ms) *best_ms = best;
     return MM_OK;
 }
 

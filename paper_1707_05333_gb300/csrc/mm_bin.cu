@@ -10,9 +10,9 @@
 
 namespace mm {
 
-__device__ __forceinline__ int bin_coord(double x, double bs, int g)
+__device__ __forceinline__ int bin_coord(double x, double ibs, int g)
 {
-    int c = (int)floor(x / bs);
+    int c = (int)floor(x * ibs);
     return c < 0 ? 0 : (c >= g ? g - 1 : c);
 }
 
@@ -50,8 +50,8 @@ __global__ void k_bin_count(const double *__restrict__ pos, int64_t n, const Box
         atomicExch(&st->bad_cell, (int)i);
         x = y = z = 0.0;
     }
-    int b = g.bin_off + bin_coord(x, g.bs[0], g.g[0]) +
-            g.g[0] * (bin_coord(y, g.bs[1], g.g[1]) + g.g[1] * bin_coord(z, g.bs[2], g.g[2]));
+    int b = g.bin_off + bin_coord(x, g.ibs[0], g.g[0]) +
+            g.g[0] * (bin_coord(y, g.ibs[1], g.g[1]) + g.g[1] * bin_coord(z, g.ibs[2], g.g[2]));
     bin_of[i] = b;
     atomicAdd(&count[b], 1);
 }

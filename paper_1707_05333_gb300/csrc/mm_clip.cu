@@ -24,8 +24,9 @@
 //    from p to the face centroid.
 //
 // Precision.  GB300 issues FP64 at 1/64 of the FP32 rate, and the warp-wide
-// FP64 instruction count bounds this kernel.  PREC 0 solves every vertex in
-// FP64 when it is created and classifies it in FP64.  PREC 1 keeps the
+// FP64 instruction count bounds this kernel.  PREC 0 (clip_filter = 0) solves
+// every vertex in FP64 when it is created and classifies it in FP64.  PREC 1
+// (clip_filter = 1, the default) keeps the
 // vertices in FP32 during clipping together with a forward error bound, and
 // classifies with FP32 where the bound settles the sign; where it does not,
 // it solves that vertex in FP64 and classifies exactly as PREC 0 does.  At the
@@ -266,8 +267,23 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
         anyv |= outm[c];
     }
     if (anyv == 0) return;
-    if (C.np >= PMAX) { C.err |= ST_ECAP_PLANE; return; }
-    const int kp = C.np;
+    // the new plane takes the lowest slot no vertex refers to (a face that has
+    // vanished frees its slot), else a fresh one: PMAX bounds the live faces
+    unsigned long long live = 0ull;
+    for (int t = lane; t < C.nt; t += 32) {
+        const unsigned v = S.tv[t];
+        live |= (1ull << (v & 255u)) | (1ull << ((v >> 8) & 255u)) | (1ull << ((v >> 16) & 255u));
+    }
+    live = warp_or64(live);
+    const unsigned long long used = C.np >= 64 ? ~0ull : ((1ull << C.np) - 1ull);
+    const unsigned long long freeb = used & ~live;
+    int kp;
+    if (freeb) {
+        kp = __ffsll((long long)freeb) - 1;
+    } else {
+        if (C.np >= PMAX) { C.err |= ST_ECAP_PLANE; return; }
+        kp = C.np;
+    }
     if (lane == 0) {
         S.px[kp] = qx; S.py[kp] = qy; S.pz[kp] = qz; S.po[kp] = off;
         S.pnb[kp] = S.cid[k]; S.psh[kp] = S.csh[k];
@@ -390,7 +406,7 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
     __syncwarp();
     if (PREC == 0) C.solve64 += nnew;
     C.nt = nkept + nnew;
-    C.np = kp + 1;
+    C.np = max(C.np, kp + 1);
     C.cuts++;
     update_limit(S, C, lane);
 }
@@ -413,11 +429,11 @@ template <int PREC>
 __global__ void __maxnreg__(128)
 k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, int64_t n,
        const BoxDev *__restrict__ boxes, const int *__restrict__ cbox, double *__restrict__ vol,
-       double *__restrict__ cen, Slots sl, DevStatus *st, int collect)
+       double *__restrict__ cen, Slots sl, DevStatus *st, int collect, int cand_cap)
 {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t w = (int64_t)blockIdx.x * CLIP_WARPS + wid;
+    const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
     if (w >= n) return;
     ClipSmem<PREC> &S = reinterpret_cast<ClipSmem<PREC> *>(dyn_smem)[wid];
     const double4_32a me = sorted[w];
@@ -473,7 +489,7 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
         const double pp[3] = {px, py, pz};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            const int c = (int)floor(pp[d] / g.bs[d]);
+            const int c = (int)floor(pp[d] * g.ibs[d]);  // the binning kernel's formula
             cb[d] = c < 0 ? 0 : (c >= g.g[d] ? g.g[d] - 1 : c);
         }
     }
@@ -524,7 +540,7 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
             const int code = (shx + 1) + 3 * (shy + 1) + 9 * (shz + 1);
             const bool selfimg = (abs(shx) + abs(shy) + abs(shz)) <= 1;
             while (__any_sync(FULL, cur < end)) {
-                if (ncand + 32 > CBATCH) flush_batch<PREC>(S, ncand, C, lane);
+                if (ncand + 32 > cand_cap) flush_batch<PREC>(S, ncand, C, lane);
                 if (C.err) break;
                 bool keep = false;
                 double qx = 0, qy = 0, qz = 0;
@@ -701,23 +717,28 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
 template <int PREC>
 static void launch_clip_t(const double4_32a *sorted, const int *start, int64_t n, const BoxDev *boxes,
                           const int *cbox, double *vol, double *cen, Slots sl, DevStatus *st, int collect,
-                          cudaStream_t s)
+                          int warps, int cand_cap, cudaStream_t s)
 {
-    const size_t smem = sizeof(ClipSmem<PREC>) * CLIP_WARPS;
     static bool configured = false;  // the attribute is per function and process-wide
     if (!configured) {
-        cudaFuncSetAttribute(k_clip<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_clip<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(ClipSmem<PREC>) * CLIP_MAX_WARPS));
         configured = true;
     }
-    const int64_t nb = (n + CLIP_WARPS - 1) / CLIP_WARPS;
-    k_clip<PREC><<<(unsigned)nb, 32 * CLIP_WARPS, smem, s>>>(sorted, start, n, boxes, cbox, vol, cen, sl, st, collect);
+    const size_t smem = sizeof(ClipSmem<PREC>) * warps;
+    const int64_t nb = (n + warps - 1) / warps;
+    k_clip<PREC><<<(unsigned)nb, 32 * warps, smem, s>>>(sorted, start, n, boxes, cbox, vol, cen, sl, st, collect,
+                                                         cand_cap);
 }
 
 void launch_clip(const double4_32a *sorted, const int *start, int64_t n, const BoxDev *boxes, const int *cbox,
-                 int precision, int collect, double *vol, double *cen, Slots sl, DevStatus *st, cudaStream_t s)
+                 int precision, int collect, int warps, int cand_cap, double *vol, double *cen, Slots sl,
+                 DevStatus *st, cudaStream_t s)
 {
-    if (precision == 0) launch_clip_t<0>(sorted, start, n, boxes, cbox, vol, cen, sl, st, collect, s);
-    else launch_clip_t<1>(sorted, start, n, boxes, cbox, vol, cen, sl, st, collect, s);
+    warps = warps < 1 ? 1 : (warps > CLIP_MAX_WARPS ? CLIP_MAX_WARPS : warps);
+    cand_cap = cand_cap < 32 ? 32 : (cand_cap > CBATCH ? CBATCH : cand_cap);
+    if (precision == 0) launch_clip_t<0>(sorted, start, n, boxes, cbox, vol, cen, sl, st, collect, warps, cand_cap, s);
+    else launch_clip_t<1>(sorted, start, n, boxes, cbox, vol, cen, sl, st, collect, warps, cand_cap, s);
 }
 
 }  // namespace mm

@@ -123,14 +123,25 @@ __global__ void __launch_bounds__(128) k_gradient(MeshDev m, HydroCfg c, const d
         for (int k = 0; k < 5; ++k) { dmax[k] = 0.0; dmin[k] = 0.0; rn[k] = 1.0; rd[k] = 1.0; }
         for (int e = e0; e < e1; ++e) {
             const Nbr q = neighbour(m, e, L);
-            const double dx = m.cen[q.o] + q.ox - cix, dy = m.cen[n + q.o] + q.oy - ciy, dz = m.cen[2 * n + q.o] + q.oz - ciz;
+            double dx, dy, dz;
+            if (c.limiter == 3) {
+                // to the face centroid, in this cell's frame (subtract the image offset on the j side)
+                const double sh = q.sg > 0.0 ? 0.0 : 1.0;
+                dx = m.fcen[q.f] + sh * q.ox - cix;
+                dy = m.fcen[m.fs + q.f] + sh * q.oy - ciy;
+                dz = m.fcen[2 * m.fs + q.f] + sh * q.oz - ciz;
+            } else {
+                dx = m.cen[q.o] + q.ox - cix;
+                dy = m.cen[n + q.o] + q.oy - ciy;
+                dz = m.cen[2 * n + q.o] + q.oz - ciz;
+            }
             const double ivo = FROM_CHARGES ? 1.0 / m.vol[q.o] : 1.0;
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
                 const double del = g[3 * k] * dx + g[3 * k + 1] * dy + g[3 * k + 2] * dz;
                 dmax[k] = fmax(dmax[k], del);
                 dmin[k] = fmin(dmin[k], del);
-                if (c.limiter >= 2 && del != 0.0) {
+                if (c.limiter == 2 && del != 0.0) {
                     double num = c.theta * (S[k * n + q.o] * ivo - Wi[k]);
                     double den = del;
                     if (den < 0.0) { num = -num; den = -den; }
@@ -144,7 +155,7 @@ __global__ void __launch_bounds__(128) k_gradient(MeshDev m, HydroCfg c, const d
             double a = 1.0;
             if (dmax[k] > 0.0) a = fmin(a, (wmax[k] - Wi[k]) / dmax[k]);
             if (dmin[k] < 0.0) a = fmin(a, (wmin[k] - Wi[k]) / dmin[k]);
-            if (c.limiter >= 2) a *= fmin(1.0, rn[k] / rd[k]);
+            if (c.limiter == 2) a *= fmin(1.0, rn[k] / rd[k]);
             g[3 * k] *= a;
             g[3 * k + 1] *= a;
             g[3 * k + 2] *= a;
@@ -267,7 +278,7 @@ __global__ void __launch_bounds__(128) k_face_flux(MeshDev m, HydroCfg c, const 
         R.vx = WR[1] * ir - wfx; R.vy = WR[2] * ir - wfy; R.vz = WR[3] * ir - wfz;
     }
     double F[5];
-    hllc_t<double>(L, R, nx, ny, nz, c.gamma, F);
+    riemann_t<double>(c.riemann, L, R, nx, ny, nz, c.gamma, F);
     // back to the lab frame: p -> p + m w, E -> E + p.w + |w|^2/2 m
     const double A = m.area[f];
     const double fm = F[0];

@@ -139,14 +139,26 @@ __global__ void __launch_bounds__(128) k_gradient32(MeshDev m, HydroCfg c, Mixed
             const Nbr32 q = nbr32(m, x, e);
             const float4 fq = x.fq[q.f];
             const float4 o0 = rin[2 * q.o], o1 = rin[2 * q.o + 1];
-            const float dx = q.sg * fq.x + o1.y - dix, dy = q.sg * fq.y + o1.z - diy, dz = q.sg * fq.z + o1.w - diz;
+            float dx, dy, dz;
+            if (c.limiter == 3) {
+                // face centroid relative to this cell's centroid: x_f - r_i - d_i, or x_f - q - r_i - d_j
+                const float2 ff = x.ff[q.f];
+                const float hx = q.sg > 0.0f ? 0.0f : fq.x, hy = q.sg > 0.0f ? 0.0f : fq.y, hz = q.sg > 0.0f ? 0.0f : fq.z;
+                dx = fq.w - hx - dix;
+                dy = ff.x - hy - diy;
+                dz = ff.y - hz - diz;
+            } else {
+                dx = q.sg * fq.x + o1.y - dix;
+                dy = q.sg * fq.y + o1.z - diy;
+                dz = q.sg * fq.z + o1.w - diz;
+            }
             const float Wo[5] = {o0.x, o0.y, o0.z, o0.w, o1.x};
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
                 const float del = g[3 * k] * dx + g[3 * k + 1] * dy + g[3 * k + 2] * dz;
                 dmax[k] = fmaxf(dmax[k], del);
                 dmin[k] = fminf(dmin[k], del);
-                if (c.limiter >= 2 && del != 0.0f) {
+                if (c.limiter == 2 && del != 0.0f) {
                     float num = theta * (Wo[k] - Wi[k]);
                     float den = del;
                     if (den < 0.0f) { num = -num; den = -den; }
@@ -160,7 +172,7 @@ __global__ void __launch_bounds__(128) k_gradient32(MeshDev m, HydroCfg c, Mixed
             float al = 1.0f;
             if (dmax[k] > 0.0f) al = fminf(al, (wmax[k] - Wi[k]) / dmax[k]);
             if (dmin[k] < 0.0f) al = fminf(al, (wmin[k] - Wi[k]) / dmin[k]);
-            if (c.limiter >= 2) al *= fminf(1.0f, rn[k] / rd[k]);
+            if (c.limiter == 2) al *= fminf(1.0f, rn[k] / rd[k]);
             g[3 * k] *= al;
             g[3 * k + 1] *= al;
             g[3 * k + 2] *= al;
@@ -261,7 +273,7 @@ __global__ void __launch_bounds__(128) k_face_flux32(MeshDev m, HydroCfg c, Mixe
         R.vx = WR[1] * ir - wfx; R.vy = WR[2] * ir - wfy; R.vz = WR[3] * ir - wfz;
     }
     float F[5];
-    hllc_t<float>(L, R, fa.y, fa.z, fa.w, gam, F);
+    riemann_t<float>(c.riemann, L, R, fa.y, fa.z, fa.w, gam, F);
     const float A = fa.x, fm = F[0];
     const float fe = F[4] + F[1] * wfx + F[2] * wfy + F[3] * wfz + 0.5f * (wfx * wfx + wfy * wfy + wfz * wfz) * fm;
     x.flux[2 * f] = make_float4(A * fm, A * (F[1] + fm * wfx), A * (F[2] + fm * wfy), A * (F[3] + fm * wfz));

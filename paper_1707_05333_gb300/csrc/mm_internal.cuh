@@ -20,7 +20,7 @@ constexpr int TMAX = 128;   // vertices (triangles of the dual) alive at once
 constexpr int NSTAGE = 32;  // vertices created by one cut
 constexpr int MAXF = 48;    // faces written per cell
 constexpr int MAXRING = 48; // search rings before giving up
-constexpr int CLIP_WARPS = 4;
+constexpr int CLIP_MAX_WARPS = 8;  // warps (cells) per block of the clipper, tunable at run time
 
 // Device status word, read by the host after a tessellation.
 enum : int {
@@ -52,6 +52,7 @@ struct BoxDev {
     int g[3];      // bins per axis
     int bin_off;   // first bin of this box in the global bin array
     double bs[3];  // bin edge per axis
+    double ibs[3]; // 1 / bin edge (bin of x: floor(x * ibs))
     double L[3];   // box size
     double amin;   // faces with area <= amin are dropped
 };
@@ -76,7 +77,8 @@ size_t scan_tmp_size(int64_t n);
 void launch_scan(const int *in, int *out, int64_t n, int *tmp, cudaStream_t s);
 
 void launch_clip(const double4_32a *sorted, const int *start, int64_t n, const BoxDev *boxes, const int *cbox,
-                 int precision, int collect, double *vol, double *cen, Slots sl, DevStatus *st, cudaStream_t s);
+                 int precision, int collect, int warps, int cand_cap, double *vol, double *cen, Slots sl,
+                 DevStatus *st, cudaStream_t s);
 
 void launch_face_confirm(int64_t n, Slots sl, unsigned long long *emit_mask, unsigned long long *conf_mask,
                          signed char *partner, int *emit_cnt, int *conf_cnt, cudaStream_t s);
@@ -101,7 +103,7 @@ struct MeshDev {
 
 struct HydroCfg {
     double gamma, cfl, eta, chi, zeta, theta, rho_floor, eps_floor;
-    int limiter, regularize;
+    int limiter, regularize, riemann;
 };
 
 // FP32 records of the mixed-precision hydro path (see mm_hydro32.cu).

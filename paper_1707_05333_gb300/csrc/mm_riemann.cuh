@@ -61,6 +61,46 @@ __device__ __forceinline__ void hllc_t(const FaceStateT<T> &L, const FaceStateT<
     }
 }
 
+// HLL with the same wave speeds: one intermediate state from the integral
+// form of the conservation laws (no contact wave).
+template <class T>
+__device__ __forceinline__ void hll_t(const FaceStateT<T> &L, const FaceStateT<T> &R, T nx, T ny, T nz, T gamma,
+                                      T F[5])
+{
+    const T gm1 = gamma - T(1);
+    const T ul = L.vx * nx + L.vy * ny + L.vz * nz;
+    const T ur = R.vx * nx + R.vy * ny + R.vz * nz;
+    const T cl = sqrt_t(gamma * L.P / L.rho), cr = sqrt_t(gamma * R.P / R.rho);
+    const T El = L.P / gm1 + T(0.5) * L.rho * (L.vx * L.vx + L.vy * L.vy + L.vz * L.vz);
+    const T Er = R.P / gm1 + T(0.5) * R.rho * (R.vx * R.vx + R.vy * R.vy + R.vz * R.vz);
+    const T sl = min_t(ul - cl, ur - cr);
+    const T sr = max_t(ul + cl, ur + cr);
+    const T ml = L.rho * ul, mr = R.rho * ur;
+    const T Fl[5] = {ml, ml * L.vx + L.P * nx, ml * L.vy + L.P * ny, ml * L.vz + L.P * nz, (El + L.P) * ul};
+    const T Fr[5] = {mr, mr * R.vx + R.P * nx, mr * R.vy + R.P * ny, mr * R.vz + R.P * nz, (Er + R.P) * ur};
+    if (sl >= T(0)) {
+        for (int k = 0; k < 5; ++k) F[k] = Fl[k];
+        return;
+    }
+    if (sr <= T(0)) {
+        for (int k = 0; k < 5; ++k) F[k] = Fr[k];
+        return;
+    }
+    const T Ul[5] = {L.rho, L.rho * L.vx, L.rho * L.vy, L.rho * L.vz, El};
+    const T Ur[5] = {R.rho, R.rho * R.vx, R.rho * R.vy, R.rho * R.vz, Er};
+    const T id = T(1) / (sr - sl);
+    for (int k = 0; k < 5; ++k) F[k] = (sr * Fl[k] - sl * Fr[k] + sl * sr * (Ur[k] - Ul[k])) * id;
+}
+
+// The configured solver: 0 HLLC, 1 HLL.
+template <class T>
+__device__ __forceinline__ void riemann_t(int kind, const FaceStateT<T> &L, const FaceStateT<T> &R, T nx, T ny, T nz,
+                                          T gamma, T F[5])
+{
+    if (kind == 1) hll_t<T>(L, R, nx, ny, nz, gamma, F);
+    else hllc_t<T>(L, R, nx, ny, nz, gamma, F);
+}
+
 // Floors on density and specific internal energy (Sec. 4.1).  A state below
 // the density floor is reset to the floor density at rest with the floor
 // internal energy; otherwise only the internal energy is raised if needed.

@@ -1,0 +1,45 @@
+"""The benchmark's multi-rank path (one replica per rank, slowest rank's time,
+whole-job throughput) with two gloo ranks on the CPU."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    # rank 1 is slower: the job time is its time
+    value, ms = bench.aggregate(100.0 * (rank + 1), cells_per_rank=1000, steps=5, world=world)
+    out[rank] = (value, ms)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_aggregation_uses_slowest_rank():
+    world, port = 2, _free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_rank, args=(world, port, out), nprocs=world, join=True, start_method="spawn")
+    for r in range(world):
+        value, ms = out[r]
+        assert ms == pytest.approx(200.0)
+        assert value == pytest.approx(2 * 1000 * 5 / 0.2)
+
+
+def test_single_rank_aggregation():
+    import bench
+    value, ms = bench.aggregate(50.0, cells_per_rank=10, steps=2, world=1)
+    assert ms == 50.0 and value == pytest.approx(400.0)

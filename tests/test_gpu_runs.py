@@ -64,7 +64,7 @@ def test_point_blast_shock_radius_follows_sedov_taylor(oracle):
     import torch
     from paper_1707_05333_gb300 import binding
     w = WL.point_blast(48)
-    ctx = binding.Context(gamma=w.gamma, cfl=0.3, limiter=1, precision=1)
+    ctx = binding.Context(gamma=w.gamma, cfl=0.3, limiter=1, precision=1, regularize=1)
     P = H.to_dev(torch, w.pos.T)
     mesh = ctx.mm_tessellate(P, w.box)
     U = ctx.mm_prims_to_charges(mesh, H.to_dev(torch, w.rho), H.to_dev(torch, w.vel.T), H.to_dev(torch, w.pres))

@@ -39,7 +39,7 @@ def assert_state_close(G, O, rtol=RTOL_STEP):
         np.testing.assert_allclose(G[k], O[:, k], rtol=rtol, atol=rtol * scale, err_msg=f"component {k}")
 
 
-@pytest.mark.parametrize("limiter", [0, 1, 2])
+@pytest.mark.parametrize("limiter", [0, 1, 2, 3])
 def test_gradients_match_oracle(oracle, gpu, limiter):
     c, torch = gpu
     w = WL.smooth_wave(12)
@@ -64,6 +64,9 @@ CONFIGS = {
     "point_blast_12^3": dict(maker=lambda: WL.point_blast(12), kw=dict(limiter=1)),
     "static_mesh_eta0": dict(maker=lambda: WL.smooth_wave(9), kw=dict(limiter=1, eta=0.0), random=True),
     "no_limiter_ragged_11^3": dict(maker=lambda: WL.smooth_wave(11), kw=dict(limiter=0), random=True),
+    "hll_shock_tube_48x6x6": dict(maker=lambda: WL.shock_tube(48, 6, 6), kw=dict(limiter=1, riemann=1)),
+    "face_centroid_limiter_random": dict(maker=lambda: WL.smooth_wave(10), kw=dict(limiter=3, regularize=1),
+                                         random=True),
 }
 
 

@@ -63,18 +63,18 @@ def test_tessellation_is_deterministic(ctx):
 
 @pytest.mark.parametrize("case", ["random_1001", "smooth_wave_16^3", "fcc_degenerate_vertices",
                                   "cubic_lattice_exact_ties", "shock_tube_64x8x8", "n5"])
-def test_mixed_clipping_gives_the_same_mesh_bit_for_bit(ctx, case):
-    """precision=1 classifies with FP32 plus an error bound and falls back to
+def test_filtered_clipping_gives_the_same_mesh_bit_for_bit(ctx, case):
+    """clip_filter=1 classifies with FP32 plus an error bound and falls back to
     the FP64 test only near ties, and re-solves every final vertex in FP64:
-    the mesh must equal the FP64 path's exactly."""
+    the mesh must equal the direct FP64 clipper's (clip_filter=0) exactly."""
     c, torch = ctx
     pos, box = CASES[case]()
-    _, _, A = H.gpu_tessellate(c, torch, pos, box)
-    c.set_config(precision=1)
+    c.set_config(clip_filter=0)
     try:
-        _, _, B = H.gpu_tessellate(c, torch, pos, box)
+        _, _, A = H.gpu_tessellate(c, torch, pos, box)
     finally:
-        c.set_config(precision=0)
+        c.set_config(clip_filter=1)
+    _, _, B = H.gpu_tessellate(c, torch, pos, box)
     for k in A:
         np.testing.assert_array_equal(A[k], B[k], err_msg=k)
 
@@ -82,15 +82,15 @@ def test_mixed_clipping_gives_the_same_mesh_bit_for_bit(ctx, case):
 def test_counters(ctx):
     c, torch = ctx
     pos = WL.random_points(4000, seed=11)
-    c.set_config(collect_stats=1)
+    c.set_config(collect_stats=1, clip_filter=0)
     try:
         H.gpu_tessellate(c, torch, pos, np.ones(3))
         s0 = c.mm_tess_stats()
-        c.set_config(precision=1)
+        c.set_config(clip_filter=1)
         H.gpu_tessellate(c, torch, pos, np.ones(3))
         s1 = c.mm_tess_stats()
     finally:
-        c.set_config(collect_stats=0, precision=0)
+        c.set_config(collect_stats=0, clip_filter=1)
     assert s0["cuts"] == s1["cuts"] > 10 * 4000
     assert s0["fp64_plane_tests"] > 100 * s1["fp64_plane_tests"]
     assert s0["max_planes"] <= 64 and s0["max_vertices"] <= 128
@@ -144,3 +144,31 @@ def test_full_size_shear_layer_sampled_cells(oracle, ctx):
         for k, a in want.items():
             assert k in got, (ci, k)
             assert abs(got[k] - a) <= 1e-9 * scale
+
+
+@pytest.mark.parametrize("warps,cap,scale", [(2, 32, 0.8), (8, 64, 1.5), (1, 48, 1.25), (4, 64, 2.5)])
+def test_tunable_settings_keep_the_mesh(oracle, ctx, warps, cap, scale):
+    c, torch = ctx
+    pos = WL.random_points(1500, seed=12)
+    T = oracle.tessellate(pos, np.ones(3), 1)
+    c.set_config(clip_warps=warps, cand_cap=cap, bin_scale=scale)
+    try:
+        _, _, G = H.gpu_tessellate(c, torch, pos, np.ones(3))
+    finally:
+        c.set_config(clip_warps=4, cand_cap=64, bin_scale=1.0)
+    H.compare_tessellations(oracle, T, G, pos, np.ones(3))
+    H.check_incidence(G)
+
+
+def test_autotune_picks_a_valid_setting(ctx):
+    c, torch = ctx
+    w = WL.shear_layer(24)
+    P = H.to_dev(torch, w.pos.T)
+    best = c.mm_autotune(P, w.box, reps=1)
+    try:
+        assert best["clip_warps"] in (2, 4, 8) and best["cand_cap"] in (32, 64)
+        assert best["bin_scale"] in (0.8, 1.0, 1.25, 1.5) and best["tessellate_ms"] > 0
+        mesh = c.mm_tessellate(P, w.box)
+        assert mesh.nfaces > 0
+    finally:
+        c.set_config(clip_warps=4, cand_cap=64, bin_scale=1.0)

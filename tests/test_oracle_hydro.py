@@ -408,3 +408,62 @@ def test_sod_tube_converges_to_exact_profile(oracle):
     sel = (x > 1.5) & (x < 6.5)
     l1 = np.mean(np.abs(rho[sel] - r1[sel]))
     assert l1 < 0.03
+
+
+# ---------------------------------------------------------------- HLL option and face-centroid limiter
+def test_hll_consistency_and_symmetry(oracle):
+    rng = np.random.default_rng(41)
+    cfg = oracle.make_cfg(gamma=1.4, riemann=1)
+    for _ in range(10):
+        W = prim_to_W(rng.uniform(0.3, 3), rng.normal(size=3), rng.uniform(0.3, 3), 1.4)
+        W2 = prim_to_W(rng.uniform(0.3, 3), rng.normal(size=3), rng.uniform(0.3, 3), 1.4)
+        n, w = rand_unit(rng), rng.normal(size=3)
+        np.testing.assert_allclose(oracle.riemann_lab(W, W, n, w, cfg),
+                                   oracle.euler_flux(W, n, 1.4) - w.dot(n) * W, rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(oracle.riemann_lab(W, W2, n, w, cfg), -oracle.riemann_lab(W2, W, -n, w, cfg),
+                                   rtol=1e-11, atol=1e-12)
+
+
+def test_hll_smears_a_stationary_contact_by_the_closed_form(oracle):
+    # HLL has no contact wave: the mass flux across a resting contact is
+    # S_L S_R (rho_R - rho_L) / (S_R - S_L), which HLLC does not have
+    g = 1.4
+    rl, rr, p = 1.0, 0.2, 0.7
+    F = oracle.hll_1d([rl, 0, 0, 0, p], [rr, 0, 0, 0, p], g)
+    cl, cr = math.sqrt(g * p / rl), math.sqrt(g * p / rr)
+    sl, sr = -max(cl, cr), max(cl, cr)
+    assert F[0] == pytest.approx(sl * sr * (rr - rl) / (sr - sl), rel=1e-13)
+    assert oracle.hllc_1d([rl, 0, 0, 0, p], [rr, 0, 0, 0, p], g)[0] == pytest.approx(0.0, abs=1e-15)
+
+
+def test_hll_near_godunov_flux_on_sod(oracle):
+    # a loose sanity bound on the Sod data (HLL drifts further from the exact
+    # flux on the 1e5 pressure-ratio problems, as expected of it)
+    (rl, ul, pl, rr, ur, pr), _ = load_toro()[0]
+    F = oracle.hll_1d([rl, ul, 0, 0, pl], [rr, ur, 0, 0, pr], 1.4)
+    G = ER.godunov_flux(rl, ul, pl, rr, ur, pr, 1.4)
+    np.testing.assert_allclose(F[[0, 1, 4]], G, atol=0.3 * np.abs(G).max())
+
+
+def test_supersonic_hll_is_upwind(oracle):
+    cfg = oracle.make_cfg(gamma=1.4, riemann=1)
+    n = np.array([0.0, 1.0, 0.0])
+    WL_ = prim_to_W(1.0, [0.1, 5.0, 0.0], 1.0, 1.4)
+    WR_ = prim_to_W(0.5, [0.0, 4.0, 0.2], 0.8, 1.4)
+    np.testing.assert_allclose(oracle.riemann_lab(WL_, WR_, n, np.zeros(3), cfg), oracle.euler_flux(WL_, n, 1.4),
+                               rtol=1e-14)
+
+
+def test_face_centroid_limiter_zeroes_extrema_and_keeps_uniform(oracle):
+    w, T, F = setup_mesh(oracle, 7)
+    n = w.n
+    rng = np.random.default_rng(9)
+    G = rng.normal(size=(5, 3))
+    W = 2.0 + T["centroid"] @ G.T
+    k = int(np.where(interior_cells(T, F, n))[0][3])
+    W[k] += 10.0
+    g = oracle.gradient(F, T["volume"], T["centroid"], w.box, W, oracle.make_cfg(limiter=3))
+    np.testing.assert_allclose(g[k], 0.0, atol=1e-14)
+    Wu = np.tile([1.0, 0.1, 0.2, 0.3, 2.0], (n, 1))
+    gu = oracle.gradient(F, T["volume"], T["centroid"], w.box, Wu, oracle.make_cfg(limiter=3))
+    np.testing.assert_allclose(gu, 0.0, atol=1e-12)
