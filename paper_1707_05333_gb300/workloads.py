@@ -138,6 +138,44 @@ def shear_layer(n_side=256, jitter=0.1):
                    5.0 / 3.0, 0.3, 20)
 
 
+def gresho_vphi(r):
+    """Tangential velocity of the Gresho-Chan vortex (Sec. 5.3): 5r inside
+    r < 0.2, 2 - 5r on 0.2 <= r < 0.4, zero beyond."""
+    r = np.asarray(r, dtype=np.float64)
+    return np.where(r < 0.2, 5.0 * r, np.where(r < 0.4, 2.0 - 5.0 * r, 0.0))
+
+
+def gresho_pressure(r):
+    """Pressure of the Gresho-Chan vortex (Sec. 5.3): 5 + 12.5 r^2 inside
+    r < 0.2, 9 + 12.5 r^2 - 20 r + 4 ln(5r) on 0.2 <= r < 0.4, 3 + 4 ln 2
+    beyond."""
+    r = np.asarray(r, dtype=np.float64)
+    mid = 9.0 + 12.5 * r * r - 20.0 * r + 4.0 * np.log(np.maximum(5.0 * r, 1e-300))
+    return np.where(r < 0.2, 5.0 + 12.5 * r * r, np.where(r < 0.4, mid, 3.0 + 4.0 * np.log(2.0)))
+
+
+def gresho_vortex(n_side=64, jitter=0.1, gamma=5.0 / 3.0):
+    """Gresho-Chan vortex (Sec. 5.3) in the periodic 1 x 1 x 0.2 box, centred
+    at (0.5, 0.5): rho = 1, v = v_phi(r) e_phi, P(r), run to t = 2.  The
+    lattice is n x n x round(0.2 n), so the equivalent 2-D resolution is n^2
+    (the paper's run: n = 64, about 50K generators).  gamma is not stated
+    for this test; 5/3 as in the other tests."""
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + 1000 + n_side))
+    nz = max(1, int(round(0.2 * n_side)))
+    box = np.array([1.0, 1.0, 0.2])
+    pos = jittered_lattice((n_side, n_side, nz), box, rng, jitter)
+    n = pos.shape[0]
+    dx, dy = pos[:, 0] - 0.5, pos[:, 1] - 0.5
+    r = np.hypot(dx, dy)
+    vphi = gresho_vphi(r)
+    inv = np.where(r > 0, 1.0 / np.maximum(r, 1e-300), 0.0)
+    vel = np.zeros((n, 3))
+    vel[:, 0] = -vphi * dy * inv
+    vel[:, 1] = vphi * dx * inv
+    return _finish(f"gresho_vortex_{n_side}x{n_side}x{nz}", pos, box, np.ones(n), vel, gresho_pressure(r),
+                   gamma, 0.3, 0)
+
+
 def gaussian_random_field(rng, n_grid=64, slope=-3.0):
     """Unit-variance periodic Gaussian random field with power spectrum k^slope."""
     k = np.fft.fftfreq(n_grid) * n_grid
@@ -210,4 +248,5 @@ WORKLOADS = {
     "shock_tube": shock_tube,
     "point_blast": point_blast,
     "shear_layer": shear_layer,
+    "gresho_vortex": gresho_vortex,
 }

@@ -1,6 +1,7 @@
 """Run-level checks of the CUDA path on the paper's test problems (Sec. 5):
-the Sod shock tube against the exact Riemann solution, and the point blast
-against the Sedov-Taylor similarity law."""
+the Sod shock tube against the exact Riemann solution, the point blast
+against the Sedov-Taylor similarity law, and the Gresho-Chan vortex against
+its steady state."""
 import math
 
 import numpy as np
@@ -84,3 +85,43 @@ def test_point_blast_shock_radius_follows_sedov_taylor(oracle):
     assert abs(r_peak - r_st) < 0.15 * r_st
     assert prof.max() > 1.5
     ctx.close()
+
+
+def test_gresho_vortex_error_converges_like_the_paper():
+    """Gresho-Chan vortex (Sec. 5.3) to t = 2 at equivalent 2-D resolutions
+    32^2, 64^2 and 128^2 (1 x 1 x 0.2 box, roundness correction on).  The
+    paper fits L1 ~ N^-0.88 to the tangential-velocity error at the
+    generators; the fitted slope here must show convergence at least as
+    fast as N^-0.5, and the 64^2 error must stay below a tenth of the peak
+    speed."""
+    import torch
+    from paper_1707_05333_gb300 import binding
+    from tests.test_oracle_gresho import gresho_l1
+    l1 = {}
+    for n_side in (32, 64, 128):
+        w = WL.gresho_vortex(n_side)
+        ctx = binding.Context(gamma=w.gamma, cfl=w.cfl, limiter=1, regularize=1)
+        pos = H.to_dev(torch, w.pos.T)
+        mesh = ctx.mm_tessellate(pos, w.box)
+        U = ctx.mm_prims_to_charges(mesh, H.to_dev(torch, w.rho), H.to_dev(torch, w.vel.T), H.to_dev(torch, w.pres))
+        dt_out = torch.empty(1, dtype=torch.float64, device="cuda")
+        dt_fix = torch.empty(1, dtype=torch.float64, device="cuda")
+        t, steps, t_end = 0.0, 0, 2.0
+        while t < t_end - 1e-12:
+            mesh = ctx.mm_tessellate(pos, w.box)
+            wv = ctx.mm_mesh_velocity(mesh, pos, U)
+            dtc = float(ctx.mm_timestep(mesh, U, wv).item())
+            step = min(dtc, t_end - t)
+            dt_fix.fill_(step)
+            ctx.mm_flux_step(mesh, pos, wv, dt_fix, U)
+            ctx.mm_drift(pos, wv, dt_fix, w.box)
+            t += step
+            steps += 1
+        l1[n_side] = gresho_l1(pos.cpu().numpy().T, U.cpu().numpy().T)
+        print(f"Gresho {n_side}^2: {steps} steps to t=2, L1(v_phi) = {l1[n_side]:.4e}")
+        ctx.close()
+    ns = np.array(sorted(l1))
+    slope = np.polyfit(np.log(ns), np.log([l1[k] for k in ns]), 1)[0]
+    print(f"Gresho fitted L1 slope {slope:.2f} (paper: -0.88)")
+    assert slope < -0.5
+    assert l1[64] < 0.1

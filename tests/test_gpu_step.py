@@ -67,6 +67,7 @@ CONFIGS = {
     "hll_shock_tube_48x6x6": dict(maker=lambda: WL.shock_tube(48, 6, 6), kw=dict(limiter=1, riemann=1)),
     "face_centroid_limiter_random": dict(maker=lambda: WL.smooth_wave(10), kw=dict(limiter=3, regularize=1),
                                          random=True),
+    "gresho_vortex_16x16x3_regularized": dict(maker=lambda: WL.gresho_vortex(16), kw=dict(limiter=1, regularize=1)),
 }
 
 
