@@ -643,32 +643,34 @@ static void face_delta(const double *centroid, const double *box, int32_t i, int
     for (int a = 0; a < 3; ++a) d[a] = centroid[3 * j + a] + sh[a] * box[a] - centroid[3 * i + a];
 }
 
-/* 3x3 solve by Gaussian elimination with partial pivoting (rhs: 5 columns). */
-static void solve3(const double *M, const double *B /* [3][5] */, double *X /* [3][5] */)
+/* 3x3 solve by Gaussian elimination with partial pivoting (nc <= 6 rhs columns). */
+static void solve3(const double *M, const double *B /* [3][nc] */, int nc, double *X /* [3][nc] */)
 {
-    double a[3][8];
+    double a[3][9];
     for (int r = 0; r < 3; ++r) {
         for (int c = 0; c < 3; ++c) a[r][c] = M[3 * r + c];
-        for (int c = 0; c < 5; ++c) a[r][3 + c] = B[5 * r + c];
+        for (int c = 0; c < nc; ++c) a[r][3 + c] = B[nc * r + c];
     }
     for (int c = 0; c < 3; ++c) {
         int p = c;
         for (int r = c + 1; r < 3; ++r)
             if (fabs(a[r][c]) > fabs(a[p][c])) p = r;
         if (p != c)
-            for (int k = 0; k < 8; ++k) { double t = a[c][k]; a[c][k] = a[p][k]; a[p][k] = t; }
+            for (int k = 0; k < 3 + nc; ++k) { double t = a[c][k]; a[c][k] = a[p][k]; a[p][k] = t; }
         for (int r = c + 1; r < 3; ++r) {
             double f = a[r][c] / a[c][c];
-            for (int k = c; k < 8; ++k) a[r][k] -= f * a[c][k];
+            for (int k = c; k < 3 + nc; ++k) a[r][k] -= f * a[c][k];
         }
     }
-    for (int c = 0; c < 5; ++c)
+    for (int c = 0; c < nc; ++c)
         for (int r = 2; r >= 0; --r) {
             double s = a[r][3 + c];
-            for (int k = r + 1; k < 3; ++k) s -= a[r][k] * X[5 * k + c];
-            X[5 * r + c] = s / a[r][r];
+            for (int k = r + 1; k < 3; ++k) s -= a[r][k] * X[nc * k + c];
+            X[nc * r + c] = s / a[r][r];
         }
 }
+
+static int state_width(const orc_cfg *cfg) { return cfg->entropy ? 6 : 5; }
 
 /* Cell-centred Green-Gauss gradient: with d_ij the vector between the two
  * cell centroids across face ij (image-corrected), M_i = 1/2 sum A n (x) d and
@@ -677,19 +679,21 @@ static void solve3(const double *M, const double *B /* [3][5] */, double *X /* [
  * (psi from the neighbourhood max/min and Delta_ij = grad . (c_j - c_i)), and
  * optionally the Duffell-MacFadyen factor min(1, max(0, theta (W_j - W_i) /
  * Delta_ij)).  limiter 3 is S10 with Delta_ij measured to the face centroid,
- * grad . (x_f - c_i), as in the original S10 scheme. */
+ * grad . (x_f - c_i), as in the original S10 scheme.  Every state column,
+ * the entropy column included, is treated alike (Sec. 4.3). */
 void orc_gradient(int64_t n, int64_t nf, const int32_t *fi, const int32_t *fj, const int32_t *fshift,
                   const double *farea, const double *fnormal, const double *fcentroid, const double *centroid,
                   const double *box, const double *W, const orc_cfg *cfg, double *grad)
 {
+    const int ng = state_width(cfg);
     double *M = (double *)calloc(9 * n, sizeof(double));
-    double *B = (double *)calloc(15 * n, sizeof(double)); /* [n][3][5] */
-    double *wmax = (double *)malloc(sizeof(double) * 5 * n);
-    double *wmin = (double *)malloc(sizeof(double) * 5 * n);
-    double *psi = (double *)malloc(sizeof(double) * 5 * n);
-    double *psidm = (double *)malloc(sizeof(double) * 5 * n);
-    memcpy(wmax, W, sizeof(double) * 5 * n);
-    memcpy(wmin, W, sizeof(double) * 5 * n);
+    double *B = (double *)calloc(3 * ng * n, sizeof(double)); /* [n][3][ng] */
+    double *wmax = (double *)malloc(sizeof(double) * ng * n);
+    double *wmin = (double *)malloc(sizeof(double) * ng * n);
+    double *psi = (double *)malloc(sizeof(double) * ng * n);
+    double *psidm = (double *)malloc(sizeof(double) * ng * n);
+    memcpy(wmax, W, sizeof(double) * ng * n);
+    memcpy(wmin, W, sizeof(double) * ng * n);
     for (int64_t f = 0; f < nf; ++f) {
         int32_t i = fi[f], j = fj[f];
         double d[3];
@@ -703,25 +707,25 @@ void orc_gradient(int64_t n, int64_t nf, const int32_t *fi, const int32_t *fj, c
                 M[9 * i + 3 * a + b] += v;
                 M[9 * j + 3 * a + b] += v;
             }
-        for (int k = 0; k < 5; ++k) {
-            double dw = W[5 * j + k] - W[5 * i + k];
+        for (int k = 0; k < ng; ++k) {
+            double dw = W[ng * j + k] - W[ng * i + k];
             for (int a = 0; a < 3; ++a) {
-                B[15 * i + 5 * a + k] += 0.5 * A * dw * nr[a];
-                B[15 * j + 5 * a + k] += 0.5 * A * dw * nr[a];
+                B[3 * ng * i + ng * a + k] += 0.5 * A * dw * nr[a];
+                B[3 * ng * j + ng * a + k] += 0.5 * A * dw * nr[a];
             }
-            if (W[5 * j + k] > wmax[5 * i + k]) wmax[5 * i + k] = W[5 * j + k];
-            if (W[5 * j + k] < wmin[5 * i + k]) wmin[5 * i + k] = W[5 * j + k];
-            if (W[5 * i + k] > wmax[5 * j + k]) wmax[5 * j + k] = W[5 * i + k];
-            if (W[5 * i + k] < wmin[5 * j + k]) wmin[5 * j + k] = W[5 * i + k];
+            if (W[ng * j + k] > wmax[ng * i + k]) wmax[ng * i + k] = W[ng * j + k];
+            if (W[ng * j + k] < wmin[ng * i + k]) wmin[ng * i + k] = W[ng * j + k];
+            if (W[ng * i + k] > wmax[ng * j + k]) wmax[ng * j + k] = W[ng * i + k];
+            if (W[ng * i + k] < wmin[ng * j + k]) wmin[ng * j + k] = W[ng * i + k];
         }
     }
     for (int64_t i = 0; i < n; ++i) {
-        double X[15];
-        solve3(M + 9 * i, B + 15 * i, X);
-        for (int k = 0; k < 5; ++k)
-            for (int a = 0; a < 3; ++a) grad[15 * i + 3 * k + a] = X[5 * a + k];
+        double X[18];
+        solve3(M + 9 * i, B + 3 * ng * i, ng, X);
+        for (int k = 0; k < ng; ++k)
+            for (int a = 0; a < 3; ++a) grad[3 * ng * i + 3 * k + a] = X[ng * a + k];
     }
-    for (int64_t t = 0; t < 5 * n; ++t) psi[t] = psidm[t] = 1.0;
+    for (int64_t t = 0; t < ng * n; ++t) psi[t] = psidm[t] = 1.0;
     if (cfg->limiter >= 1) {
         for (int64_t f = 0; f < nf; ++f) {
             int32_t i = fi[f], j = fj[f];
@@ -740,26 +744,26 @@ void orc_gradient(int64_t n, int64_t nf, const int32_t *fi, const int32_t *fj, c
                         dv[a] = sg * d[a];
                     }
                 }
-                for (int k = 0; k < 5; ++k) {
-                    const double *g = grad + 15 * c + 3 * k;
+                for (int k = 0; k < ng; ++k) {
+                    const double *g = grad + 3 * ng * c + 3 * k;
                     double del = g[0] * dv[0] + g[1] * dv[1] + g[2] * dv[2];
                     double p = 1.0;
-                    if (del > 0.0) p = (wmax[5 * c + k] - W[5 * c + k]) / del;
-                    else if (del < 0.0) p = (wmin[5 * c + k] - W[5 * c + k]) / del;
-                    if (p < psi[5 * c + k]) psi[5 * c + k] = p;
+                    if (del > 0.0) p = (wmax[ng * c + k] - W[ng * c + k]) / del;
+                    else if (del < 0.0) p = (wmin[ng * c + k] - W[ng * c + k]) / del;
+                    if (p < psi[ng * c + k]) psi[ng * c + k] = p;
                     if (cfg->limiter == 2 && del != 0.0) {
-                        double pd = cfg->theta * (W[5 * o + k] - W[5 * c + k]) / del;
+                        double pd = cfg->theta * (W[ng * o + k] - W[ng * c + k]) / del;
                         if (pd < 0.0) pd = 0.0;
-                        if (pd < psidm[5 * c + k]) psidm[5 * c + k] = pd;
+                        if (pd < psidm[ng * c + k]) psidm[ng * c + k] = pd;
                     }
                 }
             }
         }
         for (int64_t i = 0; i < n; ++i)
-            for (int k = 0; k < 5; ++k) {
-                double alpha = psi[5 * i + k] < 1.0 ? psi[5 * i + k] : 1.0;
-                if (cfg->limiter == 2) alpha *= (psidm[5 * i + k] < 1.0 ? psidm[5 * i + k] : 1.0);
-                for (int a = 0; a < 3; ++a) grad[15 * i + 3 * k + a] *= alpha;
+            for (int k = 0; k < ng; ++k) {
+                double alpha = psi[ng * i + k] < 1.0 ? psi[ng * i + k] : 1.0;
+                if (cfg->limiter == 2) alpha *= (psidm[ng * i + k] < 1.0 ? psidm[ng * i + k] : 1.0);
+                for (int a = 0; a < 3; ++a) grad[3 * ng * i + 3 * k + a] *= alpha;
             }
     }
     free(M);
@@ -770,19 +774,28 @@ void orc_gradient(int64_t n, int64_t nf, const int32_t *fi, const int32_t *fj, c
     free(psidm);
 }
 
-/* Half-step predictor: dW/dt = -sum_d A_d(W) dW/dx_d, Wh = W + dt/2 dW/dt. */
+/* Half-step predictor: dW/dt = -sum_d A_d(W) dW/dx_d, Wh = W + dt/2 dW/dt.
+ * The entropy column's flux is (rho A) m_d / rho, so its Jacobian row along
+ * d is (-A u_d, A delta_{ld}, 0, u_d) in (rho, m_l, E, rho A). */
 void orc_half_step(int64_t n, const double *W, const double *grad, const orc_cfg *cfg, double dt,
                    double *Wh)
 {
+    const int ng = state_width(cfg);
     for (int64_t i = 0; i < n; ++i) {
-        double rate[5] = {0, 0, 0, 0, 0};
+        const double *Wi = W + ng * i;
+        const double *g = grad + 3 * ng * i;
+        double rate[6] = {0, 0, 0, 0, 0, 0};
         for (int d = 0; d < 3; ++d) {
             double A[25];
-            orc_flux_jacobian(W + 5 * i, d, cfg->gamma, A);
+            orc_flux_jacobian(Wi, d, cfg->gamma, A);
             for (int r = 0; r < 5; ++r)
-                for (int c = 0; c < 5; ++c) rate[r] -= A[5 * r + c] * grad[15 * i + 3 * c + d];
+                for (int c = 0; c < 5; ++c) rate[r] -= A[5 * r + c] * g[3 * c + d];
+            if (ng == 6) {
+                double a = Wi[5] / Wi[0], ud = Wi[1 + d] / Wi[0];
+                rate[5] -= -a * ud * g[d] + a * g[3 * (1 + d) + d] + ud * g[15 + d];
+            }
         }
-        for (int r = 0; r < 5; ++r) Wh[5 * i + r] = W[5 * i + r] + 0.5 * dt * rate[r];
+        for (int r = 0; r < ng; ++r) Wh[ng * i + r] = Wi[r] + 0.5 * dt * rate[r];
     }
 }
 
@@ -858,11 +871,49 @@ static void face_basis(const double *n, double *t1, double *t2)
     cross3(n, t1, t2);
 }
 
+/* Contact speed S* and star pressure P* of the HLLC model: Davis wave speeds,
+ * S* from the jump conditions across the outer waves, and P* from the left
+ * wave's jump condition (the right one gives the same value). */
+void orc_star_state(const double *L, const double *R, double gamma, double *sl, double *ss, double *sr,
+                    double *pstar)
+{
+    double rl = L[0], ul = L[1], pl = L[4];
+    double rr = R[0], ur = R[1], pr = R[4];
+    double cl = sqrt(gamma * pl / rl), cr = sqrt(gamma * pr / rr);
+    *sl = fmin(ul - cl, ur - cr);
+    *sr = fmax(ul + cl, ur + cr);
+    *ss = (pr - pl + rl * ul * (*sl - ul) - rr * ur * (*sr - ur)) / (rl * (*sl - ul) - rr * (*sr - ur));
+    *pstar = pl + rl * (*sl - ul) * (*ss - ul);
+}
+
+/* Mach number of a shock that raises the pressure of the gas it runs into
+ * from P to P_star (Rankine-Hugoniot): M^2 = 1 + (gamma+1)/(2 gamma) (P_star / P - 1).
+ * The face's value is the larger over the two sides, 0 if neither is
+ * compressed (Sec. 4.3 reading). */
+double orc_shock_mach(const double *L, const double *R, double gamma)
+{
+    double sl, ss, sr, ps;
+    orc_star_state(L, R, gamma, &sl, &ss, &sr, &ps);
+    double m = 0.0;
+    const double *side[2] = {L, R};
+    for (int s = 0; s < 2; ++s) {
+        double p = side[s][4];
+        if (ps > p) {
+            double mk = sqrt(1.0 + (gamma + 1.0) / (2.0 * gamma) * (ps / p - 1.0));
+            if (mk > m) m = mk;
+        }
+    }
+    return m;
+}
+
 /* Boost both per-volume states into the frame of a face moving at wface,
  * rotate so that x lies along the normal (i -> j), solve, rotate back and
- * boost the flux back into the lab frame. */
+ * boost the flux back into the lab frame.  With the entropy column, rho A is
+ * a passive scalar: its flux is A of the upwind side times the mass flux
+ * (HLLC: the side of the contact; HLL: the HLL average of rho A), and it is
+ * unchanged by the boost; the face's shock Mach number goes to *mach. */
 void orc_riemann_lab(const double *WL, const double *WR, const double *nrm, const double *wf,
-                     const orc_cfg *cfg, double *F)
+                     const orc_cfg *cfg, double *F, double *mach)
 {
     double g = cfg->gamma;
     double t1[3], t2[3];
@@ -891,6 +942,20 @@ void orc_riemann_lab(const double *WL, const double *WR, const double *nrm, cons
     F[0] = fm;
     for (int d = 0; d < 3; ++d) F[1 + d] = fp[d] + fm * wf[d];
     F[4] = Fp[4] + dot3(fp, wf) + 0.5 * dot3(wf, wf) * fm;
+    if (cfg->entropy) {
+        double al = WL[5] / WL[0], ar = WR[5] / WR[0];
+        double sl, ss, sr, pst;
+        orc_star_state(pl, pr, g, &sl, &ss, &sr, &pst);
+        if (cfg->riemann == 1) {
+            double fl = pl[0] * pl[1] * al, fr = pr[0] * pr[1] * ar;
+            if (sl >= 0.0) F[5] = fl;
+            else if (sr <= 0.0) F[5] = fr;
+            else F[5] = (sr * fl - sl * fr + sl * sr * (WR[5] - WL[5])) / (sr - sl);
+        } else {
+            F[5] = fm * ((sl >= 0.0 || ss >= 0.0) ? al : ar);
+        }
+    }
+    if (mach) *mach = orc_shock_mach(pl, pr, g);
 }
 
 /* Face velocity (Sec. 4): mean of the two generator velocities plus the
@@ -913,9 +978,10 @@ void orc_face_flux(int64_t n, int64_t nf, const int32_t *fi, const int32_t *fj, 
                    const double *farea, const double *fnormal, const double *fcentroid,
                    const double *pos, const double *centroid, const double *box,
                    const double *Wh, const double *grad, const double *w, const orc_cfg *cfg,
-                   double *flux)
+                   double *flux, double *mach, double *vrate)
 {
     (void)n;
+    const int ng = state_width(cfg);
     for (int64_t f = 0; f < nf; ++f) {
         int32_t i = fi[f], j = fj[f];
         const int32_t *sh = fshift + 3 * f;
@@ -926,46 +992,107 @@ void orc_face_flux(int64_t n, int64_t nf, const int32_t *fi, const int32_t *fj, 
             cj[d] = centroid[3 * j + d] + sh[d] * box[d];
             rj[d] = pos[3 * j + d] + sh[d] * box[d];
         }
-        double WL[5], WR[5], WLf[5], WRf[5];
-        for (int k = 0; k < 5; ++k) {
-            WL[k] = Wh[5 * i + k];
-            WR[k] = Wh[5 * j + k];
+        double WL[6], WR[6], WLf[6], WRf[6];
+        for (int k = 0; k < ng; ++k) {
+            WL[k] = Wh[ng * i + k];
+            WR[k] = Wh[ng * j + k];
             for (int d = 0; d < 3; ++d) {
-                WL[k] += (fc[d] - ci[d]) * grad[15 * i + 3 * k + d];
-                WR[k] += (fc[d] - cj[d]) * grad[15 * j + 3 * k + d];
+                WL[k] += (fc[d] - ci[d]) * grad[3 * ng * i + 3 * k + d];
+                WR[k] += (fc[d] - cj[d]) * grad[3 * ng * j + 3 * k + d];
             }
         }
         orc_floor_state(WL, cfg, WLf, 0);
         orc_floor_state(WR, cfg, WRf, 0);
+        if (ng == 6) {
+            /* rho A at the face: a state reset to the density floor takes the
+             * floor state's own A; otherwise the reconstruction, not below 0 */
+            double *in[2] = {WL, WR}, *out[2] = {WLf, WRf};
+            for (int s2 = 0; s2 < 2; ++s2) {
+                if (!(in[s2][0] >= cfg->rho_floor)) {
+                    double rf = cfg->rho_floor;
+                    out[s2][5] = rf * (cfg->gamma - 1.0) * rf * cfg->eps_floor / pow(rf, cfg->gamma);
+                } else {
+                    out[s2][5] = in[s2][5] > 0.0 ? in[s2][5] : 0.0;
+                }
+            }
+        }
         double wf[3];
         face_velocity(pos + 3 * i, rj, w + 3 * i, w + 3 * j, fc, wf);
-        double F[5];
-        orc_riemann_lab(WLf, WRf, fnormal + 3 * f, wf, cfg, F);
-        for (int k = 0; k < 5; ++k) flux[5 * f + k] = farea[f] * F[k];
+        double F[6], m = 0.0;
+        orc_riemann_lab(WLf, WRf, fnormal + 3 * f, wf, cfg, F, &m);
+        for (int k = 0; k < ng; ++k) flux[ng * f + k] = farea[f] * F[k];
+        if (mach) mach[f] = m;
+        /* rate at which the moving face sweeps volume out of cell i */
+        if (vrate) vrate[f] = farea[f] * dot3(wf, fnormal + 3 * f);
     }
 }
 
 /* U_i <- U_i - dt sum_{faces of i} (+/-) A F: the face flux is along the
- * normal from i to j, so it leaves i and enters j.  Then the cell floors. */
+ * normal from i to j, so it leaves i and enters j.  Then the cell floors.
+ *
+ * With the entropy column (Sec. 4.3), a cell whose largest face shock Mach
+ * number is below mach_th takes its internal energy from the entropy,
+ * E = |p|^2/(2m) + A rho^gamma V' / (gamma - 1); elsewhere the energy is kept
+ * and the entropy reset from it, as is any state the floors change.  Both
+ * conversions need the cell's density at the end of the step: V' = V + dt
+ * sum_f (+/-) A_f (w_f . n_f) is the volume the moving faces sweep the cell
+ * to (the cell's true new volume is known only after the next
+ * tessellation). */
 void orc_update(int64_t n, int64_t nf, const int32_t *fi, const int32_t *fj, const double *flux,
-                double dt, const double *volume, const orc_cfg *cfg, double *U)
+                const double *mach, const double *vrate, double dt, const double *volume, const orc_cfg *cfg,
+                double *U)
 {
-    double *acc = (double *)calloc(5 * n, sizeof(double));
-    for (int64_t f = 0; f < nf; ++f)
-        for (int k = 0; k < 5; ++k) {
-            acc[5 * fi[f] + k] += flux[5 * f + k];
-            acc[5 * fj[f] + k] -= flux[5 * f + k];
+    const int ng = state_width(cfg);
+    const double g = cfg->gamma;
+    double *acc = (double *)calloc(ng * n, sizeof(double));
+    double *mc = (double *)calloc(n, sizeof(double));
+    double *dv = (double *)calloc(n, sizeof(double));
+    for (int64_t f = 0; f < nf; ++f) {
+        for (int k = 0; k < ng; ++k) {
+            acc[ng * fi[f] + k] += flux[ng * f + k];
+            acc[ng * fj[f] + k] -= flux[ng * f + k];
         }
+        if (ng == 6) {
+            if (mach[f] > mc[fi[f]]) mc[fi[f]] = mach[f];
+            if (mach[f] > mc[fj[f]]) mc[fj[f]] = mach[f];
+            dv[fi[f]] += vrate[f];
+            dv[fj[f]] -= vrate[f];
+        }
+    }
     for (int64_t i = 0; i < n; ++i) {
-        for (int k = 0; k < 5; ++k) U[5 * i + k] -= dt * acc[5 * i + k];
+        double *u = U + ng * i;
+        const double V = volume[i];
+        for (int k = 0; k < ng; ++k) u[k] -= dt * acc[ng * i + k];
+        int energy = 1;
+        const double Vn = V + dt * dv[i];
+        if (ng == 6) {
+            energy = mc[i] >= cfg->mach_th;
+            if (!energy) {
+                if (u[0] > 0.0 && u[5] > 0.0 && Vn > 0.0) {
+                    double rho = u[0] / Vn;
+                    double P = (u[5] / u[0]) * pow(rho, g);
+                    u[4] = 0.5 * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) / u[0] + P * Vn / (g - 1.0);
+                } else {
+                    energy = 1;
+                }
+            }
+        }
         double W[5], Wf[5];
         int ch = 0;
-        for (int k = 0; k < 5; ++k) W[k] = U[5 * i + k] / volume[i];
+        for (int k = 0; k < 5; ++k) W[k] = u[k] / V;
         orc_floor_state(W, cfg, Wf, &ch);
         if (ch)
-            for (int k = 0; k < 5; ++k) U[5 * i + k] = Wf[k] * volume[i];
+            for (int k = 0; k < 5; ++k) u[k] = Wf[k] * V;
+        if (ng == 6 && (energy || ch)) {
+            double Vr = Vn > 0.0 ? Vn : V;
+            double rho = u[0] / Vr;
+            double P = (g - 1.0) * (u[4] - 0.5 * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) / u[0]) / Vr;
+            u[5] = u[0] * P / pow(rho, g);
+        }
     }
     free(acc);
+    free(mc);
+    free(dv);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -985,8 +1112,9 @@ static double eff_radius(double V) { return cbrt(3.0 * V / (4.0 * M_PI)); }
 void orc_mesh_velocity(int64_t n, const double *pos, const double *U, const double *volume,
                        const double *centroid, const orc_cfg *cfg, double *w)
 {
+    const int ng = state_width(cfg);
     for (int64_t i = 0; i < n; ++i) {
-        const double *u = U + 5 * i;
+        const double *u = U + ng * i;
         for (int d = 0; d < 3; ++d) w[3 * i + d] = cfg->eta * u[1 + d] / u[0];
         if (!cfg->regularize) continue;
         double dv[3];
@@ -1008,9 +1136,10 @@ void orc_mesh_velocity(int64_t n, const double *pos, const double *U, const doub
 double orc_timestep(int64_t n, const double *U, const double *volume, const double *w,
                     const orc_cfg *cfg)
 {
+    const int ng = state_width(cfg);
     double dt = INFINITY;
     for (int64_t i = 0; i < n; ++i) {
-        const double *u = U + 5 * i;
+        const double *u = U + ng * i;
         double cs = sound_speed(u, volume[i], cfg->gamma);
         double rel[3];
         for (int d = 0; d < 3; ++d) rel[d] = u[1 + d] / u[0] - w[3 * i + d];

@@ -4,8 +4,9 @@
  * call this code; only the tests, the smoke check and the CPU-baseline leg of
  * the benchmark do.  It shares no code with the CUDA library.
  *
- * Layouts are array-of-structs: pos[n][3], W[n][5] = (rho, rho v, rho e),
- * grad[n][5][3] (component-major, then x,y,z).  Faces are either "directed"
+ * Layouts are array-of-structs: pos[n][3], W[n][ng] = (rho, rho v, rho e
+ * [, rho A]) with ng = 5, or 6 when the entropy column is on (cfg.entropy),
+ * grad[n][ng][3] (component-major, then x,y,z).  Faces are either "directed"
  * (every face of every cell, seen from that cell) or "unique" (one record per
  * shared face, i<j, or i==j with a positive image shift).
  */
@@ -24,8 +25,13 @@ typedef struct {
     int limiter;       /* 0 none, 1 S10, 2 S10 then Duffell-MacFadyen, 3 S10 to face centroids */
     int regularize;    /* 1: add the roundness correction to the mesh velocity            */
     int riemann;       /* 0 HLLC, 1 HLL (Sec. 4)                                         */
-    int pad;
+    int entropy;       /* 1: sixth state column rho A, A = P / rho^gamma, and the switch  */
+                       /*    between energy and entropy per cell (Sec. 4.3)               */
+    double mach_th;    /* energy equation where the cell's largest shock Mach number is   */
+                       /* at least mach_th, entropy equation elsewhere (1.1 in the paper) */
 } orc_cfg;
+
+/* States: per cell ng = 5 + entropy values, array of structs (n, ng). */
 
 /* Voronoi tessellation of the periodic box by clipping (Sec. 3).
  * mode 0: brute force over all generators and their 27 images.
@@ -62,10 +68,11 @@ void orc_face_flux(int64_t n, int64_t nf, const int32_t *fi, const int32_t *fj, 
                    const double *farea, const double *fnormal, const double *fcentroid,
                    const double *pos, const double *centroid, const double *box,
                    const double *Wh, const double *grad, const double *w, const orc_cfg *cfg,
-                   double *flux);
+                   double *flux, double *mach /* [nf] or NULL */, double *vrate /* [nf] or NULL */);
 
 /* Charge update U_i <- U_i - dt sum_j Phi_ij, then cell floors (Sec. 4, 4.1). */
 void orc_update(int64_t n, int64_t nf, const int32_t *fi, const int32_t *fj, const double *flux,
+                const double *mach /* [nf], used with entropy */, const double *vrate /* [nf], idem */,
                 double dt, const double *volume, const orc_cfg *cfg, double *U);
 
 /* Mesh-generator velocity w = eta v (+ roundness correction) (Sec. 4.2). */
@@ -86,7 +93,12 @@ void orc_flux_jacobian(const double *W, int d, double gamma, double *A /* [5][5]
 /* Lab-frame face flux of two per-volume states across a face with unit
  * normal nrm moving at wface (boost, rotate, HLLC, rotate back, boost back). */
 void orc_riemann_lab(const double *WL, const double *WR, const double *nrm, const double *wface,
-                     const orc_cfg *cfg, double *F);
+                     const orc_cfg *cfg, double *F, double *mach /* or NULL */);
+/* Contact speed and star pressure of the HLLC model (Davis wave speeds). */
+void orc_star_state(const double *primL, const double *primR, double gamma, double *sl, double *ss,
+                    double *sr, double *pstar);
+/* Largest Mach number of a shock running into either side (0 if none). */
+double orc_shock_mach(const double *primL, const double *primR, double gamma);
 /* One-dimensional HLLC flux in the face frame: prim = (rho, u, v1, v2, P). */
 void orc_hllc_1d(const double *primL, const double *primR, double gamma, double *F);
 /* One-dimensional HLL flux with the same wave speeds. */

@@ -7,7 +7,8 @@ tessellate -> charges to states -> mesh velocity and CFL timestep ->
 limited gradient and half step -> limited half-step gradient -> face fluxes
 in the face frame -> charge update -> drift.
 
-Arrays are array-of-structs float64: pos (n,3), W and U (n,5), grad (n,5,3).
+Arrays are array-of-structs float64: pos (n,3), W and U (n,ng), grad (n,ng,3),
+with ng = 5, or 6 when the entropy column rho A (A = P / rho^gamma) is on.
 """
 from __future__ import annotations
 
@@ -46,12 +47,19 @@ class Cfg(ctypes.Structure):
                 ("chi", ctypes.c_double), ("zeta", ctypes.c_double), ("theta", ctypes.c_double),
                 ("rho_floor", ctypes.c_double), ("eps_floor", ctypes.c_double),
                 ("limiter", ctypes.c_int), ("regularize", ctypes.c_int), ("riemann", ctypes.c_int),
-                ("pad", ctypes.c_int)]
+                ("entropy", ctypes.c_int), ("mach_th", ctypes.c_double)]
 
 
 def make_cfg(gamma=5.0 / 3.0, cfl=0.3, eta=1.0, chi=1.0, zeta=0.25, theta=0.49,
-             rho_floor=1e-10, eps_floor=1e-10, limiter=1, regularize=0, riemann=0) -> Cfg:
-    return Cfg(gamma, cfl, eta, chi, zeta, theta, rho_floor, eps_floor, limiter, regularize, riemann, 0)
+             rho_floor=1e-10, eps_floor=1e-10, limiter=1, regularize=0, riemann=0, entropy=0,
+             mach_th=1.1) -> Cfg:
+    return Cfg(gamma, cfl, eta, chi, zeta, theta, rho_floor, eps_floor, limiter, regularize, riemann, entropy,
+               mach_th)
+
+
+def width(cfg) -> int:
+    """State components per cell: 5, or 6 with the entropy column."""
+    return 6 if cfg.entropy else 5
 
 
 _P = ctypes.c_void_p
@@ -72,8 +80,8 @@ def lib():
             L.orc_gradient.argtypes = [_I64, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
             L.orc_half_step.argtypes = [_I64, _P, _P, _P, ctypes.c_double, _P]
             L.orc_face_flux.argtypes = [_I64, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
-                                        _P, _P]
-            L.orc_update.argtypes = [_I64, _I64, _P, _P, _P, ctypes.c_double, _P, _P, _P]
+                                        _P, _P, _P, _P]
+            L.orc_update.argtypes = [_I64, _I64, _P, _P, _P, _P, _P, ctypes.c_double, _P, _P, _P]
             L.orc_mesh_velocity.argtypes = [_I64, _P, _P, _P, _P, _P, _P]
             L.orc_timestep.argtypes = [_I64, _P, _P, _P, _P]
             L.orc_timestep.restype = ctypes.c_double
@@ -81,7 +89,10 @@ def lib():
             L.orc_floor_state.argtypes = [_P, _P, _P, _P]
             L.orc_euler_flux.argtypes = [_P, _P, ctypes.c_double, _P]
             L.orc_flux_jacobian.argtypes = [_P, ctypes.c_int, ctypes.c_double, _P]
-            L.orc_riemann_lab.argtypes = [_P, _P, _P, _P, _P, _P]
+            L.orc_riemann_lab.argtypes = [_P, _P, _P, _P, _P, _P, _P]
+            L.orc_star_state.argtypes = [_P, _P, ctypes.c_double, _P, _P, _P, _P]
+            L.orc_shock_mach.argtypes = [_P, _P, ctypes.c_double]
+            L.orc_shock_mach.restype = ctypes.c_double
             L.orc_hllc_1d.argtypes = [_P, _P, ctypes.c_double, _P]
             L.orc_hll_1d.argtypes = [_P, _P, ctypes.c_double, _P]
             _lib = L
@@ -152,22 +163,28 @@ def unique_faces(T):
                 centroid=T["fcentroid"][keep].copy())
 
 
-def charges_from_prims(volume, rho, vel, pres, gamma, e_add=None):
-    """U = W V with W = (rho, rho v, P/(gamma-1) + rho v^2/2) (Sec. 4)."""
+def charges_from_prims(volume, rho, vel, pres, gamma, e_add=None, entropy=False):
+    """U = W V with W = (rho, rho v, P/(gamma-1) + rho v^2/2) (Sec. 4), plus
+    rho A with A = P / rho^gamma when the entropy column is on (Sec. 4.3; an
+    energy deposit e_add raises P accordingly)."""
     vol = np.asarray(volume)
-    W = np.zeros((vol.shape[0], 5))
+    W = np.zeros((vol.shape[0], 6 if entropy else 5))
     W[:, 0] = rho
     W[:, 1:4] = rho[:, None] * vel
     W[:, 4] = pres / (gamma - 1.0) + 0.5 * rho * np.sum(vel * vel, axis=1)
     U = W * vol[:, None]
     if e_add is not None:
         U[:, 4] += e_add
+    if entropy:
+        P = pres + (0.0 if e_add is None else (gamma - 1.0) * np.asarray(e_add) / vol)
+        U[:, 5] = U[:, 0] * P / np.power(np.asarray(rho, dtype=np.float64), gamma)
     return U
 
 
 def gradient(F, volume, centroid, box, W, cfg):
     n = W.shape[0]
-    grad = np.zeros((n, 5, 3))
+    assert W.shape[1] == width(cfg)
+    grad = np.zeros((n, width(cfg), 3))
     fi, fj, sh = _c(F["i"], np.int32), _c(F["j"], np.int32), _c(F["shift"], np.int32)
     area, nrm, fc = _c(F["area"]), _c(F["normal"]), _c(F["centroid"])
     cen, box, W = _c(centroid), _c(box), _c(W)
@@ -183,22 +200,30 @@ def half_step(W, grad, cfg, dt):
     return Wh
 
 
-def face_flux(F, pos, centroid, box, Wh, grad, w, cfg):
+def face_flux(F, pos, centroid, box, Wh, grad, w, cfg, return_aux=False):
+    """Face fluxes A F (nf, ng); with return_aux also (shock Mach number,
+    swept-volume rate A w_f . n) per face."""
     nf = F["i"].shape[0]
-    flux = np.zeros((nf, 5))
+    flux = np.zeros((nf, width(cfg)))
+    mach = np.zeros(nf)
+    vrate = np.zeros(nf)
     fi, fj, sh = _c(F["i"], np.int32), _c(F["j"], np.int32), _c(F["shift"], np.int32)
     area, nrm, fc = _c(F["area"]), _c(F["normal"]), _c(F["centroid"])
     pos, cen, box, Wh, grad, w = _c(pos), _c(centroid), _c(box), _c(Wh), _c(grad), _c(w)
     lib().orc_face_flux(Wh.shape[0], nf, _p(fi), _p(fj), _p(sh), _p(area), _p(nrm), _p(fc), _p(pos),
-                        _p(cen), _p(box), _p(Wh), _p(grad), _p(w), ctypes.byref(cfg), _p(flux))
-    return flux
+                        _p(cen), _p(box), _p(Wh), _p(grad), _p(w), ctypes.byref(cfg), _p(flux), _p(mach),
+                        _p(vrate))
+    return (flux, dict(mach=mach, vrate=vrate)) if return_aux else flux
 
 
-def update(F, flux, dt, volume, cfg, U):
+def update(F, flux, dt, volume, cfg, U, aux=None):
     U = _c(U).copy()
     fi, fj = _c(F["i"], np.int32), _c(F["j"], np.int32)
     flux, vol = _c(flux), _c(volume)
-    lib().orc_update(U.shape[0], fi.shape[0], _p(fi), _p(fj), _p(flux), float(dt), _p(vol),
+    z = np.zeros(fi.shape[0])
+    mach = _c(z if aux is None else aux["mach"])
+    vrate = _c(z if aux is None else aux["vrate"])
+    lib().orc_update(U.shape[0], fi.shape[0], _p(fi), _p(fj), _p(flux), _p(mach), _p(vrate), float(dt), _p(vol),
                      ctypes.byref(cfg), _p(U))
     return U
 
@@ -244,11 +269,25 @@ def flux_jacobian(W, d, gamma):
     return A
 
 
-def riemann_lab(WL, WR, nrm, wface, cfg):
+def riemann_lab(WL, WR, nrm, wface, cfg, return_mach=False):
     WL, WR, nrm, wface = _c(WL), _c(WR), _c(nrm), _c(wface)
-    F = np.zeros(5)
-    lib().orc_riemann_lab(_p(WL), _p(WR), _p(nrm), _p(wface), ctypes.byref(cfg), _p(F))
-    return F
+    F = np.zeros(width(cfg))
+    m = ctypes.c_double(0.0)
+    lib().orc_riemann_lab(_p(WL), _p(WR), _p(nrm), _p(wface), ctypes.byref(cfg), _p(F), ctypes.byref(m))
+    return (F, m.value) if return_mach else F
+
+
+def star_state(primL, primR, gamma):
+    """(S_L, S*, S_R, P*) of the HLLC model for 1-D states (rho, u, v1, v2, P)."""
+    L, R = _c(primL), _c(primR)
+    out = [ctypes.c_double() for _ in range(4)]
+    lib().orc_star_state(_p(L), _p(R), float(gamma), *[ctypes.byref(o) for o in out])
+    return tuple(o.value for o in out)
+
+
+def shock_mach(primL, primR, gamma):
+    L, R = _c(primL), _c(primR)
+    return lib().orc_shock_mach(_p(L), _p(R), float(gamma))
 
 
 def hll_1d(primL, primR, gamma):
@@ -279,8 +318,8 @@ def step(pos, U, box, cfg, mode=1, dt=None, tess=None):
     g0 = gradient(F, vol, cen, box, W, cfg)
     Wh = half_step(W, g0, cfg, dt)
     g1 = gradient(F, vol, cen, box, Wh, cfg)
-    flux = face_flux(F, pos, cen, box, Wh, g1, w, cfg)
-    U1 = update(F, flux, dt, vol, cfg, U)
+    flux, aux = face_flux(F, pos, cen, box, Wh, g1, w, cfg, return_aux=True)
+    U1 = update(F, flux, dt, vol, cfg, U, aux)
     pos1 = drift(pos, w, dt, box)
     return dict(tess=T, faces=F, W=W, w=w, dt=dt, dt_cfl=dt_cfl, grad0=g0, Wh=Wh, grad1=g1,
-                flux=flux, U=U1, pos=pos1)
+                flux=flux, mach=aux["mach"], vrate=aux["vrate"], U=U1, pos=pos1)
