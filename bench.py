@@ -47,7 +47,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-variants", action="store_true",
-                   help="skip the mixed-precision and batched-ensemble measurements")
+                   help="skip the variant measurements (mixed precision, direct FP64 clipping, entropy "
+                        "switch, Heun integration, batched ensemble)")
     p.add_argument("--ensemble-boxes", type=int, default=512)
     return p.parse_args()
 
@@ -114,11 +115,12 @@ def clocks_stop(proc, path):
 # this pool measured 1.19 TFLOP/s at 1.995 GHz, consistent with 2 lanes/SM).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
-# Algorithmic FP64 flops per unit of clipping work: a plane test q.v > o
+# Algorithmic flops per unit of clipping work: a plane test q.v > o
 # (2 FMA + 1 MUL -> 5 flops), a three-plane solve (3 cross products, the
 # determinant, the reciprocal and the scaled numerators -> 51 flops), and a
-# face-fan term of the area/centroid sums (33 flops).
-FLOPS_PLANE_TEST, FLOPS_SOLVE, FLOPS_FAN = 5, 51, 33
+# face-fan term of the area/centroid sums in the face's own plane (two
+# offsets, a 2-D cross product, three weighted sums -> 12 flops).
+FLOPS_PLANE_TEST, FLOPS_SOLVE, FLOPS_FAN = 5, 51, 12
 # FP32 lanes: 128 per SM per clock, so one FP32 flop costs 1/64 of an FP64
 # flop of issue time on this part.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -256,44 +258,43 @@ def time_steps(torch, stream, fn, steps):
     return e0.elapsed_time(e1)
 
 
-def measure_mixed_single(args, w):
-    """The mixed-precision path on the same workload (same bench protocol)."""
+def measure_variant(args, w, steps, dtype, note, **cfg):
+    """One configuration of the step on the same workload and protocol
+    (warm-up steps, then `steps` timed steps with CUDA events)."""
     import torch
     from paper_1707_05333_gb300 import binding as BD
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        ctx = BD.Context(stream=stream, gamma=w.gamma, cfl=w.cfl, limiter=1, precision=1)
+        ctx = BD.Context(stream=stream, gamma=w.gamma, cfl=w.cfl, limiter=1, **cfg)
         pos = torch.tensor(w.pos.T.copy(), dtype=torch.float64, device="cuda")
         mesh = ctx.mm_tessellate(pos, w.box)
         U = ctx.mm_prims_to_charges(mesh, torch.tensor(w.rho, device="cuda"), torch.tensor(w.vel.T.copy(), device="cuda"),
                                     torch.tensor(w.pres, device="cuda"))
         for _ in range(args.warmup):
             ctx.mm_step(pos, U, w.box)
-        ms = time_steps(torch, stream, lambda: ctx.mm_step(pos, U, w.box), args.steps)
-        ctx.close()
-    return {"value": w.n * args.steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
-            "dtype": "f64+f32", "note": "FP32 gradients/half step/fluxes, FP64 clipping decisions, geometry and update"}
-
-
-def measure_direct_clip(args, w):
-    """FP64 hydro with the direct FP64 clipper (every vertex solved and tested
-    in FP64): the same mesh bit for bit as the filtered clipper, slower."""
-    import torch
-    from paper_1707_05333_gb300 import binding as BD
-    stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream):
-        ctx = BD.Context(stream=stream, gamma=w.gamma, cfl=w.cfl, limiter=1, precision=0, clip_filter=0)
-        pos = torch.tensor(w.pos.T.copy(), dtype=torch.float64, device="cuda")
-        mesh = ctx.mm_tessellate(pos, w.box)
-        U = ctx.mm_prims_to_charges(mesh, torch.tensor(w.rho, device="cuda"), torch.tensor(w.vel.T.copy(), device="cuda"),
-                                    torch.tensor(w.pres, device="cuda"))
-        for _ in range(args.warmup):
-            ctx.mm_step(pos, U, w.box)
-        steps = max(2, args.steps // 2)
         ms = time_steps(torch, stream, lambda: ctx.mm_step(pos, U, w.box), steps)
         ctx.close()
-    return {"value": w.n * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "dtype": "f64",
-            "note": "clip_filter=0: every clipping vertex solved and tested in FP64 as it appears"}
+    return {"value": w.n * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+            "dtype": dtype, "note": note}
+
+
+def measure_variants(args, w):
+    half = max(2, args.steps // 2)
+    return {
+        "mixed_same_workload": measure_variant(
+            args, w, args.steps, "f64+f32", "FP32 gradients/half step/fluxes, FP64 clipping decisions, geometry "
+            "and update", precision=1),
+        "direct_fp64_clip_same_workload": measure_variant(
+            args, w, half, "f64", "clip_filter=0: every clipping vertex solved and tested in FP64 as it appears",
+            clip_filter=0),
+        "entropy_switch_same_workload": measure_variant(
+            args, w, half, "f64", "sixth state column rho A and the energy/entropy switch at Mach 1.1",
+            entropy=1, mach_th=1.1),
+        "heun_same_workload": measure_variant(
+            args, w, half, "f64", "Heun time integration: two flux stages, second tessellation per step",
+            integrator=1),
+        "batched_ensemble": measure_ensemble(args),
+    }
 
 
 def measure_ensemble(args):
@@ -456,9 +457,7 @@ def run_ours(args, world, rank, local):
 
     variants = None
     if rank == 0 and not args.no_variants:
-        variants = {"mixed_same_workload": measure_mixed_single(args, w),
-                    "direct_fp64_clip_same_workload": measure_direct_clip(args, w),
-                    "batched_ensemble": measure_ensemble(args)}
+        variants = measure_variants(args, w)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

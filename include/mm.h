@@ -15,7 +15,9 @@
  *    arrays, float64: positions pos[3][n] (x row, y row, z row), charges
  *    U[5][n] = (mass, momentum x,y,z, total energy) per cell, per-volume
  *    states W[5][n] = U / V, velocities w[3][n], gradients grad[15][n] with
- *    row 3*k+d holding d(W_k)/dx_d.  n >= 1 and n <= MM_MAX_CELLS.
+ *    row 3*k+d holding d(W_k)/dx_d.  n >= 1 and n <= MM_MAX_CELLS.  With
+ *    cfg.entropy = 1 the charges and states have a sixth row (m A and
+ *    rho A, A = P / rho^gamma) and the gradients 18 rows.
  *  - Positions must lie in [0, box[d]); generators must be distinct.
  *  - Every call is enqueued on the context's stream and returns without
  *    waiting, except mm_tessellate and mm_step, which wait once for the
@@ -70,13 +72,21 @@ typedef struct {
                       /*    an exact FP64 test near ties, then FP64 vertices (same mesh, bit */
                       /*    for bit); 0: solve and test every vertex in FP64 as it appears  */
     double bin_scale; /* neighbour-search bin edge in mean generator spacings (tunable)       */
+    double mach_th;   /* energy/entropy switch: a cell whose largest face shock Mach number   */
+                      /*    is below mach_th takes its energy from its entropy (Sec. 4.3)     */
+    int entropy;      /* 1: charges carry a sixth row m A, A = P / rho^gamma, and the switch  */
+                      /*    applies (FP64 hydro only); 0: five rows, energy equation only    */
+    int integrator;   /* 0: half-step predictor with start-of-step geometry (Sec. 4.1);      */
+                      /*    1: Heun, fluxes averaged over start and end meshes (Sec. 6; FP64 */
+                      /*    hydro, no entropy column; one more tessellation per step)        */
 } mm_config;
 
 /* Fill a config with the defaults: gamma 5/3, cfl 0.3, eta 1, chi 1, zeta
  * 0.25, theta 0.49, floors 1e-10, area_rel 1e-10, S10 limiter, no
  * roundness correction, FP64 hydro, filtered clipping, no counters, HLLC,
  * 4 clip warps per block, batches of 64 candidates, bins one mean spacing
- * wide. */
+ * wide, no entropy column (mach_th 1.1 when it is switched on), half-step
+ * time integration. */
 void mm_default_config(mm_config *cfg);
 
 typedef struct mm_ctx mm_ctx;
@@ -146,7 +156,10 @@ mm_status mm_timestep(mm_ctx *ctx, const mm_mesh *mesh, const double *U, const d
  * gradient of W^n, half step W^(n+1/2) = W^n - dt/2 sum_d A_d dW/dx_d, its
  * gradient, reconstruction to face centroids, floors, boost into the frame
  * of each moving face, HLLC, boost back, and U_i -= dt sum_faces (+-) A F
- * (Sec. 4, 4.1).  dt is a DEVICE pointer to one double (e.g. from
+ * (Sec. 4, 4.1).  With cfg.entropy the sixth row is advected as a passive
+ * scalar and each cell keeps the energy equation only where its largest face
+ * shock Mach number reaches cfg.mach_th, else takes E from its entropy
+ * (Sec. 4.3).  dt is a DEVICE pointer to one double (e.g. from
  * mm_timestep).  pos[3][n] are the generator positions the mesh was built
  * from; w[3][n] the generator velocities. */
 mm_status mm_flux_step(mm_ctx *ctx, const mm_mesh *mesh, const double *pos, const double *w,
@@ -198,7 +211,8 @@ mm_status mm_sync_status(mm_ctx *ctx);
 mm_status mm_current_mesh(mm_ctx *ctx, mm_mesh *out);
 
 /* Charges from per-volume primitives on the current mesh:
- * U = (rho, rho v, P/(gamma-1) + rho |v|^2 / 2) V.  rho[n], vel[3][n], P[n]. */
+ * U = (rho, rho v, P/(gamma-1) + rho |v|^2 / 2) V, and with cfg.entropy the
+ * sixth row rho V P / rho^gamma.  rho[n], vel[3][n], P[n]. */
 mm_status mm_prims_to_charges(mm_ctx *ctx, const mm_mesh *mesh, const double *rho, const double *vel,
                               const double *P, double *U);
 

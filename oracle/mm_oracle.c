@@ -1095,6 +1095,25 @@ void orc_update(int64_t n, int64_t nf, const int32_t *fi, const int32_t *fj, con
     free(dv);
 }
 
+/* Heun's method for dU/dt = R(U, r(t)) with the generators on straight paths:
+ * U* = U^n + dt R(U^n, r^n), U** = U* + dt R(U*, r^(n+1)), and
+ * U^(n+1) = (U^n + U**) / 2 = U^n + dt/2 (R(U^n, r^n) + R(U*, r^(n+1))),
+ * the average of the fluxes at the start and the end of the step. */
+void orc_heun_average(int64_t n, const double *U0, const double *volume, const orc_cfg *cfg, double *U)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double W[5], Wf[5];
+        int ch = 0;
+        for (int k = 0; k < 5; ++k) {
+            U[5 * i + k] = 0.5 * (U0[5 * i + k] + U[5 * i + k]);
+            W[k] = U[5 * i + k] / volume[i];
+        }
+        orc_floor_state(W, cfg, Wf, &ch);
+        if (ch)
+            for (int k = 0; k < 5; ++k) U[5 * i + k] = Wf[k] * volume[i];
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Mesh velocity, timestep, drift (Sec. 4.2)                                 */
 /* ------------------------------------------------------------------------ */

@@ -99,6 +99,10 @@ void orc_star_state(const double *primL, const double *primR, double gamma, doub
                     double *sr, double *pstar);
 /* Largest Mach number of a shock running into either side (0 if none). */
 double orc_shock_mach(const double *primL, const double *primR, double gamma);
+
+/* Heun combination (Sec. 6, second-order time integration): U <- (U0 + U)/2
+ * for every cell, then the cell floors with the given volumes. */
+void orc_heun_average(int64_t n, const double *U0, const double *volume, const orc_cfg *cfg, double *U);
 /* One-dimensional HLLC flux in the face frame: prim = (rho, u, v1, v2, P). */
 void orc_hllc_1d(const double *primL, const double *primR, double gamma, double *F);
 /* One-dimensional HLL flux with the same wave speeds. */

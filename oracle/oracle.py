@@ -90,6 +90,7 @@ def lib():
             L.orc_euler_flux.argtypes = [_P, _P, ctypes.c_double, _P]
             L.orc_flux_jacobian.argtypes = [_P, ctypes.c_int, ctypes.c_double, _P]
             L.orc_riemann_lab.argtypes = [_P, _P, _P, _P, _P, _P, _P]
+            L.orc_heun_average.argtypes = [_I64, _P, _P, _P, _P]
             L.orc_star_state.argtypes = [_P, _P, ctypes.c_double, _P, _P, _P, _P]
             L.orc_shock_mach.argtypes = [_P, _P, ctypes.c_double]
             L.orc_shock_mach.restype = ctypes.c_double
@@ -304,14 +305,15 @@ def hllc_1d(primL, primR, gamma):
     return F
 
 
-def step(pos, U, box, cfg, mode=1, dt=None, tess=None):
-    """One step of the moving-mesh method (Sec. 2), returning every stage."""
+def step(pos, U, box, cfg, mode=1, dt=None, tess=None, w=None):
+    """One step of the moving-mesh method (Sec. 2), returning every stage.
+    w, if given, prescribes the generator velocities instead of Sec. 4.2's."""
     pos = _c(pos)
     T = tess if tess is not None else tessellate(pos, box, mode)
     F = unique_faces(T)
     vol, cen = T["volume"], T["centroid"]
     W = U / vol[:, None]
-    w = mesh_velocity(pos, U, vol, cen, cfg)
+    w = mesh_velocity(pos, U, vol, cen, cfg) if w is None else _c(w)
     dt_cfl = timestep(U, vol, w, cfg)
     if dt is None:
         dt = dt_cfl
@@ -323,3 +325,44 @@ def step(pos, U, box, cfg, mode=1, dt=None, tess=None):
     pos1 = drift(pos, w, dt, box)
     return dict(tess=T, faces=F, W=W, w=w, dt=dt, dt_cfl=dt_cfl, grad0=g0, Wh=Wh, grad1=g1,
                 flux=flux, mach=aux["mach"], vrate=aux["vrate"], U=U1, pos=pos1)
+
+
+def heun_average(U0, U, volume, cfg):
+    U0, vol = _c(U0), _c(volume)
+    U = _c(U).copy()
+    lib().orc_heun_average(U.shape[0], _p(U0), _p(vol), ctypes.byref(cfg), _p(U))
+    return U
+
+
+def stage(F, pos, vol, cen, box, U, w, dt, cfg):
+    """One forward-Euler stage of Heun's method on a fixed mesh: limited
+    gradient of W = U / V, reconstruction in space only (no half step),
+    face fluxes with the generators moving at w, and the charge update."""
+    W = U / vol[:, None]
+    g = gradient(F, vol, cen, box, W, cfg)
+    flux = face_flux(F, pos, cen, box, W, g, w, cfg)
+    return update(F, flux, dt, vol, cfg, U)
+
+
+def step_heun(pos, U, box, cfg, mode=1, dt=None, tess=None, w=None):
+    """Second-order time integration by Heun's method (Sec. 6, future item
+    "true second order time integration"): fluxes at the start of the step
+    on the start mesh and at its end on the mesh of the drifted generators
+    are averaged.  The generators move at their start velocity w throughout
+    (Sec. 4.2's, or the one given)."""
+    assert not cfg.entropy, "the entropy switch is defined for the half-step scheme only"
+    pos = _c(pos)
+    T0 = tess if tess is not None else tessellate(pos, box, mode)
+    F0 = unique_faces(T0)
+    vol0, cen0 = T0["volume"], T0["centroid"]
+    w = mesh_velocity(pos, U, vol0, cen0, cfg) if w is None else _c(w)
+    dt_cfl = timestep(U, vol0, w, cfg)
+    if dt is None:
+        dt = dt_cfl
+    U1 = stage(F0, pos, vol0, cen0, box, U, w, dt, cfg)
+    pos1 = drift(pos, w, dt, box)
+    T1 = tessellate(pos1, box, mode)
+    F1 = unique_faces(T1)
+    U2 = stage(F1, pos1, T1["volume"], T1["centroid"], box, U1, w, dt, cfg)
+    U3 = heun_average(U, U2, T1["volume"], cfg)
+    return dict(tess=T0, tess1=T1, w=w, dt=dt, dt_cfl=dt_cfl, U1=U1, U2=U2, U=U3, pos=pos1)

@@ -6,7 +6,8 @@ into exceptions.  There is no fallback: without the built library (see
 ``build.py``) and a CUDA device, every call raises.
 
 Layouts follow the C ABI: positions (3, n), charges and per-volume states
-(5, n), velocities (3, n), gradients (15, n); all float64, contiguous, on the
+(5, n) or (6, n) with the entropy column, velocities (3, n), gradients (15, n)
+or (18, n); all float64, contiguous, on the
 context's device.
 """
 from __future__ import annotations
@@ -43,7 +44,8 @@ class Config(ctypes.Structure):
                 ("area_rel", ctypes.c_double), ("limiter", ctypes.c_int), ("regularize", ctypes.c_int),
                 ("precision", ctypes.c_int), ("collect_stats", ctypes.c_int),
                 ("riemann", ctypes.c_int), ("clip_warps", ctypes.c_int), ("cand_cap", ctypes.c_int),
-                ("clip_filter", ctypes.c_int), ("bin_scale", ctypes.c_double)]
+                ("clip_filter", ctypes.c_int), ("bin_scale", ctypes.c_double),
+                ("mach_th", ctypes.c_double), ("entropy", ctypes.c_int), ("integrator", ctypes.c_int)]
 
 
 class MeshStruct(ctypes.Structure):
@@ -243,26 +245,31 @@ class Context:
         self._call("mm_tessellate", self.h, _ptr(pos, (3, n)), n, b, ctypes.byref(s))
         return Mesh(self, s)
 
+    @property
+    def ng(self) -> int:
+        """Rows of the charges: 5, or 6 with the entropy column."""
+        return 6 if self.config.entropy else 5
+
     def mm_gradients(self, mesh: Mesh, W: torch.Tensor) -> torch.Tensor:
-        grad = torch.empty((15, mesh.n), dtype=torch.float64, device=self.device)
-        self._call("mm_gradients", self.h, ctypes.byref(mesh.s), _ptr(W, (5, mesh.n)), _ptr(grad))
+        grad = torch.empty((3 * self.ng, mesh.n), dtype=torch.float64, device=self.device)
+        self._call("mm_gradients", self.h, ctypes.byref(mesh.s), _ptr(W, (self.ng, mesh.n)), _ptr(grad))
         return grad
 
     def mm_mesh_velocity(self, mesh: Mesh, pos, U) -> torch.Tensor:
         w = torch.empty((3, mesh.n), dtype=torch.float64, device=self.device)
         self._call("mm_mesh_velocity", self.h, ctypes.byref(mesh.s), _ptr(pos, (3, mesh.n)),
-                   _ptr(U, (5, mesh.n)), _ptr(w))
+                   _ptr(U, (self.ng, mesh.n)), _ptr(w))
         return w
 
     def mm_timestep(self, mesh: Mesh, U, w) -> torch.Tensor:
         dt = torch.empty((1,), dtype=torch.float64, device=self.device)
-        self._call("mm_timestep", self.h, ctypes.byref(mesh.s), _ptr(U, (5, mesh.n)), _ptr(w, (3, mesh.n)),
+        self._call("mm_timestep", self.h, ctypes.byref(mesh.s), _ptr(U, (self.ng, mesh.n)), _ptr(w, (3, mesh.n)),
                    _ptr(dt))
         return dt
 
     def mm_flux_step(self, mesh: Mesh, pos, w, dt: torch.Tensor, U: torch.Tensor) -> None:
         self._call("mm_flux_step", self.h, ctypes.byref(mesh.s), _ptr(pos, (3, mesh.n)), _ptr(w, (3, mesh.n)),
-                   _ptr(dt, (1,)), _ptr(U, (5, mesh.n)))
+                   _ptr(dt, (1,)), _ptr(U, (self.ng, mesh.n)))
 
     def mm_drift(self, pos, w, dt: torch.Tensor, box) -> None:
         n = pos.shape[1]
@@ -272,7 +279,7 @@ class Context:
     def mm_step(self, pos, U, box, dt_fixed: torch.Tensor | None = None, dt_out=None, w_out=None):
         n = pos.shape[1]
         b = (ctypes.c_double * 3)(*[float(x) for x in box])
-        self._call("mm_step", self.h, _ptr(pos, (3, n)), _ptr(U, (5, n)), n, b,
+        self._call("mm_step", self.h, _ptr(pos, (3, n)), _ptr(U, (self.ng, n)), n, b,
                    _ptr(dt_fixed, (1,)), _ptr(dt_out, (1,)), _ptr(w_out, (3, n)))
 
     def mm_step_batched(self, pos, U, box_off, boxes, dt_out=None):
@@ -284,7 +291,7 @@ class Context:
         bx = _np.ascontiguousarray(boxes, dtype=_np.float64).reshape(-1)
         nbox = len(off) - 1
         self._keep = (off, bx)
-        self._call("mm_step_batched", self.h, _ptr(pos, (3, n)), _ptr(U, (5, n)), n,
+        self._call("mm_step_batched", self.h, _ptr(pos, (3, n)), _ptr(U, (self.ng, n)), n,
                    off.ctypes.data_as(ctypes.POINTER(_c_i64)), bx.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                    nbox, _ptr(dt_out, (nbox,)))
 
@@ -313,7 +320,7 @@ class Context:
         return Mesh(self, s)
 
     def mm_prims_to_charges(self, mesh: Mesh, rho, vel, P) -> torch.Tensor:
-        U = torch.empty((5, mesh.n), dtype=torch.float64, device=self.device)
+        U = torch.empty((self.ng, mesh.n), dtype=torch.float64, device=self.device)
         self._call("mm_prims_to_charges", self.h, ctypes.byref(mesh.s), _ptr(rho, (mesh.n,)),
                    _ptr(vel, (3, mesh.n)), _ptr(P, (mesh.n,)), _ptr(U))
         return U
@@ -321,7 +328,7 @@ class Context:
     def mm_totals(self, U) -> torch.Tensor:
         n = U.shape[1]
         out = torch.empty((5,), dtype=torch.float64, device=self.device)
-        self._call("mm_totals", self.h, _ptr(U, (5, n)), n, _ptr(out))
+        self._call("mm_totals", self.h, _ptr(U, (U.shape[0], n)), n, _ptr(out))
         return out
 
     def mm_set_timing(self, on: bool) -> None:

@@ -66,6 +66,7 @@ struct mm_ctx {
     Buf face_i, face_j, face_shift, face_area, face_normal, face_cen, inc_face;
     // hydro scratch
     Buf Wh, grad, flux, w_int, dt_int, tot_partial, drift_box, drift_cbox;
+    Buf heun_U0;  // start-of-step charges of a Heun step
     // mixed-precision records
     Buf x_fij, x_fa, x_fq, x_ff, x_cw, x_ch, x_grad, x_wv, x_flux;
     DevStatus *st = nullptr;        // device
@@ -180,6 +181,8 @@ static HydroCfg hydro_cfg(const mm_config &g)
     h.limiter = g.limiter;
     h.regularize = g.regularize;
     h.riemann = g.riemann;
+    h.entropy = g.entropy;
+    h.mach_th = g.mach_th;
     return h;
 }
 
@@ -189,6 +192,13 @@ static mm_status check_cfg(mm_ctx *c, const mm_config *g)
     if (!(g->gamma > 1.0) || !std::isfinite(g->gamma)) return fail(c, MM_EINVAL, "gamma must be > 1");
     if (!(g->cfl > 0.0)) return fail(c, MM_EINVAL, "cfl must be > 0");
     if (g->limiter < 0 || g->limiter > 3) return fail(c, MM_EINVAL, "limiter must be 0, 1, 2 or 3");
+    if (g->entropy != 0 && g->entropy != 1) return fail(c, MM_EINVAL, "entropy must be 0 or 1");
+    if (g->entropy && g->precision != 0)
+        return fail(c, MM_EINVAL, "the entropy column needs the FP64 hydro path (precision 0)");
+    if (g->entropy && !(g->mach_th >= 0.0)) return fail(c, MM_EINVAL, "mach_th must be >= 0");
+    if (g->integrator != 0 && g->integrator != 1) return fail(c, MM_EINVAL, "integrator must be 0 or 1");
+    if (g->integrator == 1 && (g->precision != 0 || g->entropy))
+        return fail(c, MM_EINVAL, "Heun integration needs FP64 hydro without the entropy column");
     if (g->riemann < 0 || g->riemann > 1) return fail(c, MM_EINVAL, "riemann must be 0 (HLLC) or 1 (HLL)");
     if (g->precision < 0 || g->precision > 1) return fail(c, MM_EINVAL, "precision must be 0 or 1");
     if (!(g->rho_floor > 0.0) || !(g->eps_floor >= 0.0)) return fail(c, MM_EINVAL, "floors must be positive");
@@ -469,8 +479,11 @@ static mm_status ensure_hydro(mm_ctx *c, int64_t n, int64_t fs)
             (r = ensure(c, c->x_wv, n * sizeof(float4))))
             return r;
     } else {
-        if ((r = ensure(c, c->Wh, 5 * n * sizeof(double))) || (r = ensure(c, c->grad, 15 * n * sizeof(double))) ||
-            (r = ensure(c, c->flux, 5 * F * sizeof(double))))
+        // with the entropy column: 6 state rows, and 8 flux rows (the entropy
+        // flux, each face's shock Mach number and its swept-volume rate)
+        const int64_t ng = c->cfg.entropy ? 6 : 5, nfr = c->cfg.entropy ? 8 : 5;
+        if ((r = ensure(c, c->Wh, ng * n * sizeof(double))) || (r = ensure(c, c->grad, 3 * ng * n * sizeof(double))) ||
+            (r = ensure(c, c->flux, nfr * F * sizeof(double))))
             return r;
     }
     return MM_OK;
@@ -507,9 +520,37 @@ static mm_status hydro_enqueue(mm_ctx *c, const MeshDev &m, const double *pos, c
     return MM_OK;
 }
 
+// One forward-Euler stage of Heun's method on mesh m: states W = U / V, their
+// limited gradient, face fluxes reconstructed in space only, and the update.
+static mm_status heun_stage(mm_ctx *c, const MeshDev &m, const double *pos, const double *w, const double *dt,
+                            double *U)
+{
+    HydroCfg h = hydro_cfg(c->cfg);
+    cudaStream_t s = c->stream;
+    stage_mark(c, MM_STAGE_GRADIENT_HALF, true);
+    launch_states(m, h, U, P<double>(c->Wh), s);
+    stage_mark(c, MM_STAGE_GRADIENT_HALF, false);
+    stage_mark(c, MM_STAGE_GRADIENT, true);
+    launch_gradient(m, h, P<double>(c->Wh), false, P<double>(c->grad), nullptr, nullptr, s);
+    stage_mark(c, MM_STAGE_GRADIENT, false);
+    stage_mark(c, MM_STAGE_FACE_FLUX, true);
+    launch_face_flux(m, h, pos, w, P<double>(c->Wh), P<double>(c->grad), P<double>(c->flux), s);
+    stage_mark(c, MM_STAGE_FACE_FLUX, false);
+    stage_mark(c, MM_STAGE_UPDATE, true);
+    launch_update(m, h, P<double>(c->flux), dt, U, s);
+    stage_mark(c, MM_STAGE_UPDATE, false);
+    CKLAUNCH();
+    c->launches += 4;
+    return MM_OK;
+}
+
 // Mesh velocity + per-box CFL timestep (or a copy of the fixed dt), the flux
-// step and the drift, on the mesh of the last tessellation.
-static mm_status step_rest(mm_ctx *c, double *pos, double *U, const double *dt_fixed, double *w, double *dt)
+// step and the drift, on the mesh of the last tessellation.  With
+// integrator 1 (Heun): stage 1 on the start mesh, drift, a second
+// tessellation, stage 2 on the end mesh with the same generator velocities,
+// and the average of the start and stage-2 charges.
+static mm_status step_rest(mm_ctx *c, double *pos, double *U, const double *dt_fixed, double *w, double *dt,
+                           bool fixed)
 {
     const MeshDev m = c->mesh;
     HydroCfg h = hydro_cfg(c->cfg);
@@ -527,12 +568,28 @@ static mm_status step_rest(mm_ctx *c, double *pos, double *U, const double *dt_f
     }
     stage_mark(c, MM_STAGE_MESH_VELOCITY, false);
     CKLAUNCH();
-    if ((r = hydro_enqueue(c, m, pos, w, dt, U))) return r;
+    if (c->cfg.integrator == 1) {
+        const size_t ubytes = sizeof(double) * 5 * (size_t)m.n;
+        if ((r = ensure(c, c->heun_U0, ubytes))) return r;
+        CK(cudaMemcpyAsync(c->heun_U0.p, U, ubytes, cudaMemcpyDeviceToDevice, s));
+        if ((r = heun_stage(c, m, pos, w, dt, U))) return r;
+    } else if ((r = hydro_enqueue(c, m, pos, w, dt, U))) {
+        return r;
+    }
     stage_mark(c, MM_STAGE_DRIFT, true);
     launch_drift(pos, m.n, w, dt, m.cbox, m.boxL, s);
     stage_mark(c, MM_STAGE_DRIFT, false);
     CKLAUNCH();
     c->launches += 1;
+    if (c->cfg.integrator == 1) {
+        if ((r = tess_enqueue(c, pos, fixed))) return r;
+        if (!fixed && (r = ensure_hydro(c, c->mesh.n, c->mesh.fs))) return r;
+        const MeshDev m1 = c->mesh;
+        if ((r = heun_stage(c, m1, pos, w, dt, U))) return r;
+        launch_heun_average(m1, h, P<double>(c->heun_U0), U, s);
+        CKLAUNCH();
+        c->launches += 1;
+    }
     return MM_OK;
 }
 
@@ -567,6 +624,9 @@ void mm_default_config(mm_config *g)
     g->cand_cap = 64;
     g->clip_filter = 1;
     g->bin_scale = 1.0;
+    g->mach_th = 1.1;
+    g->entropy = 0;
+    g->integrator = 0;
 }
 
 mm_status mm_create(mm_ctx **out, const mm_config *cfg, void *cuda_stream)
@@ -605,7 +665,7 @@ void mm_destroy(mm_ctx *c)
                    &c->face_off, &c->inc_off, &c->face_i, &c->face_j, &c->face_shift, &c->face_area,
                    &c->face_normal, &c->face_cen, &c->inc_face, &c->Wh, &c->grad, &c->flux, &c->w_int, &c->dt_int,
                    &c->tot_partial, &c->drift_box, &c->drift_cbox, &c->x_fij, &c->x_fa, &c->x_fq, &c->x_ff,
-                   &c->x_cw, &c->x_ch, &c->x_grad, &c->x_wv, &c->x_flux};
+                   &c->x_cw, &c->x_ch, &c->x_grad, &c->x_wv, &c->x_flux, &c->heun_U0};
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
@@ -735,7 +795,7 @@ mm_status mm_step(mm_ctx *c, double *pos, double *U, int64_t n, const double box
         return r;
     double *w = w_out ? w_out : P<double>(c->w_int);
     double *dt = dt_out ? dt_out : P<double>(c->dt_int);
-    return step_rest(c, pos, U, dt_fixed, w, dt);
+    return step_rest(c, pos, U, dt_fixed, w, dt, false);
 }
 
 mm_status mm_step_batched(mm_ctx *c, double *pos, double *U, int64_t n, const int64_t *box_off, const double *boxes,
@@ -770,6 +830,8 @@ mm_status mm_step_batched(mm_ctx *c, double *pos, double *U, int64_t n, const in
         if ((r = ensure_faces(c, fcap, icap)) || (r = ensure_hydro(c, n, c->fcap)) ||
             (r = ensure(c, c->w_int, 3 * n * sizeof(double))) || (r = ensure(c, c->dt_int, sizeof(double) * nbox)))
             return r;
+        // nothing may be allocated while the stream is being captured
+        if (c->cfg.integrator == 1 && (r = ensure(c, c->heun_U0, sizeof(double) * 5 * (size_t)n))) return r;
         CK(cudaStreamSynchronize(c->stream));
         const int64_t l0 = c->launches;
         c->capturing = true;
@@ -780,7 +842,7 @@ mm_status mm_step_batched(mm_ctx *c, double *pos, double *U, int64_t n, const in
         }
         double *dt = P<double>(c->dt_int);
         r = tess_enqueue(c, pos, true);
-        if (r == MM_OK) r = step_rest(c, pos, U, nullptr, P<double>(c->w_int), dt);
+        if (r == MM_OK) r = step_rest(c, pos, U, nullptr, P<double>(c->w_int), dt, true);
         if (r == MM_OK && dt_out) {
             e = cudaMemcpyAsync(dt_out, dt, sizeof(double) * nbox, cudaMemcpyDeviceToDevice, c->stream);
             if (e != cudaSuccess) r = fail(c, MM_ECUDA, "dt copy: %s", cudaGetErrorString(e));

@@ -41,10 +41,15 @@ __device__ __forceinline__ Nbr neighbour(const MeshDev &m, int e, const double *
     return r;
 }
 
-__device__ __forceinline__ void load5(const double *S, int64_t n, int64_t i, double inv_v, double w[5])
+template <int NG>
+__device__ __forceinline__ void loadw(const double *S, int64_t n, int64_t i, double inv_v, double w[NG])
 {
 #pragma unroll
-    for (int k = 0; k < 5; ++k) w[k] = S[k * n + i] * inv_v;
+    for (int k = 0; k < NG; ++k) w[k] = S[k * n + i] * inv_v;
+}
+__device__ __forceinline__ void load5(const double *S, int64_t n, int64_t i, double inv_v, double w[5])
+{
+    loadw<5>(S, n, i, inv_v, w);
 }
 
 __device__ __forceinline__ bool apply_floor(double W[5], double rho_floor, double eps_floor)
@@ -55,7 +60,9 @@ __device__ __forceinline__ bool apply_floor(double W[5], double rho_floor, doubl
 // ---------------------------------------------------------------------------
 // Gradient + limiter (+ half-step predictor when PREDICT)
 // ---------------------------------------------------------------------------
-template <bool FROM_CHARGES, bool PREDICT>
+// NG = 5 state columns, or 6 with the entropy column rho A (Sec. 4.3), which
+// is treated like the others and advected in the predictor.
+template <bool FROM_CHARGES, bool PREDICT, int NG>
 __global__ void __launch_bounds__(128) k_gradient(MeshDev m, HydroCfg c, const double *__restrict__ S,
                                                   double *__restrict__ grad, double *__restrict__ Wh,
                                                   const double *__restrict__ dtp)
@@ -64,20 +71,20 @@ __global__ void __launch_bounds__(128) k_gradient(MeshDev m, HydroCfg c, const d
     const int64_t n = m.n;
     if (i >= n) return;
     const double ivi = FROM_CHARGES ? 1.0 / m.vol[i] : 1.0;
-    double Wi[5];
-    load5(S, n, i, ivi, Wi);
+    double Wi[NG];
+    loadw<NG>(S, n, i, ivi, Wi);
     const double cix = m.cen[i], ciy = m.cen[n + i], ciz = m.cen[2 * n + i];
     const int e0 = m.inc_off[i], e1 = m.inc_off[i + 1];
     const double *L = m.boxL + 3 * m.cbox[i];
 
     // M = 1/2 sum A n (x) d,  b_k = 1/2 sum A (W_o - W_i)_k n
     double M[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    double b[15];
-    double wmax[5], wmin[5];
+    double b[3 * NG];
+    double wmax[NG], wmin[NG];
 #pragma unroll
-    for (int k = 0; k < 5; ++k) { wmax[k] = Wi[k]; wmin[k] = Wi[k]; }
+    for (int k = 0; k < NG; ++k) { wmax[k] = Wi[k]; wmin[k] = Wi[k]; }
 #pragma unroll
-    for (int k = 0; k < 15; ++k) b[k] = 0.0;
+    for (int k = 0; k < 3 * NG; ++k) b[k] = 0.0;
     for (int e = e0; e < e1; ++e) {
         const Nbr q = neighbour(m, e, L);
         const double ha = 0.5 * m.area[q.f];
@@ -89,7 +96,7 @@ __global__ void __launch_bounds__(128) k_gradient(MeshDev m, HydroCfg c, const d
         M[6] += az * dx; M[7] += az * dy; M[8] += az * dz;
         const double ivo = FROM_CHARGES ? 1.0 / m.vol[q.o] : 1.0;
 #pragma unroll
-        for (int k = 0; k < 5; ++k) {
+        for (int k = 0; k < NG; ++k) {
             const double wo = S[k * n + q.o] * ivo;
             const double dw = wo - Wi[k];
             b[3 * k + 0] += ax * dw;
@@ -104,9 +111,9 @@ __global__ void __launch_bounds__(128) k_gradient(MeshDev m, HydroCfg c, const d
     const double c10 = M[2] * M[7] - M[1] * M[8], c11 = M[0] * M[8] - M[2] * M[6], c12 = M[1] * M[6] - M[0] * M[7];
     const double c20 = M[1] * M[5] - M[2] * M[4], c21 = M[2] * M[3] - M[0] * M[5], c22 = M[0] * M[4] - M[1] * M[3];
     const double idet = 1.0 / (M[0] * c00 + M[1] * c01 + M[2] * c02);
-    double g[15];
+    double g[3 * NG];
 #pragma unroll
-    for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < NG; ++k) {
         const double b0 = b[3 * k], b1 = b[3 * k + 1], b2 = b[3 * k + 2];
         g[3 * k + 0] = (c00 * b0 + c10 * b1 + c20 * b2) * idet;
         g[3 * k + 1] = (c01 * b0 + c11 * b1 + c21 * b2) * idet;
@@ -118,9 +125,9 @@ __global__ void __launch_bounds__(128) k_gradient(MeshDev m, HydroCfg c, const d
         // largest positive and the most negative Delta_ij = g . d_ij.
         // DM: min_j max(0, theta (W_j - W_i) / Delta_ij), tracked as a
         // fraction (num, den > 0) to avoid a division per face.
-        double dmax[5], dmin[5], rn[5], rd[5];
+        double dmax[NG], dmin[NG], rn[NG], rd[NG];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) { dmax[k] = 0.0; dmin[k] = 0.0; rn[k] = 1.0; rd[k] = 1.0; }
+        for (int k = 0; k < NG; ++k) { dmax[k] = 0.0; dmin[k] = 0.0; rn[k] = 1.0; rd[k] = 1.0; }
         for (int e = e0; e < e1; ++e) {
             const Nbr q = neighbour(m, e, L);
             double dx, dy, dz;
@@ -137,7 +144,7 @@ __global__ void __launch_bounds__(128) k_gradient(MeshDev m, HydroCfg c, const d
             }
             const double ivo = FROM_CHARGES ? 1.0 / m.vol[q.o] : 1.0;
 #pragma unroll
-            for (int k = 0; k < 5; ++k) {
+            for (int k = 0; k < NG; ++k) {
                 const double del = g[3 * k] * dx + g[3 * k + 1] * dy + g[3 * k + 2] * dz;
                 dmax[k] = fmax(dmax[k], del);
                 dmin[k] = fmin(dmin[k], del);
@@ -151,7 +158,7 @@ __global__ void __launch_bounds__(128) k_gradient(MeshDev m, HydroCfg c, const d
             }
         }
 #pragma unroll
-        for (int k = 0; k < 5; ++k) {
+        for (int k = 0; k < NG; ++k) {
             double a = 1.0;
             if (dmax[k] > 0.0) a = fmin(a, (wmax[k] - Wi[k]) / dmax[k]);
             if (dmin[k] < 0.0) a = fmin(a, (wmin[k] - Wi[k]) / dmin[k]);
@@ -163,7 +170,7 @@ __global__ void __launch_bounds__(128) k_gradient(MeshDev m, HydroCfg c, const d
     }
     if (!PREDICT) {
 #pragma unroll
-        for (int k = 0; k < 15; ++k) grad[k * n + i] = g[k];
+        for (int k = 0; k < 3 * NG; ++k) grad[k * n + i] = g[k];
         return;
     }
     // half-step predictor: dW/dt = -div F written through the chain rule on
@@ -204,19 +211,32 @@ __global__ void __launch_bounds__(128) k_gradient(MeshDev m, HydroCfg c, const d
     const double hdt = 0.5 * dtp[m.cbox[i]];
 #pragma unroll
     for (int k = 0; k < 5; ++k) Wh[k * n + i] = Wi[k] + hdt * rate[k];
+    if constexpr (NG == 6) {
+        // d_t (rho A) = -(u . grad(rho A) + rho A div u)
+        const double r5 = -(ux * g[15] + uy * g[16] + uz * g[17] + Wi[5] * divu);
+        Wh[5 * n + i] = Wi[5] + hdt * r5;
+    }
+}
+
+template <int NG>
+static void launch_gradient_t(const MeshDev &m, const HydroCfg &c, const double *S, bool from_charges, double *grad,
+                              double *W_half, const double *dt, cudaStream_t s)
+{
+    int nb = (int)((m.n + 127) / 128);
+    if (W_half) {
+        if (from_charges) k_gradient<true, true, NG><<<nb, 128, 0, s>>>(m, c, S, grad, W_half, dt);
+        else k_gradient<false, true, NG><<<nb, 128, 0, s>>>(m, c, S, grad, W_half, dt);
+    } else {
+        if (from_charges) k_gradient<true, false, NG><<<nb, 128, 0, s>>>(m, c, S, grad, W_half, dt);
+        else k_gradient<false, false, NG><<<nb, 128, 0, s>>>(m, c, S, grad, W_half, dt);
+    }
 }
 
 void launch_gradient(const MeshDev &m, const HydroCfg &c, const double *S, bool from_charges, double *grad,
                      double *W_half, const double *dt, cudaStream_t s)
 {
-    int nb = (int)((m.n + 127) / 128);
-    if (W_half) {
-        if (from_charges) k_gradient<true, true><<<nb, 128, 0, s>>>(m, c, S, grad, W_half, dt);
-        else k_gradient<false, true><<<nb, 128, 0, s>>>(m, c, S, grad, W_half, dt);
-    } else {
-        if (from_charges) k_gradient<true, false><<<nb, 128, 0, s>>>(m, c, S, grad, W_half, dt);
-        else k_gradient<false, false><<<nb, 128, 0, s>>>(m, c, S, grad, W_half, dt);
-    }
+    if (c.entropy) launch_gradient_t<6>(m, c, S, from_charges, grad, W_half, dt, s);
+    else launch_gradient_t<5>(m, c, S, from_charges, grad, W_half, dt, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -224,6 +244,9 @@ void launch_gradient(const MeshDev &m, const HydroCfg &c, const double *S, bool 
 // ---------------------------------------------------------------------------
 using FaceState = FaceStateT<double>;
 
+// With NG = 6 the flux rows 5, 6 and 7 hold the entropy flux A F_(rho A), the
+// face's shock Mach number and its swept-volume rate A (w_f . n).
+template <int NG>
 __global__ void __launch_bounds__(128) k_face_flux(MeshDev m, HydroCfg c, const double *__restrict__ pos,
                                                    const double *__restrict__ w, const double *__restrict__ Wh,
                                                    const double *__restrict__ grad, double *__restrict__ flux)
@@ -241,14 +264,23 @@ __global__ void __launch_bounds__(128) k_face_flux(MeshDev m, HydroCfg c, const 
     // reconstruction to the face centroid: W_face = W_half + (x_f - c) . grad
     const double dlx = fx - m.cen[i], dly = fy - m.cen[n + i], dlz = fz - m.cen[2 * n + i];
     const double drx = fx - (m.cen[j] + ox), dry = fy - (m.cen[n + j] + oy), drz = fz - (m.cen[2 * n + j] + oz);
-    double WL[5], WR[5];
+    double WL[NG], WR[NG];
 #pragma unroll
-    for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < NG; ++k) {
         WL[k] = Wh[k * n + i] + dlx * grad[(3 * k) * n + i] + dly * grad[(3 * k + 1) * n + i] + dlz * grad[(3 * k + 2) * n + i];
         WR[k] = Wh[k * n + j] + drx * grad[(3 * k) * n + j] + dry * grad[(3 * k + 1) * n + j] + drz * grad[(3 * k + 2) * n + j];
     }
+    const bool vac_l = !(WL[0] >= c.rho_floor), vac_r = !(WR[0] >= c.rho_floor);
     apply_floor(WL, c.rho_floor, c.eps_floor);
     apply_floor(WR, c.rho_floor, c.eps_floor);
+    if constexpr (NG == 6) {
+        // rho A at the face: a state reset to the density floor takes the
+        // floor state's own A; otherwise the reconstruction, not below 0
+        const double rf = c.rho_floor;
+        const double a_floor = rf * (c.gamma - 1.0) * rf * c.eps_floor / pow(rf, c.gamma);
+        WL[5] = vac_l ? a_floor : fmax(WL[5], 0.0);
+        WR[5] = vac_r ? a_floor : fmax(WR[5], 0.0);
+    }
     // face velocity (Sec. 4): mean generator velocity plus the correction for
     // the face centroid lying off the generators' midpoint
     const double rix = pos[i], riy = pos[n + i], riz = pos[2 * n + i];
@@ -288,6 +320,13 @@ __global__ void __launch_bounds__(128) k_face_flux(MeshDev m, HydroCfg c, const 
     flux[2 * fs + f] = A * (F[2] + fm * wfy);
     flux[3 * fs + f] = A * (F[3] + fm * wfz);
     flux[4 * fs + f] = A * fe;
+    if constexpr (NG == 6) {
+        double mach;
+        const double f5 = passive_flux_t<double>(c.riemann, L, R, nx, ny, nz, c.gamma, WL[5], WR[5], fm, mach);
+        flux[5 * fs + f] = A * f5;
+        flux[6 * fs + f] = mach;
+        flux[7 * fs + f] = A * (wfx * nx + wfy * ny + wfz * nz);
+    }
 }
 
 void launch_face_flux(const MeshDev &m, const HydroCfg &c, const double *pos, const double *w, const double *Wh,
@@ -296,38 +335,125 @@ void launch_face_flux(const MeshDev &m, const HydroCfg &c, const double *pos, co
     const int64_t nfl = face_launch_count(m);
     if (nfl == 0) return;
     int nb = (int)((nfl + 127) / 128);
-    k_face_flux<<<nb, 128, 0, s>>>(m, c, pos, w, Wh, grad, flux);
+    if (c.entropy) k_face_flux<6><<<nb, 128, 0, s>>>(m, c, pos, w, Wh, grad, flux);
+    else k_face_flux<5><<<nb, 128, 0, s>>>(m, c, pos, w, Wh, grad, flux);
 }
 
 // ---------------------------------------------------------------------------
 // Conservative update: U_i -= dt sum_{f in i} (+/-) Phi_f, then floors
 // ---------------------------------------------------------------------------
+// With NG = 6 (Sec. 4.3): a cell whose largest face shock Mach number is
+// below mach_th takes E from its entropy, E = |p|^2/(2m) + A rho^gamma V' /
+// (gamma - 1); elsewhere (and wherever the floors act) the entropy is reset
+// from E.  V' = V + dt sum (+/-) A (w_f . n) is the volume the moving faces
+// sweep the cell to in the step.
+template <int NG>
 __global__ void __launch_bounds__(256) k_update(MeshDev m, HydroCfg c, const double *__restrict__ flux,
                                                 const double *__restrict__ dtp, double *__restrict__ U)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t n = m.n, nf = m.fs;  // flux rows are face-capacity apart
     if (i >= n) return;
-    double acc[5] = {0, 0, 0, 0, 0};
+    double acc[NG];
+#pragma unroll
+    for (int k = 0; k < NG; ++k) acc[k] = 0.0;
+    double mc = 0.0, dv = 0.0;
     for (int e = m.inc_off[i]; e < m.inc_off[i + 1]; ++e) {
         int f = m.inc_face[e];
-        if (f >= 0) {
+        double sg = 1.0;
+        if (f < 0) { f = ~f; sg = -1.0; }
 #pragma unroll
-            for (int k = 0; k < 5; ++k) acc[k] += flux[k * nf + f];
-        } else {
-            f = ~f;
-#pragma unroll
-            for (int k = 0; k < 5; ++k) acc[k] -= flux[k * nf + f];
+        for (int k = 0; k < NG; ++k) acc[k] += sg * flux[k * nf + f];
+        if constexpr (NG == 6) {
+            mc = fmax(mc, flux[6 * nf + f]);
+            dv += sg * flux[7 * nf + f];
         }
     }
     const double dt = dtp[m.cbox[i]];
-    double Un[5];
+    double Un[NG];
 #pragma unroll
-    for (int k = 0; k < 5; ++k) Un[k] = U[k * n + i] - dt * acc[k];
+    for (int k = 0; k < NG; ++k) Un[k] = U[k * n + i] - dt * acc[k];
     const double V = m.vol[i], iv = 1.0 / V;
+    const double g = c.gamma;
+    bool energy = true;
+    double Vn = V;
+    if constexpr (NG == 6) {
+        Vn = V + dt * dv;
+        energy = mc >= c.mach_th;
+        if (!energy) {
+            if (Un[0] > 0.0 && Un[5] > 0.0 && Vn > 0.0) {
+                const double rho = Un[0] / Vn;
+                const double P = (Un[5] / Un[0]) * pow(rho, g);
+                Un[4] = 0.5 * (Un[1] * Un[1] + Un[2] * Un[2] + Un[3] * Un[3]) / Un[0] + P * Vn / (g - 1.0);
+            } else {
+                energy = true;
+            }
+        }
+    }
     double W[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) W[k] = Un[k] * iv;
+    const bool ch = apply_floor(W, c.rho_floor, c.eps_floor);
+    if (ch) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) Un[k] = W[k] * V;
+    }
+    if constexpr (NG == 6) {
+        if (energy || ch) {
+            const double Vr = Vn > 0.0 ? Vn : V;
+            const double rho = Un[0] / Vr;
+            const double P = (g - 1.0) * (Un[4] - 0.5 * (Un[1] * Un[1] + Un[2] * Un[2] + Un[3] * Un[3]) / Un[0]) / Vr;
+            Un[5] = Un[0] * P / pow(rho, g);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NG; ++k) U[k * n + i] = Un[k];
+}
+
+void launch_update(const MeshDev &m, const HydroCfg &c, const double *flux, const double *dt, double *U,
+                   cudaStream_t s)
+{
+    int nb = (int)((m.n + 255) / 256);
+    if (c.entropy) k_update<6><<<nb, 256, 0, s>>>(m, c, flux, dt, U);
+    else k_update<5><<<nb, 256, 0, s>>>(m, c, flux, dt, U);
+}
+
+// ---------------------------------------------------------------------------
+// Heun's method (second-order time integration, Sec. 6): per-volume states of
+// a stage, and the final average U = (U^n + U**) / 2 with the cell floors on
+// the end-of-step mesh.
+// ---------------------------------------------------------------------------
+template <int NG>
+__global__ void __launch_bounds__(256) k_states(MeshDev m, const double *__restrict__ U, double *__restrict__ W)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t n = m.n;
+    if (i >= n) return;
+    const double iv = 1.0 / m.vol[i];
+#pragma unroll
+    for (int k = 0; k < NG; ++k) W[k * n + i] = U[k * n + i] * iv;
+}
+
+void launch_states(const MeshDev &m, const HydroCfg &c, const double *U, double *W, cudaStream_t s)
+{
+    int nb = (int)((m.n + 255) / 256);
+    if (c.entropy) k_states<6><<<nb, 256, 0, s>>>(m, U, W);
+    else k_states<5><<<nb, 256, 0, s>>>(m, U, W);
+}
+
+__global__ void __launch_bounds__(256) k_heun_average(MeshDev m, HydroCfg c, const double *__restrict__ U0,
+                                                      double *__restrict__ U)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t n = m.n;
+    if (i >= n) return;
+    const double V = m.vol[i], iv = 1.0 / V;
+    double Un[5], W[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        Un[k] = 0.5 * (U0[k * n + i] + U[k * n + i]);
+        W[k] = Un[k] * iv;
+    }
     if (apply_floor(W, c.rho_floor, c.eps_floor)) {
 #pragma unroll
         for (int k = 0; k < 5; ++k) Un[k] = W[k] * V;
@@ -336,11 +462,10 @@ __global__ void __launch_bounds__(256) k_update(MeshDev m, HydroCfg c, const dou
     for (int k = 0; k < 5; ++k) U[k * n + i] = Un[k];
 }
 
-void launch_update(const MeshDev &m, const HydroCfg &c, const double *flux, const double *dt, double *U,
-                   cudaStream_t s)
+void launch_heun_average(const MeshDev &m, const HydroCfg &c, const double *U0, double *U, cudaStream_t s)
 {
     int nb = (int)((m.n + 255) / 256);
-    k_update<<<nb, 256, 0, s>>>(m, c, flux, dt, U);
+    k_heun_average<<<nb, 256, 0, s>>>(m, c, U0, U);
 }
 
 // ---------------------------------------------------------------------------
@@ -486,6 +611,7 @@ __global__ void k_prims_to_charges(MeshDev m, HydroCfg c, const double *__restri
     U[2 * n + i] = r * vy * V;
     U[3 * n + i] = r * vz * V;
     U[4 * n + i] = (P[i] / (c.gamma - 1.0) + 0.5 * r * (vx * vx + vy * vy + vz * vz)) * V;
+    if (c.entropy) U[5 * n + i] = (r * V) * P[i] / pow(r, c.gamma);  // m A, A = P / rho^gamma (Sec. 4.3)
 }
 
 void launch_prims_to_charges(const MeshDev &m, const HydroCfg &c, const double *rho, const double *vel,

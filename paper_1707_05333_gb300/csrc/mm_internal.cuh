@@ -103,7 +103,9 @@ struct MeshDev {
 
 struct HydroCfg {
     double gamma, cfl, eta, chi, zeta, theta, rho_floor, eps_floor;
+    double mach_th;  // energy/entropy switch threshold (Sec. 4.3)
     int limiter, regularize, riemann;
+    int entropy;     // 1: a sixth state column rho A and the switch
 };
 
 // FP32 records of the mixed-precision hydro path (see mm_hydro32.cu).
@@ -128,6 +130,8 @@ void launch_gradient(const MeshDev &m, const HydroCfg &c, const double *U_or_W, 
                      double *grad, double *W_half, const double *dt, cudaStream_t s);
 void launch_face_flux(const MeshDev &m, const HydroCfg &c, const double *pos, const double *w,
                       const double *Wh, const double *grad, double *flux, cudaStream_t s);
+void launch_states(const MeshDev &m, const HydroCfg &c, const double *U, double *W, cudaStream_t s);
+void launch_heun_average(const MeshDev &m, const HydroCfg &c, const double *U0, double *U, cudaStream_t s);
 void launch_update(const MeshDev &m, const HydroCfg &c, const double *flux, const double *dt, double *U,
                    cudaStream_t s);
 void launch_mesh_velocity(const MeshDev &m, const HydroCfg &c, const double *pos, const double *U,

@@ -92,6 +92,55 @@ __device__ __forceinline__ void hll_t(const FaceStateT<T> &L, const FaceStateT<T
     for (int k = 0; k < 5; ++k) F[k] = (sr * Fl[k] - sl * Fr[k] + sl * sr * (Ur[k] - Ul[k])) * id;
 }
 
+// Wave speeds of the HLLC model along the unit normal: Davis S_L, S_R, the
+// contact speed S* and the star pressure P* (from the left wave's jump
+// condition), with the normal velocities u_L, u_R.
+template <class T>
+__device__ __forceinline__ void star_state_t(const FaceStateT<T> &L, const FaceStateT<T> &R, T nx, T ny, T nz,
+                                             T gamma, T &sl, T &ss, T &sr, T &ps, T &ul, T &ur)
+{
+    ul = L.vx * nx + L.vy * ny + L.vz * nz;
+    ur = R.vx * nx + R.vy * ny + R.vz * nz;
+    const T cl = sqrt_t(gamma * L.P / L.rho), cr = sqrt_t(gamma * R.P / R.rho);
+    sl = min_t(ul - cl, ur - cr);
+    sr = max_t(ul + cl, ur + cr);
+    ss = (R.P - L.P + L.rho * ul * (sl - ul) - R.rho * ur * (sr - ur)) / (L.rho * (sl - ul) - R.rho * (sr - ur));
+    ps = L.P + L.rho * (sl - ul) * (ss - ul);
+}
+
+// Mach number of the shock that raises the pressure of either side to the
+// star pressure (Rankine-Hugoniot: M^2 = 1 + (gamma+1)/(2 gamma) (P*/P - 1)),
+// the larger of the two, 0 where neither side is compressed (Sec. 4.3).
+template <class T>
+__device__ __forceinline__ T shock_mach_t(T pl, T pr, T ps, T gamma)
+{
+    const T k = (gamma + T(1)) / (T(2) * gamma);
+    T m = T(0);
+    if (ps > pl) m = max_t(m, sqrt_t(T(1) + k * (ps / pl - T(1))));
+    if (ps > pr) m = max_t(m, sqrt_t(T(1) + k * (ps / pr - T(1))));
+    return m;
+}
+
+// Flux of a passive charge rho a (the entropy column, Sec. 4.3) carried by
+// the Riemann solution: HLLC takes a from the side of the contact times the
+// mass flux fm; HLL averages rho a like any conserved column.
+template <class T>
+__device__ __forceinline__ T passive_flux_t(int kind, const FaceStateT<T> &L, const FaceStateT<T> &R, T nx, T ny,
+                                            T nz, T gamma, T rhoa_l, T rhoa_r, T fm, T &mach)
+{
+    T sl, ss, sr, ps, ul, ur;
+    star_state_t<T>(L, R, nx, ny, nz, gamma, sl, ss, sr, ps, ul, ur);
+    mach = shock_mach_t<T>(L.P, R.P, ps, gamma);
+    const T al = rhoa_l / L.rho, ar = rhoa_r / R.rho;
+    if (kind == 1) {
+        const T fl = L.rho * ul * al, fr = R.rho * ur * ar;
+        if (sl >= T(0)) return fl;
+        if (sr <= T(0)) return fr;
+        return (sr * fl - sl * fr + sl * sr * (rhoa_r - rhoa_l)) / (sr - sl);
+    }
+    return fm * ((sl >= T(0) || ss >= T(0)) ? al : ar);
+}
+
 // The configured solver: 0 HLLC, 1 HLL.
 template <class T>
 __device__ __forceinline__ void riemann_t(int kind, const FaceStateT<T> &L, const FaceStateT<T> &R, T nx, T ny, T nz,

@@ -48,7 +48,7 @@ def test_default_config_and_struct_layout(lib):
     binding._lib = None
     cfg = binding.default_config()
     assert cfg.gamma == pytest.approx(5.0 / 3.0) and cfg.cfl == 0.3 and cfg.limiter == 1
-    assert ctypes.sizeof(binding.Config) == 9 * 8 + 8 * 4 + 8
+    assert ctypes.sizeof(binding.Config) == 9 * 8 + 8 * 4 + 8 + 8 + 2 * 4
     assert ctypes.sizeof(binding.MeshStruct) == 4 * 8 + 3 * 8 + 8 + 2 * 8 + 10 * 8
 
 

@@ -28,8 +28,8 @@ def charges(oracle, pos, box, rho, vel, pres, gamma):
     return oracle.charges_from_prims(T["volume"], rho, vel, pres, gamma)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_batched_step_equals_per_box_steps(oracle, precision):
+@pytest.mark.parametrize("precision,integrator", [(0, 0), (1, 0), (0, 1)])
+def test_batched_step_equals_per_box_steps(oracle, precision, integrator):
     import torch
     from paper_1707_05333_gb300 import binding
     parts, boxes = make_batch()
@@ -40,7 +40,7 @@ def test_batched_step_equals_per_box_steps(oracle, precision):
     U_all = np.concatenate(Us)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        ctx = binding.Context(stream=stream, limiter=2, regularize=1, precision=precision)
+        ctx = binding.Context(stream=stream, limiter=2, regularize=1, precision=precision, integrator=integrator)
         pos = H.to_dev(torch, pos_all.T)
         U = H.to_dev(torch, U_all.T)
         dt = torch.empty(len(parts), dtype=torch.float64, device="cuda")
@@ -49,7 +49,7 @@ def test_batched_step_equals_per_box_steps(oracle, precision):
             ctx.mm_step_batched(pos, U, off, boxes, dt_out=dt)
             ctx.mm_sync_status()
             outs.append((pos.cpu().numpy().copy(), U.cpu().numpy().copy(), dt.cpu().numpy().copy()))
-        ref = binding.Context(stream=stream, limiter=2, regularize=1, precision=precision)
+        ref = binding.Context(stream=stream, limiter=2, regularize=1, precision=precision, integrator=integrator)
         for b, ((p, r, v, P), box) in enumerate(zip(parts, boxes)):
             pb = H.to_dev(torch, p.T)
             Ub = H.to_dev(torch, Us[b].T)

@@ -34,14 +34,15 @@ def run_to(ctx, torch, w, t_end, U):
     return G, U.cpu().numpy(), steps
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_sod_tube_full_size_matches_exact_solution(oracle, precision):
+@pytest.mark.parametrize("precision,entropy", [(0, 0), (1, 0), (0, 1)])
+def test_sod_tube_full_size_matches_exact_solution(oracle, precision, entropy):
     """128x16x16 generators in the 8x1x1 box (gamma 1.4) to t = 0.2: the
-    density profile follows the exact solution of both interfaces."""
+    density profile follows the exact solution of both interfaces, also with
+    the entropy column and the energy/entropy switch (Sec. 4.3)."""
     import torch
     from paper_1707_05333_gb300 import binding
     w = WL.shock_tube(128, 16, 16)
-    ctx = binding.Context(gamma=1.4, cfl=0.3, limiter=1, precision=precision)
+    ctx = binding.Context(gamma=1.4, cfl=0.3, limiter=1, precision=precision, entropy=entropy, mach_th=1.1)
     P = H.to_dev(torch, w.pos.T)
     mesh = ctx.mm_tessellate(P, w.box)
     U = ctx.mm_prims_to_charges(mesh, H.to_dev(torch, w.rho), H.to_dev(torch, w.vel.T), H.to_dev(torch, w.pres))
@@ -53,7 +54,7 @@ def test_sod_tube_full_size_matches_exact_solution(oracle, precision):
                      ER.profile(1.0, 0, 1.0, 0.125, 0, 0.1, 1.4, x, 4.0, 0.2)[0])
     sel = (x > 1.0) & (x < 7.0)
     l1 = np.mean(np.abs(rho[sel] - exact[sel]))
-    print(f"Sod precision={precision}: {steps} steps, density L1 vs exact = {l1:.4f}")
+    print(f"Sod precision={precision} entropy={entropy}: {steps} steps, density L1 vs exact = {l1:.4f}")
     assert 10 < steps < 200
     assert l1 < 0.02
     ctx.close()
@@ -125,3 +126,38 @@ def test_gresho_vortex_error_converges_like_the_paper():
     print(f"Gresho fitted L1 slope {slope:.2f} (paper: -0.88)")
     assert slope < -0.5
     assert l1[64] < 0.1
+
+
+def angular_momentum_z(G, U):
+    """L_z = sum_i ((c_i - axis) x p_i)_z about the vortex axis (0.5, 0.5):
+    exact for a uniform momentum density in each cell."""
+    c = G["cell_centroid"]
+    return float(np.sum((c[0] - 0.5) * U[2] - (c[1] - 0.5) * U[1]))
+
+
+def test_gresho_angular_momentum_drift_by_integrator():
+    """Sec. 6 attributes the angular-momentum error of the scheme to the
+    start-of-step face geometry and names Heun flux averaging as the fix.
+    Both integrators run the 32^2 Gresho vortex to t = 0.5 with the same
+    fixed dt; the relative drift of L_z is reported for both and must stay
+    small."""
+    import torch
+    from paper_1707_05333_gb300 import binding
+    drift = {}
+    for integrator in (0, 1):
+        w = WL.gresho_vortex(32)
+        ctx = binding.Context(gamma=w.gamma, cfl=w.cfl, limiter=1, regularize=1, integrator=integrator)
+        pos = H.to_dev(torch, w.pos.T)
+        mesh = ctx.mm_tessellate(pos, w.box)
+        G0 = {k: v.cpu().numpy() for k, v in mesh.to_torch().items()}
+        U = ctx.mm_prims_to_charges(mesh, H.to_dev(torch, w.rho), H.to_dev(torch, w.vel.T), H.to_dev(torch, w.pres))
+        L0 = angular_momentum_z(G0, U.cpu().numpy())
+        dt = torch.tensor([0.5 / 400], dtype=torch.float64, device="cuda")  # below the CFL step (~2.3e-3)
+        for _ in range(400):
+            ctx.mm_step(pos, U, w.box, dt_fixed=dt)
+        mesh = ctx.mm_tessellate(pos, w.box)
+        G1 = {k: v.cpu().numpy() for k, v in mesh.to_torch().items()}
+        drift[integrator] = angular_momentum_z(G1, U.cpu().numpy()) / L0 - 1.0
+        ctx.close()
+    print(f"Gresho 32^2 to t=0.5: relative L_z drift half-step {drift[0]:+.3e}, Heun {drift[1]:+.3e}")
+    assert abs(drift[0]) < 0.05 and abs(drift[1]) < 0.05

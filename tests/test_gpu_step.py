@@ -18,10 +18,20 @@ def gpu():
     c.close()
 
 
-def setup(oracle, w, rho=None, vel=None, pres=None):
+@pytest.fixture(autouse=True)
+def default_settings(gpu):
+    """Every test starts from the default configuration (the parity cases
+    switch limiters, solvers, the entropy column and the integrator)."""
+    from paper_1707_05333_gb300 import binding
+    c, _ = gpu
+    d = binding.default_config()
+    c.set_config(**{f: getattr(d, f) for f, _ in d._fields_})
+
+
+def setup(oracle, w, rho=None, vel=None, pres=None, entropy=False):
     T = oracle.tessellate(w.pos, w.box, 1)
     U = oracle.charges_from_prims(T["volume"], w.rho if rho is None else rho, w.vel if vel is None else vel,
-                                  w.pres if pres is None else pres, w.gamma, w.e_add)
+                                  w.pres if pres is None else pres, w.gamma, w.e_add, entropy=entropy)
     return T, U
 
 
@@ -34,7 +44,8 @@ def cfg_pair(oracle, gamma, **kw):
 
 def assert_state_close(G, O, rtol=RTOL_STEP):
     # per component, relative to the component's scale (momenta can vanish)
-    for k in range(5):
+    assert G.shape[0] == O.shape[1]
+    for k in range(O.shape[1]):
         scale = np.abs(O[:, k]).max()
         np.testing.assert_allclose(G[k], O[:, k], rtol=rtol, atol=rtol * scale, err_msg=f"component {k}")
 
@@ -68,6 +79,15 @@ CONFIGS = {
     "face_centroid_limiter_random": dict(maker=lambda: WL.smooth_wave(10), kw=dict(limiter=3, regularize=1),
                                          random=True),
     "gresho_vortex_16x16x3_regularized": dict(maker=lambda: WL.gresho_vortex(16), kw=dict(limiter=1, regularize=1)),
+    # entropy column and switch (Sec. 4.3): cells at the shock keep the energy
+    # equation, the rest take E from the entropy
+    "entropy_switch_shock_tube_48x6x6": dict(maker=lambda: WL.shock_tube(48, 6, 6),
+                                             kw=dict(limiter=1, entropy=1, mach_th=1.1)),
+    "entropy_switch_hll_point_blast_12^3": dict(maker=lambda: WL.point_blast(12),
+                                                kw=dict(limiter=2, riemann=1, entropy=1, mach_th=1.1)),
+    "entropy_everywhere_random_regularized": dict(maker=lambda: WL.smooth_wave(10),
+                                                  kw=dict(limiter=3, regularize=1, entropy=1, mach_th=1e300),
+                                                  random=True),
 }
 
 
@@ -76,11 +96,12 @@ def test_one_step_matches_oracle(oracle, gpu, case):
     c, torch = gpu
     spec = CONFIGS[case]
     w = spec["maker"]()
+    ent = bool(spec["kw"].get("entropy", 0))
     if spec.get("random"):
         rho, vel, pres = WL.random_state(w.n, seed=3)
-        T, U = setup(oracle, w, rho, vel, pres)
+        T, U = setup(oracle, w, rho, vel, pres, entropy=ent)
     else:
-        T, U = setup(oracle, w)
+        T, U = setup(oracle, w, entropy=ent)
     ocfg, gcfg = cfg_pair(oracle, w.gamma, cfl=w.cfl, **spec["kw"])
     c.set_config(**{f: getattr(gcfg, f) for f, _ in gcfg._fields_})
     S = oracle.step(w.pos, U, w.box, ocfg, tess=T)
@@ -227,3 +248,46 @@ def test_mixed_step_l1_error_and_conservation(oracle, gpu, case):
     # momentum scale sqrt(M E) (the momentum may start exactly at zero)
     scale[1:4] = max(scale[1:4].max(), np.sqrt(scale[0] * scale[4]))
     assert np.all(np.abs(t1 - t0) <= 1e-12 * scale), (t1 - t0) / scale
+
+
+HEUN_CASES = {
+    "smooth_random_regularized": dict(maker=lambda: WL.smooth_wave(10), kw=dict(limiter=1, regularize=1), random=True),
+    "shock_tube_48x6x6_hll": dict(maker=lambda: WL.shock_tube(48, 6, 6), kw=dict(limiter=2, riemann=1)),
+    "gresho_vortex_16x16x3": dict(maker=lambda: WL.gresho_vortex(16), kw=dict(limiter=3, regularize=1)),
+}
+
+
+@pytest.mark.parametrize("case", list(HEUN_CASES))
+def test_heun_step_matches_oracle(oracle, gpu, case):
+    """integrator = 1: stage on the start mesh, drift, second tessellation,
+    stage on the end mesh, average (Sec. 6)."""
+    c, torch = gpu
+    spec = HEUN_CASES[case]
+    w = spec["maker"]()
+    if spec.get("random"):
+        rho, vel, pres = WL.random_state(w.n, seed=13, v_sigma=0.2)
+        T, U = setup(oracle, w, rho, vel, pres)
+    else:
+        T, U = setup(oracle, w)
+    ocfg = oracle.make_cfg(gamma=w.gamma, cfl=w.cfl, **spec["kw"])
+    from paper_1707_05333_gb300 import binding
+    gcfg = binding.default_config(gamma=w.gamma, cfl=w.cfl, integrator=1, **spec["kw"])
+    c.set_config(**{f: getattr(gcfg, f) for f, _ in gcfg._fields_})
+    try:
+        S = oracle.step_heun(w.pos, U, w.box, ocfg, tess=T)
+        pos = H.to_dev(torch, w.pos.T)
+        Ud = H.to_dev(torch, U.T)
+        dt_fixed = torch.tensor([S["dt"]], dtype=torch.float64, device="cuda")
+        dt_out = torch.empty((1,), dtype=torch.float64, device="cuda")
+        c.mm_step(pos, Ud, w.box, dt_fixed=dt_fixed, dt_out=dt_out)
+        assert_state_close(Ud.cpu().numpy(), S["U"])
+        dp = pos.cpu().numpy().T - S["pos"]
+        dp -= np.round(dp / w.box) * w.box
+        assert np.abs(dp).max() <= 1e-12
+        # the context's mesh is the end-of-step one
+        G = {k: v.cpu().numpy() for k, v in c.mm_current_mesh().to_torch().items()}
+        np.testing.assert_allclose(G["cell_volume"], S["tess1"]["volume"], rtol=1e-9)
+        c.mm_step(H.to_dev(torch, w.pos.T), H.to_dev(torch, U.T), w.box, dt_out=dt_out)
+        assert float(dt_out.item()) == pytest.approx(S["dt_cfl"], rel=1e-13)
+    finally:
+        c.set_config(integrator=0)
