@@ -504,7 +504,10 @@ static mm_status hydro_enqueue(mm_ctx *c, const MeshDev &m, const double *pos, c
         return MM_OK;
     }
     stage_mark(c, MM_STAGE_GRADIENT_HALF, true);
-    launch_gradient(m, h, U, true, nullptr, P<double>(c->Wh), dt, s);
+    // states W^n = U / V, once per cell, in the gradient buffer (the second
+    // gradient pass overwrites them only after the first has read them)
+    launch_states(m, h, U, P<double>(c->grad), s);
+    launch_gradient(m, h, P<double>(c->grad), false, nullptr, P<double>(c->Wh), dt, s);
     stage_mark(c, MM_STAGE_GRADIENT_HALF, false);
     stage_mark(c, MM_STAGE_GRADIENT, true);
     launch_gradient(m, h, P<double>(c->Wh), false, P<double>(c->grad), nullptr, nullptr, s);
@@ -516,7 +519,7 @@ static mm_status hydro_enqueue(mm_ctx *c, const MeshDev &m, const double *pos, c
     launch_update(m, h, P<double>(c->flux), dt, U, s);
     stage_mark(c, MM_STAGE_UPDATE, false);
     CKLAUNCH();
-    c->launches += 4;
+    c->launches += 5;
     return MM_OK;
 }
 

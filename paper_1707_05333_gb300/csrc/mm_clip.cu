@@ -37,15 +37,44 @@
 namespace mm {
 
 constexpr unsigned FULL = 0xffffffffu;
+#ifndef MM_CLIP_MAXNREG
+#define MM_CLIP_MAXNREG 128  // registers per thread of the clipping kernel
+#endif
 constexpr int CBATCH = 64;  // candidate buffer; flushed (sorted + clipped) when full
 static_assert(CBATCH == PMAX, "the candidate buffer doubles as per-face storage");
 
+// Vertex storage.  PREC 0 keeps FP64 vertices throughout.  PREC 1 keeps FP32
+// vertices with their error bounds while clipping and solves the FP64
+// vertices only at the end, when the FP32 copies and |v|^2 bounds are dead:
+// the two sets share the same bytes.
 template <int PREC>
-struct ClipSmem {
+struct VertStore;
+template <>
+struct VertStore<0> {
+    double tx[TMAX], ty[TMAX], tz[TMAX];
+    long long tr2[TMAX];  // bits of |v|^2
+    float tfx[1], tfy[1], tfz[1], terr[1];
+};
+template <>
+struct VertStore<1> {
+    union {
+        struct {
+            double tx[TMAX], ty[TMAX], tz[TMAX];  // after clipping
+        };
+        struct {
+            long long tr2[TMAX];  // bits of an FP32 upper bound of |v|^2
+            float tfx[TMAX], tfy[TMAX], tfz[TMAX], terr[TMAX];
+        };
+    };
+};
+
+template <int PREC>
+struct ClipSmem : VertStore<PREC> {
     union {
         struct {
             double x[CBATCH], y[CBATCH], z[CBATCH];
             long long d2[CBATCH];  // bit pattern of |q|^2 (non-negative: orders like the value)
+            float fx[PREC ? CBATCH : 1], fy[PREC ? CBATCH : 1], fz[PREC ? CBATCH : 1], fo[PREC ? CBATCH : 1];
         } c;
         struct {
             double a[PMAX], x[PMAX], y[PMAX], z[PMAX];  // per-face area and centroid
@@ -54,13 +83,10 @@ struct ClipSmem {
     int cid[CBATCH], csh[CBATCH];
     double px[PMAX], py[PMAX], pz[PMAX], po[PMAX];  // planes x.q <= po
     int pnb[PMAX], psh[PMAX];
-    double tx[TMAX], ty[TMAX], tz[TMAX];  // FP64 vertices (PREC 1: only after clipping)
-    long long tr2[TMAX];                  // bits of |v|^2 (PREC 1: an upper bound)
     unsigned tv[TMAX];                    // a | b << 8 | c << 16
     unsigned long long bm[PMAX];          // removed directed edges x -> y
     unsigned stage[NSTAGE];               // triangles created by the current cut
     float pfx[PREC ? PMAX : 1], pfy[PREC ? PMAX : 1], pfz[PREC ? PMAX : 1], pfo[PREC ? PMAX : 1];
-    float tfx[PREC ? TMAX : 1], tfy[PREC ? TMAX : 1], tfz[PREC ? TMAX : 1], terr[PREC ? TMAX : 1];
 };
 
 // floor(a / b) for b > 0 in integer arithmetic
@@ -74,17 +100,20 @@ __device__ __forceinline__ double warp_sum(double v)
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     return v;
 }
-__device__ __forceinline__ long long warp_max_ll(long long v)
+// Warp-wide maximum of a non-negative 64-bit value: the high words first,
+// then the low words of the lanes holding the largest high word.
+__device__ __forceinline__ long long warp_max_nonneg(long long v)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(FULL, v, o));
-    return v;
+    const unsigned long long u = (unsigned long long)v;
+    const unsigned hi = __reduce_max_sync(FULL, (unsigned)(u >> 32));
+    const unsigned lo = __reduce_max_sync(FULL, (unsigned)(u >> 32) == hi ? (unsigned)u : 0u);
+    return (long long)(((unsigned long long)hi << 32) | lo);
 }
 __device__ __forceinline__ unsigned long long warp_or64(unsigned long long v)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v |= __shfl_xor_sync(FULL, v, o);
-    return v;
+    const unsigned lo = __reduce_or_sync(FULL, (unsigned)v);
+    const unsigned hi = __reduce_or_sync(FULL, (unsigned)(v >> 32));
+    return ((unsigned long long)hi << 32) | lo;
 }
 
 // Intersection of planes a, b, c in FP64 with explicitly rounded operations
@@ -113,6 +142,14 @@ __device__ __forceinline__ void vertex64(const S_t &S, int a, int b, int c, doub
 __device__ __forceinline__ bool beyond64(double qx, double qy, double qz, double off, double x, double y, double z)
 {
     return __fma_rn(qx, x, __fma_rn(qy, y, __dmul_rn(qz, z))) > off;
+}
+
+// |q|^2 / 2 from the bit pattern of |q|^2: halving a normal double lowers its
+// exponent by one, an integer operation.
+__device__ __forceinline__ double half_of(long long d2bits)
+{
+    if (((d2bits >> 52) & 0x7ff) > 1) return __longlong_as_double(d2bits - (1LL << 52));
+    return 0.5 * __longlong_as_double(d2bits);
 }
 
 __device__ __forceinline__ long long r2_bits64(double x, double y, double z)
@@ -210,9 +247,20 @@ __device__ __forceinline__ void update_limit(ClipSmem<PREC> &S, CellState &C, in
 {
     long long m = 0;
     for (int t = lane; t < C.nt; t += 32) m = max(m, S.tr2[t]);
-    m = warp_max_ll(m);
-    if constexpr (PREC == 0) C.lim = __double_as_longlong(4.0 * __longlong_as_double(m));
-    else C.lim = __double_as_longlong(4.0 * (double)__int_as_float((int)m));
+    if constexpr (PREC == 0) {
+        m = warp_max_nonneg(m);
+        C.lim = __double_as_longlong(4.0 * __longlong_as_double(m));
+    } else {
+        // the bounds are positive floats: their bit patterns fit 32 bits, and
+        // 4 (double) f is f's exponent moved to the double bias plus two
+        const unsigned fb = __reduce_max_sync(FULL, (unsigned)m);
+        const unsigned e = fb >> 23;
+        if (e != 0u && e < 255u)
+            C.lim = (long long)(((unsigned long long)(e + (1023u - 127u + 2u)) << 52) |
+                                ((unsigned long long)(fb & 0x7fffffu) << 29));
+        else
+            C.lim = __double_as_longlong(4.0 * (double)__int_as_float((int)fb));
+    }
 }
 
 // Clip the cell by candidate k.  Warp-uniform control flow throughout.
@@ -220,15 +268,15 @@ template <int PREC>
 __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
 {
     const double qx = S.u.c.x[k], qy = S.u.c.y[k], qz = S.u.c.z[k];
-    const double off = 0.5 * __longlong_as_double(S.u.c.d2[k]);
+    const double off = half_of(S.u.c.d2[k]);
     const int nchunk = (C.nt + 31) >> 5;
     unsigned outm[TMAX / 32];
     unsigned anyv = 0;
     C.tested++;
     if (PREC == 0) C.pred64 += C.nt;
     float fqx = 0.f, fqy = 0.f, fqz = 0.f, foff = 0.f, fqn = 0.f;
-    if (PREC == 1) {
-        fqx = (float)qx; fqy = (float)qy; fqz = (float)qz; foff = (float)off;
+    if constexpr (PREC == 1) {
+        fqx = S.u.c.fx[k]; fqy = S.u.c.fy[k]; fqz = S.u.c.fz[k]; foff = S.u.c.fo[k];
         fqn = sqrtf(2.0f * foff) * 1.0000005f;
     }
 #pragma unroll
@@ -309,31 +357,32 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
     for (int c = 0; c < TMAX / 32; ++c) {
         if (c >= nchunk) break;
         if (outm[c] == 0) continue;  // warp-uniform
-        unsigned e[3];
-        int cnt = 0;
+        // rim edges of this lane's removed triangle, kept in registers
+        unsigned e0 = 0, e1 = 0, e2 = 0;
+        bool f0 = false, f1 = false, f2 = false;
         if ((outm[c] >> lane) & 1u) {
-            unsigned v = S.tv[c * 32 + lane];
-            unsigned a = v & 255u, b = (v >> 8) & 255u, cc = (v >> 16) & 255u;
-            unsigned ex[3] = {a, b, cc}, ey[3] = {b, cc, a};
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                if (!((S.bm[ey[q]] >> ex[q]) & 1ull)) {
-                    e[cnt++] = ex[q] | (ey[q] << 8) | ((unsigned)kp << 16);
-                    xs |= 1ull << ex[q];
-                    ys |= 1ull << ey[q];
-                }
-            }
+            const unsigned v = S.tv[c * 32 + lane];
+            const unsigned a = v & 255u, b = (v >> 8) & 255u, cc = (v >> 16) & 255u;
+            const unsigned hk = (unsigned)kp << 16;
+            f0 = !((S.bm[b] >> a) & 1ull);   // a -> b
+            f1 = !((S.bm[cc] >> b) & 1ull);  // b -> cc
+            f2 = !((S.bm[a] >> cc) & 1ull);  // cc -> a
+            e0 = a | (b << 8) | hk;
+            e1 = b | (cc << 8) | hk;
+            e2 = cc | (a << 8) | hk;
+            if (f0) { xs |= 1ull << a; ys |= 1ull << b; }
+            if (f1) { xs |= 1ull << b; ys |= 1ull << cc; }
+            if (f2) { xs |= 1ull << cc; ys |= 1ull << a; }
         }
-        int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(FULL, incl, o);
-            if (lane >= o) incl += y;
-        }
-        int tot = __shfl_sync(FULL, incl, 31);
-        int base = nnew + incl - cnt;
-        for (int q = 0; q < cnt; ++q)
-            if (base + q < NSTAGE) S.stage[base + q] = e[q];
+        const int cnt = (int)f0 + (int)f1 + (int)f2;
+        // exclusive prefix of cnt (0..3) from the ballots of its two bits
+        const unsigned b0 = __ballot_sync(FULL, cnt & 1), b1 = __ballot_sync(FULL, cnt & 2);
+        const unsigned lt = lanemask_lt();
+        const int tot = __popc(b0) + 2 * __popc(b1);
+        int o = nnew + __popc(b0 & lt) + 2 * __popc(b1 & lt);
+        if (f0) { if (o < NSTAGE) S.stage[o] = e0; ++o; }
+        if (f1) { if (o < NSTAGE) S.stage[o] = e1; ++o; }
+        if (f2) { if (o < NSTAGE) S.stage[o] = e2; ++o; }
         nnew += tot;
     }
     __syncwarp();
@@ -416,6 +465,16 @@ __device__ void flush_batch(ClipSmem<PREC> &S, int &ncand, CellState &C, int lan
 {
     if (ncand == 0) return;
     sort_candidates(S, ncand, lane);
+    if constexpr (PREC == 1) {
+        // FP32 copies of the sorted planes, one lane per candidate
+        for (int k = lane; k < ncand; k += 32) {
+            S.u.c.fx[k] = (float)S.u.c.x[k];
+            S.u.c.fy[k] = (float)S.u.c.y[k];
+            S.u.c.fz[k] = (float)S.u.c.z[k];
+            S.u.c.fo[k] = (float)half_of(S.u.c.d2[k]);
+        }
+        __syncwarp();
+    }
     for (int k = 0; k < ncand; ++k) {
         if (S.u.c.d2[k] > C.lim) break;
         clip_by<PREC>(S, k, C, lane);
@@ -426,7 +485,7 @@ __device__ void flush_batch(ClipSmem<PREC> &S, int &ncand, CellState &C, int lan
 }
 
 template <int PREC>
-__global__ void __maxnreg__(128)
+__global__ void __maxnreg__(MM_CLIP_MAXNREG)
 k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, int64_t n,
        const BoxDev *__restrict__ boxes, const int *__restrict__ cbox, double *__restrict__ vol,
        double *__restrict__ cen, Slots sl, DevStatus *st, int collect, int cand_cap)
@@ -447,7 +506,7 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
     if (lane < 6) {
         const int d = lane >> 1;
         const double sg = (lane & 1) ? -1.0 : 1.0;
-        const double L = g.L[d];
+        const double L = d == 0 ? Lx : (d == 1 ? Ly : Lz);
         S.px[lane] = d == 0 ? sg * L : 0.0;
         S.py[lane] = d == 1 ? sg * L : 0.0;
         S.pz[lane] = d == 2 ? sg * L : 0.0;
@@ -605,15 +664,26 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
             S.u.f.a[p] = 0.0;
             if (t0 < 0) continue;  // plane no longer bounds the cell
             // Fan about the polygon's first vertex v0 with offsets d = v - v0
-            // formed once per vertex: edge (a, b) spans the triangle (v0, a, b)
-            // with w = q . (d_a x d_b) = 2 |q| times its signed area, so
-            // area = |sum w| / (2|q|), pyramid volume A |q| / 6 = |sum w| / 12,
-            // centroid = v0 + sum w (d_a + d_b) / (3 sum w).  Offsets from v0
-            // keep the rounding relative to the face's own size.
+            // formed once per vertex.  The offsets lie in the plane x.q = o,
+            // so d_a x d_b is parallel to q and q . (d_a x d_b) equals
+            // (|q|^2 / q_k) times the 2-D cross product of the two coordinates
+            // other than k, the axis where |q| is largest.  Edge (a, b) spans
+            // the triangle (v0, a, b) with 2-D weight w; with W = sum w:
+            // area = |W| |q| / (2 |q_k|), pyramid volume A |q| / 6 =
+            // |W| |q|^2 / (12 |q_k|), centroid offset = sum w (d_a + d_b) / (3 W)
+            // in the two kept coordinates, and in the k-th from the plane
+            // equation q . offset = 0.  Offsets from v0 keep the rounding
+            // relative to the face's own size.
             const double qx = S.px[p], qy = S.py[p], qz = S.pz[p];
-            const double x0 = S.tx[t0], y0 = S.ty[t0], z0 = S.tz[t0];
-            double ax = 0.0, ay = 0.0, az = 0.0;  // offset of the current vertex
-            double W = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+            const double aqx = fabs(qx), aqy = fabs(qy), aqz = fabs(qz);
+            const int k = (aqx >= aqy && aqx >= aqz) ? 0 : (aqy >= aqz ? 1 : 2);
+            const double *T1 = k == 0 ? S.ty : S.tx;  // kept coordinates (u, v)
+            const double *T2 = k == 2 ? S.ty : S.tz;
+            const double qk = k == 0 ? qx : (k == 1 ? qy : qz);
+            const double q1 = k == 0 ? qy : qx, q2 = k == 2 ? qy : qz;
+            const double u0 = T1[t0], v0 = T2[t0];
+            double au = 0.0, av = 0.0;  // offset of the current vertex
+            double W = 0.0, su = 0.0, sv = 0.0;
             int cnt = 0;
             bool ok = false;
             for (int guard = 0; guard < TMAX; ++guard) {
@@ -630,26 +700,29 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
                 if (tn < 0) break;
                 ++cnt;
                 if (tn == t0) { ok = true; break; }
-                const double bx = S.tx[tn] - x0, by = S.ty[tn] - y0, bz = S.tz[tn] - z0;
-                const double w = qx * (ay * bz - az * by) + qy * (az * bx - ax * bz) + qz * (ax * by - ay * bx);
+                const double bu = T1[tn] - u0, bv = T2[tn] - v0;
+                const double w = au * bv - av * bu;
                 W += w;
-                sx += w * (ax + bx);
-                sy += w * (ay + by);
-                sz += w * (az + bz);
-                ax = bx; ay = by; az = bz;
+                su += w * (au + bu);
+                sv += w * (av + bv);
+                au = bu; av = bv;
                 y = z;
             }
             fan += cnt;
             if (!ok) { C.err |= ST_EDEGEN; continue; }
             const double aw = fabs(W);
-            const double area = 0.5 * aw / sqrt(2.0 * S.po[p]);
+            const double qn2 = 2.0 * S.po[p];  // |q|^2
+            const double iq = 1.0 / qk, iqk = fabs(iq);
+            const double area = 0.5 * aw * (qn2 * rsqrt(qn2)) * iqk;
             const double i3w = W != 0.0 ? 1.0 / (3.0 * W) : 0.0;
-            const double fx = x0 + sx * i3w;
-            const double fy = y0 + sy * i3w;
-            const double fz = z0 + sz * i3w;
+            const double du = su * i3w, dv = sv * i3w;
+            const double dk = -(q1 * du + q2 * dv) * iq;
+            const double fx = S.tx[t0] + (k == 0 ? dk : du);
+            const double fy = S.ty[t0] + (k == 1 ? dk : (k == 0 ? du : dv));
+            const double fz = S.tz[t0] + (k == 2 ? dk : dv);
             S.u.f.a[p] = area;
             S.u.f.x[p] = fx; S.u.f.y[p] = fy; S.u.f.z[p] = fz;
-            const double vp = aw * (1.0 / 12.0);
+            const double vp = aw * qn2 * iqk * (1.0 / 12.0);
             vl += vp;
             vcx += 0.75 * vp * fx;
             vcy += 0.75 * vp * fy;
@@ -697,9 +770,10 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
         }
         sl.cnt[self] = nface;
         vol[self] = vl;
-        cen[self] = px + vcx / vl;
-        cen[n + self] = py + vcy / vl;
-        cen[2 * n + self] = pz + vcz / vl;
+        const double ivl = 1.0 / vl;
+        cen[self] = px + vcx * ivl;
+        cen[n + self] = py + vcy * ivl;
+        cen[2 * n + self] = pz + vcz * ivl;
         if (collect) {
             atomicMax(&st->max_cand, maxcand);
             atomicMax(&st->max_planes, C.np);

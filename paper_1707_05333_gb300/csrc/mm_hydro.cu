@@ -9,6 +9,10 @@ namespace mm {
 
 constexpr unsigned FULL_MASK_HYDRO = 0xffffffffu;
 
+#ifndef MM_GRAD_MINBLOCKS
+#define MM_GRAD_MINBLOCKS 1  // resident blocks per SM the gradient kernel is compiled for
+#endif
+
 __device__ __forceinline__ void decode_shift(int code, double &sx, double &sy, double &sz)
 {
     sx = (double)(code % 3 - 1);
@@ -24,6 +28,18 @@ struct Nbr {
     double ox, oy, oz;
 };
 
+// Flip the sign of x when the mask has the sign bit set (an integer op).
+__device__ __forceinline__ double flip(double x, long long smask)
+{
+    return __longlong_as_double(__double_as_longlong(x) ^ smask);
+}
+
+// One axis of an image offset: digit 0, 1, 2 of the image code means -L, 0, +L.
+__device__ __forceinline__ double image_axis(int digit, double L)
+{
+    return digit == 1 ? 0.0 : (digit == 2 ? L : -L);
+}
+
 __device__ __forceinline__ Nbr neighbour(const MeshDev &m, int e, const double *L)
 {
     Nbr r;
@@ -33,11 +49,11 @@ __device__ __forceinline__ Nbr neighbour(const MeshDev &m, int e, const double *
     r.f = f;
     r.o = fwd ? m.face_j[f] : m.face_i[f];
     r.sg = fwd ? 1.0 : -1.0;
-    double sx, sy, sz;
-    decode_shift(m.face_shift[f], sx, sy, sz);
-    r.ox = r.sg * sx * L[0];
-    r.oy = r.sg * sy * L[1];
-    r.oz = r.sg * sz * L[2];
+    const long long sm = fwd ? 0LL : (long long)0x8000000000000000ULL;
+    const int code = m.face_shift[f];
+    r.ox = flip(image_axis(code % 3, L[0]), sm);
+    r.oy = flip(image_axis((code / 3) % 3, L[1]), sm);
+    r.oz = flip(image_axis(code / 9, L[2]), sm);
     return r;
 }
 
@@ -63,7 +79,7 @@ __device__ __forceinline__ bool apply_floor(double W[5], double rho_floor, doubl
 // NG = 5 state columns, or 6 with the entropy column rho A (Sec. 4.3), which
 // is treated like the others and advected in the predictor.
 template <bool FROM_CHARGES, bool PREDICT, int NG>
-__global__ void __launch_bounds__(128) k_gradient(MeshDev m, HydroCfg c, const double *__restrict__ S,
+__global__ void __launch_bounds__(128, MM_GRAD_MINBLOCKS) k_gradient(MeshDev m, HydroCfg c, const double *__restrict__ S,
                                                   double *__restrict__ grad, double *__restrict__ Wh,
                                                   const double *__restrict__ dtp)
 {
@@ -85,12 +101,16 @@ __global__ void __launch_bounds__(128) k_gradient(MeshDev m, HydroCfg c, const d
     for (int k = 0; k < NG; ++k) { wmax[k] = Wi[k]; wmin[k] = Wi[k]; }
 #pragma unroll
     for (int k = 0; k < 3 * NG; ++k) b[k] = 0.0;
+    // (M and b are summed with A rather than A/2: the factor 2 cancels
+    // exactly in M^-1 b)
     for (int e = e0; e < e1; ++e) {
         const Nbr q = neighbour(m, e, L);
-        const double ha = 0.5 * m.area[q.f];
-        const double nx = q.sg * m.normal[q.f], ny = q.sg * m.normal[m.fs + q.f], nz = q.sg * m.normal[2 * m.fs + q.f];
+        const double A = m.area[q.f];
+        const long long sm = q.sg > 0.0 ? 0LL : (long long)0x8000000000000000ULL;
+        const double nx = flip(m.normal[q.f], sm), ny = flip(m.normal[m.fs + q.f], sm),
+                     nz = flip(m.normal[2 * m.fs + q.f], sm);
         const double dx = m.cen[q.o] + q.ox - cix, dy = m.cen[n + q.o] + q.oy - ciy, dz = m.cen[2 * n + q.o] + q.oz - ciz;
-        const double ax = ha * nx, ay = ha * ny, az = ha * nz;
+        const double ax = A * nx, ay = A * ny, az = A * nz;
         M[0] += ax * dx; M[1] += ax * dy; M[2] += ax * dz;
         M[3] += ay * dx; M[4] += ay * dy; M[5] += ay * dz;
         M[6] += az * dx; M[7] += az * dy; M[8] += az * dz;
