@@ -58,7 +58,7 @@ struct mm_ctx {
     int64_t nbins = 0, tess_n = 0;
     int64_t tables_gen = 0;  // bumped whenever the box tables are rewritten
     // binning
-    Buf bin_of, bin_count, bin_start, bin_cursor, sorted, scan_tmp;
+    Buf bin_of, bin_count, bin_start, bin_cursor, sorted, sortedf, scan_tmp;
     // clipping output
     Buf vol, cen, s_cnt, s_nb, s_sh, s_area, s_fc;
     // face compaction
@@ -375,7 +375,7 @@ static mm_status ensure_tess_buffers(mm_ctx *c, int64_t n)
     const size_t scan_n = (size_t)((nbins > n ? nbins : n) + 1);
     if ((r = ensure(c, c->bin_of, n * sizeof(int))) || (r = ensure(c, c->bin_count, (nbins + 1) * sizeof(int))) ||
         (r = ensure(c, c->bin_start, (nbins + 1) * sizeof(int))) || (r = ensure(c, c->bin_cursor, nbins * sizeof(int))) ||
-        (r = ensure(c, c->sorted, n * sizeof(double4_32a))) ||
+        (r = ensure(c, c->sorted, n * sizeof(double4_32a))) || (r = ensure(c, c->sortedf, n * sizeof(float4))) ||
         (r = ensure(c, c->scan_tmp, scan_tmp_size(scan_n) * sizeof(int))) || (r = ensure(c, c->vol, n * sizeof(double))) ||
         (r = ensure(c, c->cen, 3 * n * sizeof(double))) || (r = ensure(c, c->s_cnt, n * sizeof(int))) ||
         (r = ensure(c, c->s_nb, ns * sizeof(int))) || (r = ensure(c, c->s_sh, ns)) ||
@@ -403,14 +403,14 @@ static mm_status tess_enqueue(mm_ctx *c, const double *pos, bool fixed)
     launch_bin_count(pos, n, boxes, cbox, P<int>(c->bin_of), P<int>(c->bin_count), c->st, s);
     launch_scan(P<int>(c->bin_count), P<int>(c->bin_start), nbins, P<int>(c->scan_tmp), s);
     launch_bin_scatter(pos, n, P<int>(c->bin_of), P<int>(c->bin_start), P<int>(c->bin_cursor), P<double4_32a>(c->sorted), s);
-    launch_bin_sort(P<int>(c->bin_start), nbins, P<double4_32a>(c->sorted), s);
+    launch_bin_sort(P<int>(c->bin_start), nbins, P<double4_32a>(c->sorted), P<float4>(c->sortedf), s);
     CKLAUNCH();
     stage_mark(c, MM_STAGE_BIN, false);
     c->launches += 6;
 
     Slots sl{P<int>(c->s_cnt), P<int>(c->s_nb), P<unsigned char>(c->s_sh), P<double>(c->s_area), P<double>(c->s_fc)};
     stage_mark(c, MM_STAGE_CLIP, true);
-    launch_clip(P<double4_32a>(c->sorted), P<int>(c->bin_start), n, boxes, cbox, c->cfg.clip_filter ? 1 : 0,
+    launch_clip(P<double4_32a>(c->sorted), P<float4>(c->sortedf), P<int>(c->bin_start), n, boxes, cbox, c->cfg.clip_filter ? 1 : 0,
                 c->cfg.collect_stats,
                 c->cfg.clip_warps, c->cfg.cand_cap, P<double>(c->vol), P<double>(c->cen), sl, c->st, s);
     CKLAUNCH();
@@ -663,7 +663,7 @@ void mm_destroy(mm_ctx *c)
     cudaStreamSynchronize(c->stream);
     drop_graph(c);
     Buf *bufs[] = {&c->boxes_dev, &c->boxL_dev, &c->box_off_dev, &c->cbox, &c->bin_of, &c->bin_count, &c->bin_start,
-                   &c->bin_cursor, &c->sorted, &c->scan_tmp, &c->vol, &c->cen, &c->s_cnt, &c->s_nb, &c->s_sh,
+                   &c->bin_cursor, &c->sorted, &c->sortedf, &c->scan_tmp, &c->vol, &c->cen, &c->s_cnt, &c->s_nb, &c->s_sh,
                    &c->s_area, &c->s_fc, &c->emit_mask, &c->conf_mask, &c->partner, &c->emit_cnt, &c->conf_cnt,
                    &c->face_off, &c->inc_off, &c->face_i, &c->face_j, &c->face_shift, &c->face_area,
                    &c->face_normal, &c->face_cen, &c->inc_face, &c->Wh, &c->grad, &c->flux, &c->w_int, &c->dt_int,

@@ -70,7 +70,8 @@ __global__ void k_bin_scatter(const double *__restrict__ pos, int64_t n, const i
 // Order each bin's generators by index, so that everything downstream (the
 // candidate batches of the clipper, hence plane order and rounding) is
 // independent of the atomics' order.  Bins hold a handful of generators.
-__global__ void k_bin_sort(const int *__restrict__ start, int64_t nbins, double4_32a *__restrict__ sorted)
+__global__ void k_bin_sort(const int *__restrict__ start, int64_t nbins, double4_32a *__restrict__ sorted,
+                           float4 *__restrict__ sortedf)
 {
     int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (b >= nbins) return;
@@ -84,12 +85,17 @@ __global__ void k_bin_sort(const int *__restrict__ start, int64_t nbins, double4
         }
         sorted[m + 1] = v;
     }
+    // FP32 copies of the positions for the clipper's candidate filter
+    for (int k = lo; k < hi; ++k) {
+        const double4_32a v = sorted[k];
+        sortedf[k] = make_float4((float)v.x, (float)v.y, (float)v.z, 0.0f);
+    }
 }
 
-void launch_bin_sort(const int *start, int64_t nbins, double4_32a *sorted, cudaStream_t s)
+void launch_bin_sort(const int *start, int64_t nbins, double4_32a *sorted, float4 *sortedf, cudaStream_t s)
 {
     int nb = (int)((nbins + 255) / 256);
-    k_bin_sort<<<nb, 256, 0, s>>>(start, nbins, sorted);
+    k_bin_sort<<<nb, 256, 0, s>>>(start, nbins, sorted, sortedf);
 }
 
 void launch_bin_count(const double *pos, int64_t n, const BoxDev *boxes, const int *cbox, int *bin_of, int *count,

@@ -12,7 +12,7 @@
 //    the plane; the directed edges of removed triangles whose reverse edge is
 //    not also removed form the rim of the hole, and each rim edge x->y
 //    becomes a new triangle (x, y, k).  A 64x64 bit matrix in shared memory
-//    answers "is y->x removed" in O(1).
+//    answers "is y->x removed" in O(1); it is marked with 32-bit atomics.
 //  * Candidates come from a uniform grid of bins, ring by ring (Chebyshev
 //    distance in bins), filtered by |q| < 2 r_max, sorted by (|q|, id, image)
 //    with a warp bitonic sort, and clipped in that order.  The cell is
@@ -41,6 +41,7 @@ constexpr unsigned FULL = 0xffffffffu;
 #define MM_CLIP_MAXNREG 128  // registers per thread of the clipping kernel
 #endif
 constexpr int CBATCH = 64;  // candidate buffer; flushed (sorted + clipped) when full
+constexpr int ETAB = 256;   // edge hash table slots used by the face walk
 static_assert(CBATCH == PMAX, "the candidate buffer doubles as per-face storage");
 
 // Vertex storage.  PREC 0 keeps FP64 vertices throughout.  PREC 1 keeps FP32
@@ -53,7 +54,7 @@ template <>
 struct VertStore<0> {
     double tx[TMAX], ty[TMAX], tz[TMAX];
     long long tr2[TMAX];  // bits of |v|^2
-    float tfx[1], tfy[1], tfz[1], terr[1];
+    float4 tf[1];
 };
 template <>
 struct VertStore<1> {
@@ -63,7 +64,7 @@ struct VertStore<1> {
         };
         struct {
             long long tr2[TMAX];  // bits of an FP32 upper bound of |v|^2
-            float tfx[TMAX], tfy[TMAX], tfz[TMAX], terr[TMAX];
+            float4 tf[TMAX];      // FP32 vertex (x, y, z) and its error bound (w)
         };
     };
 };
@@ -74,19 +75,21 @@ struct ClipSmem : VertStore<PREC> {
         struct {
             double x[CBATCH], y[CBATCH], z[CBATCH];
             long long d2[CBATCH];  // bit pattern of |q|^2 (non-negative: orders like the value)
-            float fx[PREC ? CBATCH : 1], fy[PREC ? CBATCH : 1], fz[PREC ? CBATCH : 1], fo[PREC ? CBATCH : 1];
+            float4 cf[CBATCH];     // FP32 copies (q, |q|^2 / 2) for filtered clipping
         } c;
         struct {
             double a[PMAX], x[PMAX], y[PMAX], z[PMAX];  // per-face area and centroid
+            unsigned etab[ETAB];                        // directed edge -> (triangle, third corner)
         } f;
     } u;
     int cid[CBATCH], csh[CBATCH];
     double px[PMAX], py[PMAX], pz[PMAX], po[PMAX];  // planes x.q <= po
     int pnb[PMAX], psh[PMAX];
     unsigned tv[TMAX];                    // a | b << 8 | c << 16
-    unsigned long long bm[PMAX];          // removed directed edges x -> y
+    unsigned bm[2 * PMAX];                // removed directed edges x -> y: bit y % 32 of word 2x + y / 32
     unsigned stage[NSTAGE];               // triangles created by the current cut
-    float pfx[PREC ? PMAX : 1], pfy[PREC ? PMAX : 1], pfz[PREC ? PMAX : 1], pfo[PREC ? PMAX : 1];
+    float4 pf[PREC ? PMAX : 1];  // FP32 planes (q, o)
+    float pfn[PREC ? PMAX : 1];  // FP32 |q| = sqrt(2 o) of each plane (for the vertex error bound)
 };
 
 // floor(a / b) for b > 0 in integer arithmetic
@@ -166,24 +169,41 @@ __device__ __forceinline__ long long r2_bits64(double x, double y, double z)
 __device__ __forceinline__ void vertex32(const ClipSmem<1> &S, int a, int b, int c, float &x, float &y, float &z,
                                          float &err)
 {
-    const float ax = S.pfx[a], ay = S.pfy[a], az = S.pfz[a], ao = S.pfo[a];
-    const float bx = S.pfx[b], by = S.pfy[b], bz = S.pfz[b], bo = S.pfo[b];
-    const float cx = S.pfx[c], cy = S.pfy[c], cz = S.pfz[c], co = S.pfo[c];
+    const float4 Pa = S.pf[a], Pb = S.pf[b], Pc = S.pf[c];
+    const float ax = Pa.x, ay = Pa.y, az = Pa.z, ao = Pa.w;
+    const float bx = Pb.x, by = Pb.y, bz = Pb.z, bo = Pb.w;
+    const float cx = Pc.x, cy = Pc.y, cz = Pc.z, co = Pc.w;
     const float bcx = fmaf(by, cz, -bz * cy), bcy = fmaf(bz, cx, -bx * cz), bcz = fmaf(bx, cy, -by * cx);
     const float cax = fmaf(cy, az, -cz * ay), cay = fmaf(cz, ax, -cx * az), caz = fmaf(cx, ay, -cy * ax);
     const float abx = fmaf(ay, bz, -az * by), aby = fmaf(az, bx, -ax * bz), abz = fmaf(ax, by, -ay * bx);
     const float det = fmaf(ax, bcx, fmaf(ay, bcy, az * bcz));
-    const float inv = 1.0f / det;
+    const float inv = __frcp_rn(det);
     x = fmaf(ao, bcx, fmaf(bo, cax, co * abx)) * inv;
     y = fmaf(ao, bcy, fmaf(bo, cay, co * aby)) * inv;
     z = fmaf(ao, bcz, fmaf(bo, caz, co * abz)) * inv;
     // |q_k| = sqrt(2 o_k)
-    const float la = sqrtf(2.0f * ao), lb = sqrtf(2.0f * bo), lc = sqrtf(2.0f * co);
+    const float la = S.pfn[a], lb = S.pfn[b], lc = S.pfn[c];
     const float H = la * lb * lc / fabsf(det);
     const float vn = fabsf(x) + fabsf(y) + fabsf(z);
     const float u = 5.9604645e-8f;
     err = 3.0f * u * H * (5.5f * (la + lb + lc) + 13.0f * vn);
     if (!(u * H < 1e-3f) || !(err < 1e30f)) err = __int_as_float(0x7f800000);  // +inf
+}
+
+// The rare exact paths of the filtered clipper, kept out of line so that the
+// unrolled loops around them stay small: the FP64 plane test of a vertex the
+// FP32 bound cannot settle, and the FP64 solve of an ill-conditioned vertex.
+template <class S_t>
+__device__ __noinline__ bool beyond_exact(const S_t &S, unsigned v, double qx, double qy, double qz, double off)
+{
+    double x, y, z;
+    vertex64(S, v & 255u, (v >> 8) & 255u, (v >> 16) & 255u, x, y, z);
+    return beyond64(qx, qy, qz, off, x, y, z);
+}
+template <class S_t>
+__device__ __noinline__ void vertex64_call(const S_t &S, int a, int b, int c, double &x, double &y, double &z)
+{
+    vertex64(S, a, b, c, x, y, z);
 }
 
 // Candidate order: (|q|^2, id, image code).
@@ -236,6 +256,8 @@ __device__ void sort_candidates(ClipSmem<PREC> &S, int m, int lane)
 struct CellState {
     int np, nt;
     long long lim;  // bits of 4 r_max^2: a candidate with |q|^2 above it cannot cut
+    float limk;     // FP32 gather threshold: at least lim plus the FP32 rounding of |q|^2
+    float slack;    // 2e-6 max(L): the position-rounding term of that margin
     int err;
     int cuts;
     // work counters (warp-uniform), reported when the caller collects stats
@@ -247,9 +269,11 @@ __device__ __forceinline__ void update_limit(ClipSmem<PREC> &S, CellState &C, in
 {
     long long m = 0;
     for (int t = lane; t < C.nt; t += 32) m = max(m, S.tr2[t]);
+    float m4;
     if constexpr (PREC == 0) {
         m = warp_max_nonneg(m);
         C.lim = __double_as_longlong(4.0 * __longlong_as_double(m));
+        m4 = (float)__longlong_as_double(C.lim);
     } else {
         // the bounds are positive floats: their bit patterns fit 32 bits, and
         // 4 (double) f is f's exponent moved to the double bias plus two
@@ -260,7 +284,12 @@ __device__ __forceinline__ void update_limit(ClipSmem<PREC> &S, CellState &C, in
                                 ((unsigned long long)(fb & 0x7fffffu) << 29));
         else
             C.lim = __double_as_longlong(4.0 * (double)__int_as_float((int)fb));
+        m4 = 4.0f * __int_as_float((int)fb);
     }
+    // An FP32 |q|^2 from FP32 copies of positions and offsets is within
+    // 2e-7 |q|^2 + 1.3e-6 max(L) |q| of the exact one (positions and offsets
+    // below 3 max(L)): this threshold keeps every candidate the exact test would.
+    C.limk = fmaf(m4, 1.00001f, C.slack * sqrtf(m4));
 }
 
 // Clip the cell by candidate k.  Warp-uniform control flow throughout.
@@ -276,7 +305,8 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
     if (PREC == 0) C.pred64 += C.nt;
     float fqx = 0.f, fqy = 0.f, fqz = 0.f, foff = 0.f, fqn = 0.f;
     if constexpr (PREC == 1) {
-        fqx = S.u.c.fx[k]; fqy = S.u.c.fy[k]; fqz = S.u.c.fz[k]; foff = S.u.c.fo[k];
+        const float4 F = S.u.c.cf[k];
+        fqx = F.x; fqy = F.y; fqz = F.z; foff = F.w;
         fqn = sqrtf(2.0f * foff) * 1.0000005f;
     }
 #pragma unroll
@@ -292,10 +322,11 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
         } else {
             bool unsure = false;
             if (live) {
-                const float vx = S.tfx[t], vy = S.tfy[t], vz = S.tfz[t];
+                const float4 V = S.tf[t];
+                const float vx = V.x, vy = V.y, vz = V.z;
                 const float s = fmaf(fqx, vx, fmaf(fqy, vy, fmaf(fqz, vz, -foff)));
                 const float mag = fabsf(fqx * vx) + fabsf(fqy * vy) + fabsf(fqz * vz) + foff;
-                const float B = fqn * S.terr[t] + 16.0f * 5.9604645e-8f * mag;
+                const float B = fqn * V.w + 16.0f * 5.9604645e-8f * mag;
                 if (fabsf(s) > B) o = s > 0.0f;
                 else unsure = true;
             }
@@ -303,39 +334,43 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
             if (um) {
                 C.pred64 += __popc(um);
                 C.solve64 += __popc(um);
-                if (unsure) {
-                    const unsigned v = S.tv[t];
-                    double x, y, z;
-                    vertex64(S, v & 255u, (v >> 8) & 255u, (v >> 16) & 255u, x, y, z);
-                    o = beyond64(qx, qy, qz, off, x, y, z);
-                }
+                if (unsure) o = beyond_exact(S, S.tv[t], qx, qy, qz, off);
             }
         }
         outm[c] = __ballot_sync(FULL, o);
         anyv |= outm[c];
     }
     if (anyv == 0) return;
-    // the new plane takes the lowest slot no vertex refers to (a face that has
-    // vanished frees its slot), else a fresh one: PMAX bounds the live faces
-    unsigned long long live = 0ull;
-    for (int t = lane; t < C.nt; t += 32) {
-        const unsigned v = S.tv[t];
-        live |= (1ull << (v & 255u)) | (1ull << ((v >> 8) & 255u)) | (1ull << ((v >> 16) & 255u));
-    }
-    live = warp_or64(live);
-    const unsigned long long used = C.np >= 64 ? ~0ull : ((1ull << C.np) - 1ull);
-    const unsigned long long freeb = used & ~live;
+    // the new plane takes a fresh slot while fewer than 32 are in use (one
+    // lane per face when the faces are summed); beyond that, the lowest slot
+    // no vertex refers to (a face that has vanished frees its slot), else a
+    // fresh one: PMAX bounds the live faces
     int kp;
-    if (freeb) {
-        kp = __ffsll((long long)freeb) - 1;
-    } else {
-        if (C.np >= PMAX) { C.err |= ST_ECAP_PLANE; return; }
+    if (C.np < 32) {
         kp = C.np;
+    } else {
+        unsigned long long live = 0ull;
+        for (int t = lane; t < C.nt; t += 32) {
+            const unsigned v = S.tv[t];
+            live |= (1ull << (v & 255u)) | (1ull << ((v >> 8) & 255u)) | (1ull << ((v >> 16) & 255u));
+        }
+        live = warp_or64(live);
+        const unsigned long long used = C.np >= 64 ? ~0ull : ((1ull << C.np) - 1ull);
+        const unsigned long long freeb = used & ~live;
+        if (freeb) {
+            kp = __ffsll((long long)freeb) - 1;
+        } else {
+            if (C.np >= PMAX) { C.err |= ST_ECAP_PLANE; return; }
+            kp = C.np;
+        }
     }
     if (lane == 0) {
         S.px[kp] = qx; S.py[kp] = qy; S.pz[kp] = qz; S.po[kp] = off;
         S.pnb[kp] = S.cid[k]; S.psh[kp] = S.csh[k];
-        if constexpr (PREC == 1) { S.pfx[kp] = fqx; S.pfy[kp] = fqy; S.pfz[kp] = fqz; S.pfo[kp] = foff; }
+        if constexpr (PREC == 1) {
+            S.pf[kp] = make_float4(fqx, fqy, fqz, foff);
+            S.pfn[kp] = sqrtf(2.0f * foff);
+        }
     }
     // mark the directed edges of the removed triangles
 #pragma unroll
@@ -344,9 +379,9 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
         if ((outm[c] >> lane) & 1u) {
             unsigned v = S.tv[c * 32 + lane];
             unsigned a = v & 255u, b = (v >> 8) & 255u, cc = (v >> 16) & 255u;
-            atomicOr(&S.bm[a], 1ull << b);
-            atomicOr(&S.bm[b], 1ull << cc);
-            atomicOr(&S.bm[cc], 1ull << a);
+            atomicOr(&S.bm[2 * a + (b >> 5)], 1u << (b & 31u));
+            atomicOr(&S.bm[2 * b + (cc >> 5)], 1u << (cc & 31u));
+            atomicOr(&S.bm[2 * cc + (a >> 5)], 1u << (a & 31u));
         }
     }
     __syncwarp();
@@ -364,9 +399,9 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
             const unsigned v = S.tv[c * 32 + lane];
             const unsigned a = v & 255u, b = (v >> 8) & 255u, cc = (v >> 16) & 255u;
             const unsigned hk = (unsigned)kp << 16;
-            f0 = !((S.bm[b] >> a) & 1ull);   // a -> b
-            f1 = !((S.bm[cc] >> b) & 1ull);  // b -> cc
-            f2 = !((S.bm[a] >> cc) & 1ull);  // cc -> a
+            f0 = !((S.bm[2 * b + (a >> 5)] >> (a & 31u)) & 1u);    // a -> b
+            f1 = !((S.bm[2 * cc + (b >> 5)] >> (b & 31u)) & 1u);   // b -> cc
+            f2 = !((S.bm[2 * a + (cc >> 5)] >> (cc & 31u)) & 1u);  // cc -> a
             e0 = a | (b << 8) | hk;
             e1 = b | (cc << 8) | hk;
             e2 = cc | (a << 8) | hk;
@@ -386,7 +421,7 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
         nnew += tot;
     }
     __syncwarp();
-    for (int r = lane; r < C.np; r += 32) S.bm[r] = 0ull;
+    for (int r = lane; r < 2 * C.np; r += 32) S.bm[r] = 0u;
     xs = warp_or64(xs);
     ys = warp_or64(ys);
     if (nnew > NSTAGE) { C.err |= ST_ECAP_STAGE; return; }
@@ -407,12 +442,12 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
         unsigned v = 0;
         long long r2 = 0;
         double x = 0, y = 0, z = 0;
-        float fx = 0, fy = 0, fz = 0, fe = 0;
+        float4 fv = make_float4(0.f, 0.f, 0.f, 0.f);
         if (keep) {
             v = S.tv[t];
             r2 = S.tr2[t];
             if constexpr (PREC == 0) { x = S.tx[t]; y = S.ty[t]; z = S.tz[t]; }
-            else { fx = S.tfx[t]; fy = S.tfy[t]; fz = S.tfz[t]; fe = S.terr[t]; }
+            else fv = S.tf[t];
         }
         __syncwarp();
         if (keep) {
@@ -420,7 +455,7 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
             S.tv[d] = v;
             S.tr2[d] = r2;
             if constexpr (PREC == 0) { S.tx[d] = x; S.ty[d] = y; S.tz[d] = z; }
-            else { S.tfx[d] = fx; S.tfy[d] = fy; S.tfz[d] = fz; S.terr[d] = fe; }
+            else S.tf[d] = fv;
         }
         dst += __popc(km);
         __syncwarp();
@@ -442,14 +477,16 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
                 // ill-conditioned intersection: solve it in FP64 now and keep
                 // its FP32 rounding, whose error is then one rounding per axis
                 double X, Y, Z;
-                vertex64(S, v & 255u, (v >> 8) & 255u, kp, X, Y, Z);
+                vertex64_call(S, v & 255u, (v >> 8) & 255u, kp, X, Y, Z);
                 x = (float)X; y = (float)Y; z = (float)Z;
                 er = 1.2e-7f * (fabsf(x) + fabsf(y) + fabsf(z)) + 1e-38f;
             }
-            S.tfx[t] = x; S.tfy[t] = y; S.tfz[t] = z; S.terr[t] = er;
-            // an FP32 upper bound of |v|^2, kept as the bit pattern of a positive float
-            const float r = sqrtf(x * x + y * y + z * z) * 1.000001f + er;
-            S.tr2[t] = (long long)__float_as_int(r * r * 1.000001f);
+            S.tf[t] = make_float4(x, y, z, er);
+            // an FP32 upper bound of (|v| + er)^2 <= |v|^2 + er (2 |v|_1 + er),
+            // kept as the bit pattern of a positive float
+            const float s2 = fmaf(x, x, fmaf(y, y, z * z));
+            const float l1 = fabsf(x) + fabsf(y) + fabsf(z);
+            S.tr2[t] = (long long)__float_as_int(fmaf(er, fmaf(2.0f, l1, er), s2) * 1.00001f);
         }
     }
     __syncwarp();
@@ -460,18 +497,38 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
     update_limit(S, C, lane);
 }
 
+// What a flush needs to form the exact candidate planes: the binned
+// generators, this generator and the box.
+struct Gather {
+    const double4_32a *sorted;
+    double px, py, pz, Lx, Ly, Lz;
+};
+
 template <int PREC>
-__device__ void flush_batch(ClipSmem<PREC> &S, int &ncand, CellState &C, int lane)
+__device__ void flush_batch(ClipSmem<PREC> &S, int &ncand, CellState &C, int lane, const Gather &G)
 {
     if (ncand == 0) return;
+    // exact planes, one lane per candidate: q = r_j + s L - p in FP64 and the
+    // bit pattern of |q|^2 (the sort key); the buffer held the sorted index
+    for (int k = lane; k < ncand; k += 32) {
+        const int code = S.csh[k];
+        const double4_32a P = G.sorted[S.cid[k]];
+        const int dx = code % 3, dy = (code / 3) % 3, dz = code / 9;
+        const double ox = dx == 0 ? -G.Lx - G.px : (dx == 2 ? G.Lx - G.px : -G.px);
+        const double oy = dy == 0 ? -G.Ly - G.py : (dy == 2 ? G.Ly - G.py : -G.py);
+        const double oz = dz == 0 ? -G.Lz - G.pz : (dz == 2 ? G.Lz - G.pz : -G.pz);
+        const double qx = P.x + ox, qy = P.y + oy, qz = P.z + oz;
+        S.u.c.x[k] = qx; S.u.c.y[k] = qy; S.u.c.z[k] = qz;
+        S.u.c.d2[k] = __double_as_longlong(__fma_rn(qx, qx, __fma_rn(qy, qy, __dmul_rn(qz, qz))));
+        S.cid[k] = (int)__double_as_longlong(P.w);
+    }
+    __syncwarp();
     sort_candidates(S, ncand, lane);
     if constexpr (PREC == 1) {
         // FP32 copies of the sorted planes, one lane per candidate
         for (int k = lane; k < ncand; k += 32) {
-            S.u.c.fx[k] = (float)S.u.c.x[k];
-            S.u.c.fy[k] = (float)S.u.c.y[k];
-            S.u.c.fz[k] = (float)S.u.c.z[k];
-            S.u.c.fo[k] = (float)half_of(S.u.c.d2[k]);
+            S.u.c.cf[k] = make_float4((float)S.u.c.x[k], (float)S.u.c.y[k], (float)S.u.c.z[k],
+                                      (float)half_of(S.u.c.d2[k]));
         }
         __syncwarp();
     }
@@ -486,7 +543,8 @@ __device__ void flush_batch(ClipSmem<PREC> &S, int &ncand, CellState &C, int lan
 
 template <int PREC>
 __global__ void __maxnreg__(MM_CLIP_MAXNREG)
-k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, int64_t n,
+k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sortedf, const int *__restrict__ start,
+       int64_t n,
        const BoxDev *__restrict__ boxes, const int *__restrict__ cbox, double *__restrict__ vol,
        double *__restrict__ cen, Slots sl, DevStatus *st, int collect, int cand_cap)
 {
@@ -516,8 +574,9 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
         s3[d] = (lane & 1) ? -1 : 1;
         S.psh[lane] = (s3[0] + 1) + 3 * (s3[1] + 1) + 9 * (s3[2] + 1);
         if constexpr (PREC == 1) {
-            S.pfx[lane] = (float)S.px[lane]; S.pfy[lane] = (float)S.py[lane]; S.pfz[lane] = (float)S.pz[lane];
-            S.pfo[lane] = (float)S.po[lane];
+            const float fo = (float)S.po[lane];
+            S.pf[lane] = make_float4((float)S.px[lane], (float)S.py[lane], (float)S.pz[lane], fo);
+            S.pfn[lane] = sqrtf(2.0f * fo);
         }
     }
     if (lane < 8) {
@@ -531,14 +590,16 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
         if constexpr (PREC == 0) S.tr2[lane] = r2_bits64(x, y, z);
         else S.tr2[lane] = (long long)__float_as_int((float)(x * x + y * y + z * z) * 1.000001f);
         if constexpr (PREC == 0) { S.tx[lane] = x; S.ty[lane] = y; S.tz[lane] = z; }
-        else { S.tfx[lane] = (float)x; S.tfy[lane] = (float)y; S.tfz[lane] = (float)z; S.terr[lane] = 0.0f; }
+        else S.tf[lane] = make_float4((float)x, (float)y, (float)z, 0.0f);
     }
-    for (int r = lane; r < PMAX; r += 32) S.bm[r] = 0ull;
+    for (int r = lane; r < 2 * PMAX; r += 32) S.bm[r] = 0u;
     __syncwarp();
     CellState C;
     C.np = 6;
     C.nt = 8;
     C.lim = __double_as_longlong(Lx * Lx + Ly * Ly + Lz * Lz);
+    C.limk = __int_as_float(0x7f800000);  // keep everything until the first cut
+    C.slack = 2e-6f * (float)fmax(Lx, fmax(Ly, Lz));
     C.err = 0;
     C.cuts = 0;
     C.pred64 = C.solve64 = C.fan64 = C.tested = 0;
@@ -553,6 +614,7 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
         }
     }
     // image offsets s L - p for s = -1, 0, +1 (selected, not recomputed, per bin)
+    const Gather G{sorted, px, py, pz, Lx, Ly, Lz};
     const double omx = -Lx - px, o0x = -px, opx = Lx - px;
     const double omy = -Ly - py, o0y = -py, opy = Ly - py;
     const double omz = -Lz - pz, o0z = -pz, opz = Lz - pz;
@@ -580,9 +642,11 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
                 const int ch = max(abs(ox), max(abs(oy), abs(oz)));
                 if (ch >= rl) {
                     int bx = cb[0] + ox, by = cb[1] + oy, bz = cb[2] + oz;
-                    shx = floordiv(bx, g.g[0]);
-                    shy = floordiv(by, g.g[1]);
-                    shz = floordiv(bz, g.g[2]);
+                    // the image of a bin index: comparisons for the usual
+                    // range [-g, 2g), a division beyond it (rings wider than the grid)
+                    shx = (bx >= -g.g[0] && bx < 2 * g.g[0]) ? (bx < 0 ? -1 : (bx >= g.g[0] ? 1 : 0)) : floordiv(bx, g.g[0]);
+                    shy = (by >= -g.g[1] && by < 2 * g.g[1]) ? (by < 0 ? -1 : (by >= g.g[1] ? 1 : 0)) : floordiv(by, g.g[1]);
+                    shz = (bz >= -g.g[2] && bz < 2 * g.g[2]) ? (bz < 0 ? -1 : (bz >= g.g[2] ? 1 : 0)) : floordiv(bz, g.g[2]);
                     bx -= shx * g.g[0];
                     by -= shy * g.g[1];
                     bz -= shz * g.g[2];
@@ -593,38 +657,36 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
                     if (abs(shx) > 1 || abs(shy) > 1 || abs(shz) > 1) end = cur;
                 }
             }
-            const double offx = shx < 0 ? omx : (shx > 0 ? opx : o0x);
-            const double offy = shy < 0 ? omy : (shy > 0 ? opy : o0y);
-            const double offz = shz < 0 ? omz : (shz > 0 ? opz : o0z);
+            // FP32 offsets for the gather filter (the exact ones are formed at flush time)
+            const float offx = (float)(shx < 0 ? omx : (shx > 0 ? opx : o0x));
+            const float offy = (float)(shy < 0 ? omy : (shy > 0 ? opy : o0y));
+            const float offz = (float)(shz < 0 ? omz : (shz > 0 ? opz : o0z));
             const int code = (shx + 1) + 3 * (shy + 1) + 9 * (shz + 1);
             const bool selfimg = (abs(shx) + abs(shy) + abs(shz)) <= 1;
             while (__any_sync(FULL, cur < end)) {
-                if (ncand + 32 > cand_cap) flush_batch<PREC>(S, ncand, C, lane);
+                if (ncand + 32 > cand_cap) flush_batch<PREC>(S, ncand, C, lane, G);
                 if (C.err) break;
                 bool keep = false;
-                double qx = 0, qy = 0, qz = 0;
-                long long d2b = 0;
-                int j = 0;
+                const int idx = cur;
                 if (cur < end) {
-                    const double4_32a P = sorted[cur];
+                    const float4 Pf = sortedf[cur];
                     ++cur;
-                    j = (int)__double_as_longlong(P.w);
-                    qx = P.x + offx; qy = P.y + offy; qz = P.z + offz;
-                    d2b = __double_as_longlong(__fma_rn(qx, qx, __fma_rn(qy, qy, __dmul_rn(qz, qz))));
-                    keep = !(j == self && selfimg) && d2b < C.lim;
+                    const float qx = Pf.x + offx, qy = Pf.y + offy, qz = Pf.z + offz;
+                    const float d2f = fmaf(qx, qx, fmaf(qy, qy, qz * qz));
+                    // the generator itself is sorted entry w
+                    keep = !((int64_t)idx == w && selfimg) && d2f <= C.limk;
                 }
                 const unsigned km = __ballot_sync(FULL, keep);
                 if (keep) {
                     const int s = ncand + __popc(km & lanemask_lt());
-                    S.u.c.x[s] = qx; S.u.c.y[s] = qy; S.u.c.z[s] = qz; S.u.c.d2[s] = d2b;
-                    S.cid[s] = j; S.csh[s] = code;
+                    S.cid[s] = idx; S.csh[s] = code;
                 }
                 ncand += __popc(km);
                 maxcand = max(maxcand, ncand);
                 __syncwarp();
             }
         }
-        flush_batch<PREC>(S, ncand, C, lane);
+        flush_batch<PREC>(S, ncand, C, lane, G);
         ++rings;
         // radius the gathered rings are guaranteed to cover
         const double rr = (double)rh;
@@ -650,16 +712,56 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
     }
     double vl = 0.0, vcx = 0.0, vcy = 0.0, vcz = 0.0;
     unsigned fan = 0;  // polygon edges summed (work counter)
+    // Edge table for the face walk: every directed edge x -> y of a vertex
+    // triangle (x, y, z) maps to that triangle and z, so the next vertex
+    // around a face is one lookup.  Keys are unique in a closed
+    // triangulation; the load stays below 3/4 (else the walk scans instead).
+    // The first triangle of each face is the lowest index containing it.
+    const bool use_tab = !C.err && 3 * C.nt <= (3 * ETAB) / 4;
+    unsigned *etab = S.u.f.etab;
+    int *first = S.cid;  // the candidate ids are dead after clipping
+    if (use_tab) {
+        for (int i = lane; i < ETAB; i += 32) etab[i] = 0xffffffffu;
+        for (int i = lane; i < C.np; i += 32) first[i] = 0x7fffffff;
+        __syncwarp();
+        for (int e = lane; e < 3 * C.nt; e += 32) {
+            const int t = e / 3, k = e - 3 * (e / 3);
+            const unsigned v = S.tv[t];
+            const unsigned a = v & 255u, b = (v >> 8) & 255u, c = (v >> 16) & 255u;
+            const unsigned x = k == 0 ? a : (k == 1 ? b : c);
+            const unsigned y = k == 0 ? b : (k == 1 ? c : a);
+            const unsigned z = k == 0 ? c : (k == 1 ? a : b);
+            const unsigned key = x * 64u + y;
+            const unsigned ent = (key << 13) | (z << 7) | (unsigned)t;
+            unsigned h = (key * 2654435761u) >> 24;
+            for (int probe = 0; probe < ETAB; ++probe) {
+                if (atomicCAS(&etab[h], 0xffffffffu, ent) == 0xffffffffu) break;
+                h = (h + 1) & (ETAB - 1);
+            }
+            atomicMin(&first[x], t);
+        }
+        __syncwarp();
+    }
     if (!C.err) {
         for (int p = lane; p < C.np; p += 32) {
             int t0 = -1;
             unsigned y = 0;
-            for (int t = 0; t < C.nt; ++t) {
-                const unsigned v = S.tv[t];
-                const unsigned a = v & 255u, b = (v >> 8) & 255u, c = (v >> 16) & 255u;
-                if (a == (unsigned)p) { t0 = t; y = c; break; }
-                if (b == (unsigned)p) { t0 = t; y = a; break; }
-                if (c == (unsigned)p) { t0 = t; y = b; break; }
+            if (use_tab) {
+                const int f0 = first[p];
+                if (f0 != 0x7fffffff) {
+                    t0 = f0;
+                    const unsigned v = S.tv[t0];
+                    const unsigned a = v & 255u, b = (v >> 8) & 255u, c = (v >> 16) & 255u;
+                    y = a == (unsigned)p ? c : (b == (unsigned)p ? a : b);
+                }
+            } else {
+                for (int t = 0; t < C.nt; ++t) {
+                    const unsigned v = S.tv[t];
+                    const unsigned a = v & 255u, b = (v >> 8) & 255u, c = (v >> 16) & 255u;
+                    if (a == (unsigned)p) { t0 = t; y = c; break; }
+                    if (b == (unsigned)p) { t0 = t; y = a; break; }
+                    if (c == (unsigned)p) { t0 = t; y = b; break; }
+                }
             }
             S.u.f.a[p] = 0.0;
             if (t0 < 0) continue;  // plane no longer bounds the cell
@@ -690,12 +792,23 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
                 // next vertex around p: the triangle containing p -> y
                 int tn = -1;
                 unsigned z = 0;
-                for (int t = 0; t < C.nt; ++t) {
-                    const unsigned v = S.tv[t];
-                    const unsigned a = v & 255u, b = (v >> 8) & 255u, c = (v >> 16) & 255u;
-                    if (a == (unsigned)p && b == y) { tn = t; z = c; break; }
-                    if (b == (unsigned)p && c == y) { tn = t; z = a; break; }
-                    if (c == (unsigned)p && a == y) { tn = t; z = b; break; }
+                if (use_tab) {
+                    const unsigned key = (unsigned)p * 64u + y;
+                    unsigned h = (key * 2654435761u) >> 24;
+                    for (int probe = 0; probe < ETAB; ++probe) {
+                        const unsigned ent = etab[h];
+                        if (ent == 0xffffffffu) break;
+                        if ((ent >> 13) == key) { tn = (int)(ent & 127u); z = (ent >> 7) & 63u; break; }
+                        h = (h + 1) & (ETAB - 1);
+                    }
+                } else {
+                    for (int t = 0; t < C.nt; ++t) {
+                        const unsigned v = S.tv[t];
+                        const unsigned a = v & 255u, b = (v >> 8) & 255u, c = (v >> 16) & 255u;
+                        if (a == (unsigned)p && b == y) { tn = t; z = c; break; }
+                        if (b == (unsigned)p && c == y) { tn = t; z = a; break; }
+                        if (c == (unsigned)p && a == y) { tn = t; z = b; break; }
+                    }
                 }
                 if (tn < 0) break;
                 ++cnt;
@@ -789,7 +902,8 @@ k_clip(const double4_32a *__restrict__ sorted, const int *__restrict__ start, in
 }
 
 template <int PREC>
-static void launch_clip_t(const double4_32a *sorted, const int *start, int64_t n, const BoxDev *boxes,
+static void launch_clip_t(const double4_32a *sorted, const float4 *sortedf, const int *start, int64_t n,
+                          const BoxDev *boxes,
                           const int *cbox, double *vol, double *cen, Slots sl, DevStatus *st, int collect,
                           int warps, int cand_cap, cudaStream_t s)
 {
@@ -801,18 +915,20 @@ static void launch_clip_t(const double4_32a *sorted, const int *start, int64_t n
     }
     const size_t smem = sizeof(ClipSmem<PREC>) * warps;
     const int64_t nb = (n + warps - 1) / warps;
-    k_clip<PREC><<<(unsigned)nb, 32 * warps, smem, s>>>(sorted, start, n, boxes, cbox, vol, cen, sl, st, collect,
+    k_clip<PREC><<<(unsigned)nb, 32 * warps, smem, s>>>(sorted, sortedf, start, n, boxes, cbox, vol, cen, sl, st,
+                                                         collect,
                                                          cand_cap);
 }
 
-void launch_clip(const double4_32a *sorted, const int *start, int64_t n, const BoxDev *boxes, const int *cbox,
+void launch_clip(const double4_32a *sorted, const float4 *sortedf, const int *start, int64_t n, const BoxDev *boxes,
+                 const int *cbox,
                  int precision, int collect, int warps, int cand_cap, double *vol, double *cen, Slots sl,
                  DevStatus *st, cudaStream_t s)
 {
     warps = warps < 1 ? 1 : (warps > CLIP_MAX_WARPS ? CLIP_MAX_WARPS : warps);
     cand_cap = cand_cap < 32 ? 32 : (cand_cap > CBATCH ? CBATCH : cand_cap);
-    if (precision == 0) launch_clip_t<0>(sorted, start, n, boxes, cbox, vol, cen, sl, st, collect, warps, cand_cap, s);
-    else launch_clip_t<1>(sorted, start, n, boxes, cbox, vol, cen, sl, st, collect, warps, cand_cap, s);
+    if (precision == 0) launch_clip_t<0>(sorted, sortedf, start, n, boxes, cbox, vol, cen, sl, st, collect, warps, cand_cap, s);
+    else launch_clip_t<1>(sorted, sortedf, start, n, boxes, cbox, vol, cen, sl, st, collect, warps, cand_cap, s);
 }
 
 }  // namespace mm

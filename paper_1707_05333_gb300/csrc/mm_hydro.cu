@@ -179,9 +179,12 @@ __global__ void __launch_bounds__(128, MM_GRAD_MINBLOCKS) k_gradient(MeshDev m, 
         }
 #pragma unroll
         for (int k = 0; k < NG; ++k) {
+            // the ratios matter only below 1 (min(1, x)), so most cells skip the
+            // FP64 divisions: x < 1 exactly when the numerator is the smaller
             double a = 1.0;
-            if (dmax[k] > 0.0) a = fmin(a, (wmax[k] - Wi[k]) / dmax[k]);
-            if (dmin[k] < 0.0) a = fmin(a, (wmin[k] - Wi[k]) / dmin[k]);
+            const double up = wmax[k] - Wi[k], dn = wmin[k] - Wi[k];
+            if (dmax[k] > 0.0 && up < dmax[k]) a = fmin(a, up / dmax[k]);
+            if (dmin[k] < 0.0 && dn > dmin[k]) a = fmin(a, dn / dmin[k]);
             if (c.limiter == 2) a *= fmin(1.0, rn[k] / rd[k]);
             g[3 * k] *= a;
             g[3 * k + 1] *= a;

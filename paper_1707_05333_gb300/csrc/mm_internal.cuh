@@ -71,12 +71,13 @@ void launch_bin_count(const double *pos, int64_t n, const BoxDev *boxes, const i
                       DevStatus *st, cudaStream_t s);
 void launch_bin_scatter(const double *pos, int64_t n, const int *bin_of, const int *start, int *cursor,
                         double4_32a *sorted, cudaStream_t s);
-void launch_bin_sort(const int *start, int64_t nbins, double4_32a *sorted, cudaStream_t s);
+void launch_bin_sort(const int *start, int64_t nbins, double4_32a *sorted, float4 *sortedf, cudaStream_t s);
 // exclusive scan of in[0..n) into out[0..n], out[n] = total; tmp >= scan_tmp_size(n) ints
 size_t scan_tmp_size(int64_t n);
 void launch_scan(const int *in, int *out, int64_t n, int *tmp, cudaStream_t s);
 
-void launch_clip(const double4_32a *sorted, const int *start, int64_t n, const BoxDev *boxes, const int *cbox,
+void launch_clip(const double4_32a *sorted, const float4 *sortedf, const int *start, int64_t n, const BoxDev *boxes,
+                 const int *cbox,
                  int precision, int collect, int warps, int cand_cap, double *vol, double *cen, Slots sl,
                  DevStatus *st, cudaStream_t s);
 

@@ -172,3 +172,31 @@ def test_autotune_picks_a_valid_setting(ctx):
         assert mesh.nfaces > 0
     finally:
         c.set_config(clip_warps=4, cand_cap=64, bin_scale=1.0)
+
+
+def test_rejects_bad_sizes_and_boxes(ctx):
+    """n outside [1, MM_MAX_CELLS], non-positive box sizes and empty boxes of a
+    batch are refused with MM_EINVAL before any device memory is touched, and
+    the context stays usable."""
+    import ctypes
+    from paper_1707_05333_gb300 import binding
+    c, torch = ctx
+    pos = H.to_dev(torch, WL.random_points(64, seed=12).T)
+    p = ctypes.c_void_p(pos.data_ptr())
+    box = (ctypes.c_double * 3)(1.0, 1.0, 1.0)
+    for n in (0, -5, 100_000_001):
+        assert c.L.mm_tessellate(c.h, p, n, box, ctypes.byref(binding.MeshStruct())) == 1
+    bad = (ctypes.c_double * 3)(1.0, 0.0, 1.0)
+    assert c.L.mm_tessellate(c.h, p, 64, bad, ctypes.byref(binding.MeshStruct())) == 1
+    # a batch whose second box is empty
+    off = (ctypes.c_int64 * 3)(0, 64, 64)
+    boxes = (ctypes.c_double * 6)(1.0, 1.0, 1.0, 1.0, 1.0, 1.0)
+    U = torch.zeros((5, 64), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = binding.Context(stream=stream)
+        st = b.L.mm_step_batched(b.h, p, ctypes.c_void_p(U.data_ptr()), 64, off, boxes, 2, None)
+        assert st == 1
+        b.close()
+    _, _, G = H.gpu_tessellate(c, torch, WL.random_points(64, seed=12), np.ones(3))
+    assert abs(G["cell_volume"].sum() - 1.0) < 1e-12
