@@ -293,14 +293,31 @@ __device__ __forceinline__ void update_limit(ClipSmem<PREC> &S, CellState &C, in
 }
 
 // Clip the cell by candidate k.  Warp-uniform control flow throughout.
+// The removed-vertex masks of a cut, one 32-bit ballot per chunk of 32
+// vertices, held in two 64-bit registers: the chunk loops then need no
+// unrolling to keep them out of local memory (a smaller kernel body).
+struct ChunkMask {
+    unsigned long long lo = 0ull, hi = 0ull;
+    __device__ __forceinline__ unsigned get(int c) const
+    {
+        return (unsigned)((c < 2 ? lo : hi) >> (32 * (c & 1)));
+    }
+    __device__ __forceinline__ void put(int c, unsigned m)
+    {
+        const unsigned long long v = (unsigned long long)m << (32 * (c & 1));
+        if (c < 2) lo |= v;
+        else hi |= v;
+    }
+    __device__ __forceinline__ int count() const { return __popcll(lo) + __popcll(hi); }
+};
+
 template <int PREC>
 __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
 {
     const double qx = S.u.c.x[k], qy = S.u.c.y[k], qz = S.u.c.z[k];
     const double off = half_of(S.u.c.d2[k]);
     const int nchunk = (C.nt + 31) >> 5;
-    unsigned outm[TMAX / 32];
-    unsigned anyv = 0;
+    ChunkMask outm;
     C.tested++;
     if (PREC == 0) C.pred64 += C.nt;
     float fqx = 0.f, fqy = 0.f, fqz = 0.f, foff = 0.f, fqn = 0.f;
@@ -309,11 +326,8 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
         fqx = F.x; fqy = F.y; fqz = F.z; foff = F.w;
         fqn = sqrtf(2.0f * foff) * 1.0000005f;
     }
-#pragma unroll
-    for (int c = 0; c < TMAX / 32; ++c) outm[c] = 0u;
-#pragma unroll
-    for (int c = 0; c < TMAX / 32; ++c) {
-        if (c >= nchunk) break;
+#pragma unroll 1
+    for (int c = 0; c < nchunk; ++c) {
         bool o = false;
         const int t = c * 32 + lane;
         const bool live = t < C.nt;
@@ -337,10 +351,9 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
                 if (unsure) o = beyond_exact(S, S.tv[t], qx, qy, qz, off);
             }
         }
-        outm[c] = __ballot_sync(FULL, o);
-        anyv |= outm[c];
+        outm.put(c, __ballot_sync(FULL, o));
     }
-    if (anyv == 0) return;
+    if ((outm.lo | outm.hi) == 0ull) return;
     // the new plane takes a fresh slot while fewer than 32 are in use (one
     // lane per face when the faces are summed); beyond that, the lowest slot
     // no vertex refers to (a face that has vanished frees its slot), else a
@@ -373,10 +386,9 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
         }
     }
     // mark the directed edges of the removed triangles
-#pragma unroll
-    for (int c = 0; c < TMAX / 32; ++c) {
-        if (c >= nchunk) break;
-        if ((outm[c] >> lane) & 1u) {
+#pragma unroll 1
+    for (int c = 0; c < nchunk; ++c) {
+        if ((outm.get(c) >> lane) & 1u) {
             unsigned v = S.tv[c * 32 + lane];
             unsigned a = v & 255u, b = (v >> 8) & 255u, cc = (v >> 16) & 255u;
             atomicOr(&S.bm[2 * a + (b >> 5)], 1u << (b & 31u));
@@ -388,14 +400,14 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
     // rim edges: removed x->y whose reverse y->x is not removed
     int nnew = 0;
     unsigned long long xs = 0, ys = 0;
-#pragma unroll
-    for (int c = 0; c < TMAX / 32; ++c) {
-        if (c >= nchunk) break;
-        if (outm[c] == 0) continue;  // warp-uniform
+#pragma unroll 1
+    for (int c = 0; c < nchunk; ++c) {
+        const unsigned oc = outm.get(c);
+        if (oc == 0) continue;  // warp-uniform
         // rim edges of this lane's removed triangle, kept in registers
         unsigned e0 = 0, e1 = 0, e2 = 0;
         bool f0 = false, f1 = false, f2 = false;
-        if ((outm[c] >> lane) & 1u) {
+        if ((oc >> lane) & 1u) {
             const unsigned v = S.tv[c * 32 + lane];
             const unsigned a = v & 255u, b = (v >> 8) & 255u, cc = (v >> 16) & 255u;
             const unsigned hk = (unsigned)kp << 16;
@@ -426,18 +438,15 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
     ys = warp_or64(ys);
     if (nnew > NSTAGE) { C.err |= ST_ECAP_STAGE; return; }
     if (nnew < 3 || xs != ys || __popcll(xs) != nnew) { C.err |= ST_EDEGEN; return; }
-    int nrem = 0;
-#pragma unroll
-    for (int c = 0; c < TMAX / 32; ++c) nrem += __popc(outm[c]);
+    const int nrem = outm.count();
     const int nkept = C.nt - nrem;
     if (nkept + nnew > TMAX) { C.err |= ST_ECAP_TRI; return; }
     // compact the kept triangles in place (destinations never pass sources)
     int dst = 0;
-#pragma unroll
-    for (int c = 0; c < TMAX / 32; ++c) {
-        if (c >= nchunk) break;
+#pragma unroll 1
+    for (int c = 0; c < nchunk; ++c) {
         const int t = c * 32 + lane;
-        const bool keep = t < C.nt && !((outm[c] >> lane) & 1u);
+        const bool keep = t < C.nt && !((outm.get(c) >> lane) & 1u);
         const unsigned km = __ballot_sync(FULL, keep);
         unsigned v = 0;
         long long r2 = 0;
@@ -626,77 +635,87 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
 #pragma unroll
         for (int d = 0; d < 3; ++d) edge[d] = fmin(pp[d] - cb[d] * g.bs[d], (cb[d] + 1) * g.bs[d] - pp[d]);
     }
+    // The candidate gather is resumable: each lane walks the bins of the
+    // current ring 32 at a time, the buffer is flushed (sorted and clipped)
+    // whenever it cannot take another 32 candidates and at the end of every
+    // ring, from one call site (one copy of the clipping code in the kernel).
     int ncand = 0, maxcand = 0;
-    int rl = 0, rh = 1;
-    bool done = false;
+    int rl = 0, rh = 1, total = 27, base = 0;
     int rings = 0;
-    while (!done && !C.err) {
-        const int nb = 2 * rh + 1;
-        const int total = nb * nb * nb;
-        for (int base = 0; base < total && !C.err; base += 32) {
-            const int t = base + lane;
-            int cur = 0, end = 0;
-            int shx = 0, shy = 0, shz = 0;
-            if (t < total) {
-                const int ox = t % nb - rh, oy = (t / nb) % nb - rh, oz = t / (nb * nb) - rh;
-                const int ch = max(abs(ox), max(abs(oy), abs(oz)));
-                if (ch >= rl) {
-                    int bx = cb[0] + ox, by = cb[1] + oy, bz = cb[2] + oz;
-                    // the image of a bin index: comparisons for the usual
-                    // range [-g, 2g), a division beyond it (rings wider than the grid)
-                    shx = (bx >= -g.g[0] && bx < 2 * g.g[0]) ? (bx < 0 ? -1 : (bx >= g.g[0] ? 1 : 0)) : floordiv(bx, g.g[0]);
-                    shy = (by >= -g.g[1] && by < 2 * g.g[1]) ? (by < 0 ? -1 : (by >= g.g[1] ? 1 : 0)) : floordiv(by, g.g[1]);
-                    shz = (bz >= -g.g[2] && bz < 2 * g.g[2]) ? (bz < 0 ? -1 : (bz >= g.g[2] ? 1 : 0)) : floordiv(bz, g.g[2]);
-                    bx -= shx * g.g[0];
-                    by -= shy * g.g[1];
-                    bz -= shz * g.g[2];
-                    const int b = g.bin_off + bx + g.g[0] * (by + g.g[1] * bz);
-                    cur = start[b];
-                    end = start[b + 1];
-                    // images two or more boxes away never cut (positions lie in [0, L))
-                    if (abs(shx) > 1 || abs(shy) > 1 || abs(shz) > 1) end = cur;
+    int cur = 0, end = 0, code = 13;
+    float offx = 0.0f, offy = 0.0f, offz = 0.0f;
+    bool selfimg = true;
+    while (!C.err) {
+        bool ring_done = false;
+        while (ncand + 32 <= cand_cap) {
+            if (!__any_sync(FULL, cur < end)) {
+                if (base >= total) { ring_done = true; break; }
+                // the next 32 bins of the ring, one per lane
+                const int nb = 2 * rh + 1;
+                const int t = base + lane;
+                base += 32;
+                cur = 0;
+                end = 0;
+                int shx = 0, shy = 0, shz = 0;
+                if (t < total) {
+                    const int ox = t % nb - rh, oy = (t / nb) % nb - rh, oz = t / (nb * nb) - rh;
+                    const int ch = max(abs(ox), max(abs(oy), abs(oz)));
+                    if (ch >= rl) {
+                        int bx = cb[0] + ox, by = cb[1] + oy, bz = cb[2] + oz;
+                        // the image of a bin index: comparisons for the usual
+                        // range [-g, 2g), a division beyond it (rings wider than the grid)
+                        shx = (bx >= -g.g[0] && bx < 2 * g.g[0]) ? (bx < 0 ? -1 : (bx >= g.g[0] ? 1 : 0)) : floordiv(bx, g.g[0]);
+                        shy = (by >= -g.g[1] && by < 2 * g.g[1]) ? (by < 0 ? -1 : (by >= g.g[1] ? 1 : 0)) : floordiv(by, g.g[1]);
+                        shz = (bz >= -g.g[2] && bz < 2 * g.g[2]) ? (bz < 0 ? -1 : (bz >= g.g[2] ? 1 : 0)) : floordiv(bz, g.g[2]);
+                        bx -= shx * g.g[0];
+                        by -= shy * g.g[1];
+                        bz -= shz * g.g[2];
+                        const int b = g.bin_off + bx + g.g[0] * (by + g.g[1] * bz);
+                        cur = start[b];
+                        end = start[b + 1];
+                        // images two or more boxes away never cut (positions lie in [0, L))
+                        if (abs(shx) > 1 || abs(shy) > 1 || abs(shz) > 1) end = cur;
+                    }
                 }
+                // FP32 offsets for the gather filter (the exact ones are formed at flush time)
+                offx = (float)(shx < 0 ? omx : (shx > 0 ? opx : o0x));
+                offy = (float)(shy < 0 ? omy : (shy > 0 ? opy : o0y));
+                offz = (float)(shz < 0 ? omz : (shz > 0 ? opz : o0z));
+                code = (shx + 1) + 3 * (shy + 1) + 9 * (shz + 1);
+                selfimg = (abs(shx) + abs(shy) + abs(shz)) <= 1;
+                continue;
             }
-            // FP32 offsets for the gather filter (the exact ones are formed at flush time)
-            const float offx = (float)(shx < 0 ? omx : (shx > 0 ? opx : o0x));
-            const float offy = (float)(shy < 0 ? omy : (shy > 0 ? opy : o0y));
-            const float offz = (float)(shz < 0 ? omz : (shz > 0 ? opz : o0z));
-            const int code = (shx + 1) + 3 * (shy + 1) + 9 * (shz + 1);
-            const bool selfimg = (abs(shx) + abs(shy) + abs(shz)) <= 1;
-            while (__any_sync(FULL, cur < end)) {
-                if (ncand + 32 > cand_cap) flush_batch<PREC>(S, ncand, C, lane, G);
-                if (C.err) break;
-                bool keep = false;
-                const int idx = cur;
-                if (cur < end) {
-                    const float4 Pf = sortedf[cur];
-                    ++cur;
-                    const float qx = Pf.x + offx, qy = Pf.y + offy, qz = Pf.z + offz;
-                    const float d2f = fmaf(qx, qx, fmaf(qy, qy, qz * qz));
-                    // the generator itself is sorted entry w
-                    keep = !((int64_t)idx == w && selfimg) && d2f <= C.limk;
-                }
-                const unsigned km = __ballot_sync(FULL, keep);
-                if (keep) {
-                    const int s = ncand + __popc(km & lanemask_lt());
-                    S.cid[s] = idx; S.csh[s] = code;
-                }
-                ncand += __popc(km);
-                maxcand = max(maxcand, ncand);
-                __syncwarp();
+            bool keep = false;
+            const int idx = cur;
+            if (cur < end) {
+                const float4 Pf = sortedf[cur];
+                ++cur;
+                const float qx = Pf.x + offx, qy = Pf.y + offy, qz = Pf.z + offz;
+                const float d2f = fmaf(qx, qx, fmaf(qy, qy, qz * qz));
+                // the generator itself is sorted entry w
+                keep = !((int64_t)idx == w && selfimg) && d2f <= C.limk;
             }
+            const unsigned km = __ballot_sync(FULL, keep);
+            if (keep) {
+                const int s = ncand + __popc(km & lanemask_lt());
+                S.cid[s] = idx; S.csh[s] = code;
+            }
+            ncand += __popc(km);
+            maxcand = max(maxcand, ncand);
+            __syncwarp();
         }
         flush_batch<PREC>(S, ncand, C, lane, G);
+        if (C.err || !ring_done) continue;
         ++rings;
         // radius the gathered rings are guaranteed to cover
         const double rr = (double)rh;
         const double R = fmin(fmin(fma(rr, g.bs[0], edge[0]), fma(rr, g.bs[1], edge[1])), fma(rr, g.bs[2], edge[2]));
-        if (C.lim <= __double_as_longlong(R * R)) done = true;
-        else {
-            rl = rh + 1;
-            rh = rl;
-            if (rh > MAXRING) C.err |= ST_ECAP_RING;
-        }
+        if (C.lim <= __double_as_longlong(R * R)) break;
+        rl = rh + 1;
+        rh = rl;
+        if (rh > MAXRING) { C.err |= ST_ECAP_RING; break; }
+        total = (2 * rh + 1) * (2 * rh + 1) * (2 * rh + 1);
+        base = 0;
     }
 
     // ---- finalisation: FP64 vertices, faces, volume, centroid
