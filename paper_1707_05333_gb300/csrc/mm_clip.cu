@@ -83,6 +83,7 @@ struct ClipSmem : VertStore<PREC> {
         } f;
     } u;
     int cid[CBATCH], csh[CBATCH];
+    unsigned char perm[CBATCH];  // clipping order of the buffered candidates
     double px[PMAX], py[PMAX], pz[PMAX], po[PMAX];  // planes x.q <= po
     int pnb[PMAX], psh[PMAX];
     unsigned tv[TMAX];                    // a | b << 8 | c << 16
@@ -204,6 +205,32 @@ template <class S_t>
 __device__ __noinline__ void vertex64_call(const S_t &S, int a, int b, int c, double &x, double &y, double &z)
 {
     vertex64(S, a, b, c, x, y, z);
+}
+
+// Face walk without the edge table (cells of more than 64 vertices): the
+// first triangle holding plane p (and the corner before p in it), and the
+// triangle holding the directed edge p -> y (and its third corner), by scans.
+__device__ __noinline__ int scan_first(const unsigned *tv, int nt, unsigned p, unsigned &y)
+{
+    for (int t = 0; t < nt; ++t) {
+        const unsigned v = tv[t];
+        const unsigned a = v & 255u, b = (v >> 8) & 255u, c = (v >> 16) & 255u;
+        if (a == p) { y = c; return t; }
+        if (b == p) { y = a; return t; }
+        if (c == p) { y = b; return t; }
+    }
+    return -1;
+}
+__device__ __noinline__ int scan_next(const unsigned *tv, int nt, unsigned p, unsigned y, unsigned &z)
+{
+    for (int t = 0; t < nt; ++t) {
+        const unsigned v = tv[t];
+        const unsigned a = v & 255u, b = (v >> 8) & 255u, c = (v >> 16) & 255u;
+        if (a == p && b == y) { z = c; return t; }
+        if (b == p && c == y) { z = a; return t; }
+        if (c == p && a == y) { z = b; return t; }
+    }
+    return -1;
 }
 
 // Candidate order: (|q|^2, id, image code).
@@ -532,7 +559,31 @@ __device__ void flush_batch(ClipSmem<PREC> &S, int &ncand, CellState &C, int lan
         S.cid[k] = (int)__double_as_longlong(P.w);
     }
     __syncwarp();
-    sort_candidates(S, ncand, lane);
+    if (ncand <= 32) {
+        // one candidate per lane: bitonic network on (|q|^2 bits, id, image)
+        // with shuffles; the buffer stays in place and perm gives the order
+        const bool have = lane < ncand;
+        unsigned long long key = have ? (unsigned long long)S.u.c.d2[lane] : ~0ull;
+        unsigned tie = have ? (unsigned)S.cid[lane] * 27u + (unsigned)S.csh[lane] : ~0u;
+        int idx = lane;
+#pragma unroll
+        for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+            for (int j = kk >> 1; j > 0; j >>= 1) {
+                const unsigned long long ok = __shfl_xor_sync(FULL, key, j);
+                const unsigned ot = __shfl_xor_sync(FULL, tie, j);
+                const int oi = __shfl_xor_sync(FULL, idx, j);
+                const bool other_less = ok < key || (ok == key && ot < tie);
+                const bool lower = (lane & j) == 0, up = (lane & kk) == 0;
+                if (lower == up ? other_less : !other_less) { key = ok; tie = ot; idx = oi; }
+            }
+        }
+        if (have) S.perm[lane] = (unsigned char)idx;
+    } else {
+        sort_candidates(S, ncand, lane);
+        for (int k = lane; k < ncand; k += 32) S.perm[k] = (unsigned char)k;
+    }
+    __syncwarp();
     if constexpr (PREC == 1) {
         // FP32 copies of the sorted planes, one lane per candidate
         for (int k = lane; k < ncand; k += 32) {
@@ -542,8 +593,9 @@ __device__ void flush_batch(ClipSmem<PREC> &S, int &ncand, CellState &C, int lan
         __syncwarp();
     }
     for (int k = 0; k < ncand; ++k) {
-        if (S.u.c.d2[k] > C.lim) break;
-        clip_by<PREC>(S, k, C, lane);
+        const int kk = S.perm[k];
+        if (S.u.c.d2[kk] > C.lim) break;
+        clip_by<PREC>(S, kk, C, lane);
         if (C.err) break;
     }
     ncand = 0;
@@ -774,13 +826,7 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
                     y = a == (unsigned)p ? c : (b == (unsigned)p ? a : b);
                 }
             } else {
-                for (int t = 0; t < C.nt; ++t) {
-                    const unsigned v = S.tv[t];
-                    const unsigned a = v & 255u, b = (v >> 8) & 255u, c = (v >> 16) & 255u;
-                    if (a == (unsigned)p) { t0 = t; y = c; break; }
-                    if (b == (unsigned)p) { t0 = t; y = a; break; }
-                    if (c == (unsigned)p) { t0 = t; y = b; break; }
-                }
+                t0 = scan_first(S.tv, C.nt, (unsigned)p, y);
             }
             S.u.f.a[p] = 0.0;
             if (t0 < 0) continue;  // plane no longer bounds the cell
@@ -821,13 +867,7 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
                         h = (h + 1) & (ETAB - 1);
                     }
                 } else {
-                    for (int t = 0; t < C.nt; ++t) {
-                        const unsigned v = S.tv[t];
-                        const unsigned a = v & 255u, b = (v >> 8) & 255u, c = (v >> 16) & 255u;
-                        if (a == (unsigned)p && b == y) { tn = t; z = c; break; }
-                        if (b == (unsigned)p && c == y) { tn = t; z = a; break; }
-                        if (c == (unsigned)p && a == y) { tn = t; z = b; break; }
-                    }
+                    tn = scan_next(S.tv, C.nt, (unsigned)p, y, z);
                 }
                 if (tn < 0) break;
                 ++cnt;
