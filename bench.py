@@ -50,6 +50,8 @@ def parse():
                    help="skip the variant measurements (mixed precision, direct FP64 clipping, entropy "
                         "switch, Heun integration, batched ensemble)")
     p.add_argument("--ensemble-boxes", type=int, default=512)
+    p.add_argument("--no-autotune", action="store_true",
+                   help="keep the default clipper settings instead of tuning them first")
     return p.parse_args()
 
 
@@ -278,6 +280,20 @@ def time_steps(torch, stream, fn, steps):
     return e0.elapsed_time(e1)
 
 
+def tune_clipper(args, pos_np, box):
+    """mm_autotune on a sample of the workload (untimed): the clipper's warps
+    per block, candidate batch and bin width, reported and reused."""
+    import torch
+    from paper_1707_05333_gb300 import binding as BD
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = BD.Context(stream=stream)
+        pos = torch.tensor(pos_np.T.copy(), dtype=torch.float64, device="cuda")
+        res = ctx.mm_autotune(pos, box, reps=1)
+        ctx.close()
+    return res
+
+
 def measure_variant(args, w, steps, dtype, note, **cfg):
     """One configuration of the step on the same workload and protocol
     (warm-up steps, then `steps` timed steps with CUDA events)."""
@@ -285,7 +301,7 @@ def measure_variant(args, w, steps, dtype, note, **cfg):
     from paper_1707_05333_gb300 import binding as BD
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        ctx = BD.Context(stream=stream, gamma=w.gamma, cfl=w.cfl, limiter=1, **cfg)
+        ctx = BD.Context(stream=stream, gamma=w.gamma, cfl=w.cfl, limiter=1, **args.tuned, **cfg)
         pos = torch.tensor(w.pos.T.copy(), dtype=torch.float64, device="cuda")
         mesh = ctx.mm_tessellate(pos, w.box)
         U = ctx.mm_prims_to_charges(mesh, torch.tensor(w.rho, device="cuda"), torch.tensor(w.vel.T.copy(), device="cuda"),
@@ -327,12 +343,16 @@ def measure_ensemble(args):
     from paper_1707_05333_gb300 import workloads as WL
     sizes = WL.ensemble_sizes(args.ensemble_boxes)
     boxes = [WL.ensemble_box(b, int(nb)) for b, nb in enumerate(sizes)]
+    # the clipper tuned on the largest box of the ensemble
+    big = boxes[int(np.argmax(sizes))]
+    tuned = {} if args.no_autotune else tune_clipper(args, big.pos, big.box)
+    tunables = {k: tuned[k] for k in ("clip_warps", "cand_cap", "bin_scale")} if tuned else {}
     off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
     n = int(off[-1])
     L = np.ones((len(boxes), 3))
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        ctx = BD.Context(stream=stream, gamma=5.0 / 3.0, cfl=0.3, limiter=1, precision=1)
+        ctx = BD.Context(stream=stream, gamma=5.0 / 3.0, cfl=0.3, limiter=1, precision=1, **tunables)
         # charges from each box's own tessellation
         Us = []
         for wb in boxes:
@@ -367,7 +387,7 @@ def measure_ensemble(args):
     return {"workload": f"ensemble of {len(boxes)} periodic unit boxes, {n} cells (2^10..2^16 per box)",
             "precision": "mixed", "graph_cells_per_s": graph, "graph_ms_per_step": ms_graph / args.steps,
             "kernels_per_step": launches, "per_box_cells_per_s": box, "per_box_ms_per_step": ms_box / per_steps,
-            "speedup": graph / box}
+            "speedup": graph / box, "clipper_settings": tuned or "defaults"}
 
 
 def run_ours(args, world, rank, local):
@@ -383,10 +403,17 @@ def run_ours(args, world, rank, local):
     B.build()
     w = WL.shear_layer(args.n_side)
     prec = 0 if args.precision == "fp64" else 1
+    # clipper settings tuned on the same recipe at half the side (untimed)
+    args.tuned, tune_info = {}, None
+    if not args.no_autotune:
+        ws = WL.shear_layer(max(32, args.n_side // 2))
+        tune_info = tune_clipper(args, ws.pos, ws.box)
+        tune_info["sample"] = f"shear_layer_{max(32, args.n_side // 2)}^3"
+        args.tuned = {k: tune_info[k] for k in ("clip_warps", "cand_cap", "bin_scale")}
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         ctx = BD.Context(stream=stream, gamma=w.gamma, cfl=w.cfl, limiter=1, precision=prec,
-                         clip_filter=args.clip_filter)
+                         clip_filter=args.clip_filter, **args.tuned)
         pos0 = torch.tensor(w.pos.T.copy(), dtype=torch.float64, device="cuda")
         mesh = ctx.mm_tessellate(pos0, w.box)
         U0 = ctx.mm_prims_to_charges(mesh, torch.tensor(w.rho, device="cuda"),
@@ -495,6 +522,7 @@ def run_ours(args, world, rank, local):
                 "data": "synthetic",
                 "config": {"workload": f"shear_layer_{args.n_side}^3", "cells": n, "faces": nf,
                            "precision": args.precision, "clip_filter": args.clip_filter,
+                           "clipper_settings": tune_info or "defaults",
                            "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (state + mesh >> 129 MB), no flush"},
                 "roofline": roofline, "stage_ms": stage_ms, "tess_stats_per_cell": {k: v / n for k, v in tstats.items()
