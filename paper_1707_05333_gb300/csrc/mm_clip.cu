@@ -184,7 +184,7 @@ __device__ __forceinline__ void vertex32(const ClipSmem<1> &S, int a, int b, int
     z = fmaf(ao, bcz, fmaf(bo, caz, co * abz)) * inv;
     // |q_k| = sqrt(2 o_k)
     const float la = S.pfn[a], lb = S.pfn[b], lc = S.pfn[c];
-    const float H = la * lb * lc / fabsf(det);
+    const float H = la * lb * lc * fabsf(inv);  // P / |det| through the reciprocal (the factor 3 covers its ulp)
     const float vn = fabsf(x) + fabsf(y) + fabsf(z);
     const float u = 5.9604645e-8f;
     err = 3.0f * u * H * (5.5f * (la + lb + lc) + 13.0f * vn);
@@ -291,11 +291,11 @@ struct CellState {
     unsigned pred64, solve64, fan64, tested;
 };
 
+// The security limit from each lane's largest |v|^2 bound over the vertices
+// it handled (the kept ones it compacted and the new ones it solved).
 template <int PREC>
-__device__ __forceinline__ void update_limit(ClipSmem<PREC> &S, CellState &C, int lane)
+__device__ __forceinline__ void update_limit(CellState &C, long long m)
 {
-    long long m = 0;
-    for (int t = lane; t < C.nt; t += 32) m = max(m, S.tr2[t]);
     float m4;
     if constexpr (PREC == 0) {
         m = warp_max_nonneg(m);
@@ -469,6 +469,7 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
     const int nkept = C.nt - nrem;
     if (nkept + nnew > TMAX) { C.err |= ST_ECAP_TRI; return; }
     // compact the kept triangles in place (destinations never pass sources)
+    long long mr = 0;  // this lane's largest |v|^2 bound, for the new limit
     int dst = 0;
 #pragma unroll 1
     for (int c = 0; c < nchunk; ++c) {
@@ -488,6 +489,7 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
         __syncwarp();
         if (keep) {
             const int d = dst + __popc(km & lanemask_lt());
+            mr = max(mr, r2);
             S.tv[d] = v;
             S.tr2[d] = r2;
             if constexpr (PREC == 0) { S.tx[d] = x; S.ty[d] = y; S.tz[d] = z; }
@@ -506,6 +508,7 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
             vertex64(S, v & 255u, (v >> 8) & 255u, kp, x, y, z);
             S.tx[t] = x; S.ty[t] = y; S.tz[t] = z;
             S.tr2[t] = r2_bits64(x, y, z);
+            mr = max(mr, S.tr2[t]);
         } else {
             float x, y, z, er;
             vertex32(S, v & 255u, (v >> 8) & 255u, kp, x, y, z, er);
@@ -522,7 +525,9 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
             // kept as the bit pattern of a positive float
             const float s2 = fmaf(x, x, fmaf(y, y, z * z));
             const float l1 = fabsf(x) + fabsf(y) + fabsf(z);
-            S.tr2[t] = (long long)__float_as_int(fmaf(er, fmaf(2.0f, l1, er), s2) * 1.00001f);
+            const long long r2n = (long long)__float_as_int(fmaf(er, fmaf(2.0f, l1, er), s2) * 1.00001f);
+            S.tr2[t] = r2n;
+            mr = max(mr, r2n);
         }
     }
     __syncwarp();
@@ -530,7 +535,7 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
     C.nt = nkept + nnew;
     C.np = max(C.np, kp + 1);
     C.cuts++;
-    update_limit(S, C, lane);
+    update_limit<PREC>(C, mr);
 }
 
 // What a flush needs to form the exact candidate planes: the binned
@@ -710,7 +715,10 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
                 end = 0;
                 int shx = 0, shy = 0, shz = 0;
                 if (t < total) {
-                    const int ox = t % nb - rh, oy = (t / nb) % nb - rh, oz = t / (nb * nb) - rh;
+                    int ox, oy, oz;
+                    if (rh == 1) { ox = t % 3 - 1; oy = (t / 3) % 3 - 1; oz = t / 9 - 1; }
+                    else if (rh == 2) { ox = t % 5 - 2; oy = (t / 5) % 5 - 2; oz = t / 25 - 2; }
+                    else { ox = t % nb - rh; oy = (t / nb) % nb - rh; oz = t / (nb * nb) - rh; }
                     const int ch = max(abs(ox), max(abs(oy), abs(oz)));
                     if (ch >= rl) {
                         int bx = cb[0] + ox, by = cb[1] + oy, bz = cb[2] + oz;
