@@ -619,10 +619,13 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
     const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
     if (w >= n) return;
     ClipSmem<PREC> &S = reinterpret_cast<ClipSmem<PREC> *>(dyn_smem)[wid];
+    // A box's cells occupy the same range of indices in the input order and in
+    // the binned order (the bins are laid out box by box), so the box of
+    // binned entry w is cbox[w]: no need to wait for the generator's id.
+    const BoxDev g = boxes[cbox[w]];
     const double4_32a me = sorted[w];
     const double px = me.x, py = me.y, pz = me.z;
     const int self = (int)__double_as_longlong(me.w);
-    const BoxDev g = boxes[cbox[self]];
     const double amin = g.amin;
     const double Lx = g.L[0], Ly = g.L[1], Lz = g.L[2];
 

@@ -7,6 +7,7 @@ namespace mm {
 template <class T>
 struct FaceStateT {
     T rho, vx, vy, vz, P;  // velocity already in the face frame
+    T irho;                // 1 / rho (formed once per face state)
 };
 
 __device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
@@ -28,9 +29,10 @@ __device__ __forceinline__ void hllc_t(const FaceStateT<T> &L, const FaceStateT<
     const T gm1 = gamma - T(1);
     const T ul = L.vx * nx + L.vy * ny + L.vz * nz;
     const T ur = R.vx * nx + R.vy * ny + R.vz * nz;
-    const T cl = sqrt_t(gamma * L.P / L.rho), cr = sqrt_t(gamma * R.P / R.rho);
-    const T El = L.P / gm1 + T(0.5) * L.rho * (L.vx * L.vx + L.vy * L.vy + L.vz * L.vz);
-    const T Er = R.P / gm1 + T(0.5) * R.rho * (R.vx * R.vx + R.vy * R.vy + R.vz * R.vz);
+    const T cl = sqrt_t(gamma * L.P * L.irho), cr = sqrt_t(gamma * R.P * R.irho);
+    const T igm1 = T(1) / gm1;
+    const T El = L.P * igm1 + T(0.5) * L.rho * (L.vx * L.vx + L.vy * L.vy + L.vz * L.vz);
+    const T Er = R.P * igm1 + T(0.5) * R.rho * (R.vx * R.vx + R.vy * R.vy + R.vz * R.vz);
     const T sl = min_t(ul - cl, ur - cr);
     const T sr = max_t(ul + cl, ur + cr);
     const T ml = L.rho * (sl - ul), mr = R.rho * (sr - ur);
@@ -52,7 +54,7 @@ __device__ __forceinline__ void hllc_t(const FaceStateT<T> &L, const FaceStateT<
         // U*_K = rho_K (S_K - u_K)/(S_K - S*) (1, v_K + (S* - u_K) n, E_K/rho_K + (S* - u_K)(S* + P_K/(rho_K (S_K - u_K))))
         const T f = K.rho * (sk - uk) / (sk - ss);
         const T du = ss - uk;
-        const T es = f * (Ek / K.rho + du * (ss + K.P / (K.rho * (sk - uk))));
+        const T es = f * (Ek * K.irho + du * (ss + K.P * K.irho / (sk - uk)));
         F[0] += sk * (f - K.rho);
         F[1] += sk * (f * (K.vx + du * nx) - K.rho * K.vx);
         F[2] += sk * (f * (K.vy + du * ny) - K.rho * K.vy);
@@ -70,9 +72,10 @@ __device__ __forceinline__ void hll_t(const FaceStateT<T> &L, const FaceStateT<T
     const T gm1 = gamma - T(1);
     const T ul = L.vx * nx + L.vy * ny + L.vz * nz;
     const T ur = R.vx * nx + R.vy * ny + R.vz * nz;
-    const T cl = sqrt_t(gamma * L.P / L.rho), cr = sqrt_t(gamma * R.P / R.rho);
-    const T El = L.P / gm1 + T(0.5) * L.rho * (L.vx * L.vx + L.vy * L.vy + L.vz * L.vz);
-    const T Er = R.P / gm1 + T(0.5) * R.rho * (R.vx * R.vx + R.vy * R.vy + R.vz * R.vz);
+    const T cl = sqrt_t(gamma * L.P * L.irho), cr = sqrt_t(gamma * R.P * R.irho);
+    const T igm1 = T(1) / gm1;
+    const T El = L.P * igm1 + T(0.5) * L.rho * (L.vx * L.vx + L.vy * L.vy + L.vz * L.vz);
+    const T Er = R.P * igm1 + T(0.5) * R.rho * (R.vx * R.vx + R.vy * R.vy + R.vz * R.vz);
     const T sl = min_t(ul - cl, ur - cr);
     const T sr = max_t(ul + cl, ur + cr);
     const T ml = L.rho * ul, mr = R.rho * ur;
@@ -101,7 +104,7 @@ __device__ __forceinline__ void star_state_t(const FaceStateT<T> &L, const FaceS
 {
     ul = L.vx * nx + L.vy * ny + L.vz * nz;
     ur = R.vx * nx + R.vy * ny + R.vz * nz;
-    const T cl = sqrt_t(gamma * L.P / L.rho), cr = sqrt_t(gamma * R.P / R.rho);
+    const T cl = sqrt_t(gamma * L.P * L.irho), cr = sqrt_t(gamma * R.P * R.irho);
     sl = min_t(ul - cl, ur - cr);
     sr = max_t(ul + cl, ur + cr);
     ss = (R.P - L.P + L.rho * ul * (sl - ul) - R.rho * ur * (sr - ur)) / (L.rho * (sl - ul) - R.rho * (sr - ur));
@@ -131,7 +134,7 @@ __device__ __forceinline__ T passive_flux_t(int kind, const FaceStateT<T> &L, co
     T sl, ss, sr, ps, ul, ur;
     star_state_t<T>(L, R, nx, ny, nz, gamma, sl, ss, sr, ps, ul, ur);
     mach = shock_mach_t<T>(L.P, R.P, ps, gamma);
-    const T al = rhoa_l / L.rho, ar = rhoa_r / R.rho;
+    const T al = rhoa_l * L.irho, ar = rhoa_r * R.irho;
     if (kind == 1) {
         const T fl = L.rho * ul * al, fr = R.rho * ur * ar;
         if (sl >= T(0)) return fl;
@@ -148,6 +151,23 @@ __device__ __forceinline__ void riemann_t(int kind, const FaceStateT<T> &L, cons
 {
     if (kind == 1) hll_t<T>(L, R, nx, ny, nz, gamma, F);
     else hllc_t<T>(L, R, nx, ny, nz, gamma, F);
+}
+
+// The same floors for a face state, also returning 1 / rho of the result
+// (the kinetic energy is formed with it instead of a second division).
+template <class T>
+__device__ __forceinline__ void apply_floor_ir_t(T W[5], T rho_floor, T eps_floor, T &ir)
+{
+    if (!(W[0] >= rho_floor)) {
+        W[0] = rho_floor;
+        W[1] = W[2] = W[3] = T(0);
+        W[4] = rho_floor * eps_floor;
+        ir = T(1) / rho_floor;
+        return;
+    }
+    ir = T(1) / W[0];
+    const T ke = T(0.5) * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]) * ir;
+    if (!(W[4] - ke >= W[0] * eps_floor)) W[4] = W[0] * eps_floor + ke;
 }
 
 // Floors on density and specific internal energy (Sec. 4.1).  A state below
