@@ -66,6 +66,7 @@ struct mm_ctx {
     Buf face_i, face_j, face_shift, face_area, face_normal, face_cen, inc_face;
     // hydro scratch
     Buf Wh, grad, flux, w_int, dt_int, tot_partial, drift_box, drift_cbox;
+    Buf fgeo, minv;  // per-face A n and d, per-cell M^-1 of the gradient
     Buf heun_U0;  // start-of-step charges of a Heun step
     // mixed-precision records
     Buf x_fij, x_fa, x_fq, x_ff, x_cw, x_ch, x_grad, x_wv, x_flux;
@@ -483,7 +484,8 @@ static mm_status ensure_hydro(mm_ctx *c, int64_t n, int64_t fs)
         // flux, each face's shock Mach number and its swept-volume rate)
         const int64_t ng = c->cfg.entropy ? 6 : 5, nfr = c->cfg.entropy ? 8 : 5;
         if ((r = ensure(c, c->Wh, ng * n * sizeof(double))) || (r = ensure(c, c->grad, 3 * ng * n * sizeof(double))) ||
-            (r = ensure(c, c->flux, nfr * F * sizeof(double))))
+            (r = ensure(c, c->flux, nfr * F * sizeof(double))) || (r = ensure(c, c->fgeo, 6 * F * sizeof(double))) ||
+            (r = ensure(c, c->minv, 9 * n * sizeof(double))))
             return r;
     }
     return MM_OK;
@@ -507,10 +509,14 @@ static mm_status hydro_enqueue(mm_ctx *c, const MeshDev &m, const double *pos, c
     // states W^n = U / V, once per cell, in the gradient buffer (the second
     // gradient pass overwrites them only after the first has read them)
     launch_states(m, h, U, P<double>(c->grad), s);
-    launch_gradient(m, h, P<double>(c->grad), false, nullptr, P<double>(c->Wh), dt, s);
+    launch_face_geom(m, P<double>(c->fgeo), s);
+    launch_gradient(m, h, P<double>(c->grad), P<double>(c->fgeo), P<double>(c->minv), false, nullptr,
+                    P<double>(c->Wh), dt, s);
     stage_mark(c, MM_STAGE_GRADIENT_HALF, false);
     stage_mark(c, MM_STAGE_GRADIENT, true);
-    launch_gradient(m, h, P<double>(c->Wh), false, P<double>(c->grad), nullptr, nullptr, s);
+    // same mesh: M^-1 from the first pass
+    launch_gradient(m, h, P<double>(c->Wh), P<double>(c->fgeo), P<double>(c->minv), true, P<double>(c->grad),
+                    nullptr, nullptr, s);
     stage_mark(c, MM_STAGE_GRADIENT, false);
     stage_mark(c, MM_STAGE_FACE_FLUX, true);
     launch_face_flux(m, h, pos, w, P<double>(c->Wh), P<double>(c->grad), P<double>(c->flux), s);
@@ -519,7 +525,7 @@ static mm_status hydro_enqueue(mm_ctx *c, const MeshDev &m, const double *pos, c
     launch_update(m, h, P<double>(c->flux), dt, U, s);
     stage_mark(c, MM_STAGE_UPDATE, false);
     CKLAUNCH();
-    c->launches += 5;
+    c->launches += 6;
     return MM_OK;
 }
 
@@ -534,7 +540,9 @@ static mm_status heun_stage(mm_ctx *c, const MeshDev &m, const double *pos, cons
     launch_states(m, h, U, P<double>(c->Wh), s);
     stage_mark(c, MM_STAGE_GRADIENT_HALF, false);
     stage_mark(c, MM_STAGE_GRADIENT, true);
-    launch_gradient(m, h, P<double>(c->Wh), false, P<double>(c->grad), nullptr, nullptr, s);
+    launch_face_geom(m, P<double>(c->fgeo), s);
+    launch_gradient(m, h, P<double>(c->Wh), P<double>(c->fgeo), P<double>(c->minv), false, P<double>(c->grad),
+                    nullptr, nullptr, s);
     stage_mark(c, MM_STAGE_GRADIENT, false);
     stage_mark(c, MM_STAGE_FACE_FLUX, true);
     launch_face_flux(m, h, pos, w, P<double>(c->Wh), P<double>(c->grad), P<double>(c->flux), s);
@@ -543,7 +551,7 @@ static mm_status heun_stage(mm_ctx *c, const MeshDev &m, const double *pos, cons
     launch_update(m, h, P<double>(c->flux), dt, U, s);
     stage_mark(c, MM_STAGE_UPDATE, false);
     CKLAUNCH();
-    c->launches += 4;
+    c->launches += 5;
     return MM_OK;
 }
 
@@ -668,7 +676,7 @@ void mm_destroy(mm_ctx *c)
                    &c->face_off, &c->inc_off, &c->face_i, &c->face_j, &c->face_shift, &c->face_area,
                    &c->face_normal, &c->face_cen, &c->inc_face, &c->Wh, &c->grad, &c->flux, &c->w_int, &c->dt_int,
                    &c->tot_partial, &c->drift_box, &c->drift_cbox, &c->x_fij, &c->x_fa, &c->x_fq, &c->x_ff,
-                   &c->x_cw, &c->x_ch, &c->x_grad, &c->x_wv, &c->x_flux, &c->heun_U0};
+                   &c->x_cw, &c->x_ch, &c->x_grad, &c->x_wv, &c->x_flux, &c->heun_U0, &c->fgeo, &c->minv};
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
@@ -720,9 +728,11 @@ mm_status mm_gradients(mm_ctx *c, const mm_mesh *mesh, const double *W, double *
     if ((r = check_mesh(c, mesh))) return r;
     if (!W || !grad) return fail(c, MM_EINVAL, "null pointer argument");
     MeshDev m = mesh_from(mesh);
-    launch_gradient(m, hydro_cfg(c->cfg), W, false, grad, nullptr, nullptr, c->stream);
+    if ((r = ensure(c, c->fgeo, 6 * (m.fs > 0 ? m.fs : 1) * sizeof(double)))) return r;
+    launch_face_geom(m, P<double>(c->fgeo), c->stream);
+    launch_gradient(m, hydro_cfg(c->cfg), W, P<double>(c->fgeo), nullptr, false, grad, nullptr, nullptr, c->stream);
     CKLAUNCH();
-    c->launches += 1;
+    c->launches += 2;
     return MM_OK;
 }
 

@@ -76,11 +76,15 @@ __global__ void k_face_write(int64_t n, const double *__restrict__ pos, const Bo
         if ((em >> k) & 1ull) {
             const int f = fbase + __popcll(em & ((1ull << k) - 1ull));
             if (f < fcap) {
-                const int sx = code % 3 - 1, sy = (code / 3) % 3 - 1, sz = code / 9 - 1;
-                const double qx = pos[j] + sx * L[0] - pos[i];
-                const double qy = pos[n + j] + sy * L[1] - pos[n + i];
-                const double qz = pos[2 * n + j] + sz * L[2] - pos[2 * n + i];
-                const double inv = 1.0 / sqrt(qx * qx + qy * qy + qz * qz);
+                // image offsets -L, 0, +L by selection (no FP64 arithmetic)
+                const int cx = code % 3, cy = (code / 3) % 3, cz = code / 9;
+                const double ox = cx == 1 ? 0.0 : (cx == 2 ? L[0] : -L[0]);
+                const double oy = cy == 1 ? 0.0 : (cy == 2 ? L[1] : -L[1]);
+                const double oz = cz == 1 ? 0.0 : (cz == 2 ? L[2] : -L[2]);
+                const double qx = pos[j] + ox - pos[i];
+                const double qy = pos[n + j] + oy - pos[n + i];
+                const double qz = pos[2 * n + j] + oz - pos[2 * n + i];
+                const double inv = rsqrt(qx * qx + qy * qy + qz * qz);
                 face_i[f] = (int)i;
                 face_j[f] = j;
                 face_shift[f] = code;

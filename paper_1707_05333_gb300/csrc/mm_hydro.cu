@@ -13,13 +13,6 @@ constexpr unsigned FULL_MASK_HYDRO = 0xffffffffu;
 #define MM_GRAD_MINBLOCKS 1  // resident blocks per SM the gradient kernel is compiled for
 #endif
 
-__device__ __forceinline__ void decode_shift(int code, double &sx, double &sy, double &sz)
-{
-    sx = (double)(code % 3 - 1);
-    sy = (double)((code / 3) % 3 - 1);
-    sz = (double)(code / 9 - 1);
-}
-
 // Neighbour across incident entry e of a cell: other cell, outward normal
 // scale (+1/-1) and the image offset s L of the neighbour in this cell's frame.
 struct Nbr {
@@ -74,70 +67,132 @@ __device__ __forceinline__ bool apply_floor(double W[5], double rho_floor, doubl
 }
 
 // ---------------------------------------------------------------------------
+// Face geometry of the gradient (Sec. 4.1), once per mesh and step: per
+// unique face the area-weighted normal A n and the centroid separation
+// d = c_j + s L - c_i, both seen from side i (side j sees -A n, -d).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_face_geom(MeshDev m, double *__restrict__ geo)
+{
+    const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= face_count(m)) return;
+    const int64_t n = m.n, fs = m.fs;
+    const int i = m.face_i[f], j = m.face_j[f];
+    const int code = m.face_shift[f];
+    const double *L = m.boxL + 3 * m.cbox[i];
+    const double A = m.area[f];
+    geo[f] = A * m.normal[f];
+    geo[fs + f] = A * m.normal[fs + f];
+    geo[2 * fs + f] = A * m.normal[2 * fs + f];
+    geo[3 * fs + f] = m.cen[j] + image_axis(code % 3, L[0]) - m.cen[i];
+    geo[4 * fs + f] = m.cen[n + j] + image_axis((code / 3) % 3, L[1]) - m.cen[n + i];
+    geo[5 * fs + f] = m.cen[2 * n + j] + image_axis(code / 9, L[2]) - m.cen[2 * n + i];
+}
+
+void launch_face_geom(const MeshDev &m, double *geo, cudaStream_t s)
+{
+    const int64_t nfl = face_launch_count(m);
+    if (nfl == 0) return;
+    k_face_geom<<<(int)((nfl + 255) / 256), 256, 0, s>>>(m, geo);
+}
+
+// Order-preserving map of a double onto a signed 64-bit integer (the
+// sign-magnitude bit pattern turned into two's complement), its own inverse.
+// The running minima and maxima of the limiter are kept as such integers: the
+// comparisons then take integer instructions instead of FP64 ones, and the
+// extremum found is the same double bit for bit.
+__device__ __forceinline__ long long okey(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double okey_value(long long k)
+{
+    return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+}
+__device__ __forceinline__ long long kmax(long long a, long long b) { return a > b ? a : b; }
+__device__ __forceinline__ long long kmin(long long a, long long b) { return a < b ? a : b; }
+
+// ---------------------------------------------------------------------------
 // Gradient + limiter (+ half-step predictor when PREDICT)
 // ---------------------------------------------------------------------------
 // NG = 5 state columns, or 6 with the entropy column rho A (Sec. 4.3), which
-// is treated like the others and advected in the predictor.
-template <bool FROM_CHARGES, bool PREDICT, int NG>
+// is treated like the others and advected in the predictor.  The geometric
+// matrix M depends on the mesh only: the predictor pass stores M^-1 per cell
+// ([9][n], row major) and the second pass on the same mesh (MINV_IN) reads it.
+template <bool PREDICT, bool MINV_IN, int NG>
 __global__ void __launch_bounds__(128, MM_GRAD_MINBLOCKS) k_gradient(MeshDev m, HydroCfg c, const double *__restrict__ S,
+                                                  const double *__restrict__ geo, double *__restrict__ minv,
                                                   double *__restrict__ grad, double *__restrict__ Wh,
                                                   const double *__restrict__ dtp)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t n = m.n;
+    const int64_t n = m.n, fs = m.fs;
     if (i >= n) return;
-    const double ivi = FROM_CHARGES ? 1.0 / m.vol[i] : 1.0;
     double Wi[NG];
-    loadw<NG>(S, n, i, ivi, Wi);
-    const double cix = m.cen[i], ciy = m.cen[n + i], ciz = m.cen[2 * n + i];
+    loadw<NG>(S, n, i, 1.0, Wi);
     const int e0 = m.inc_off[i], e1 = m.inc_off[i + 1];
-    const double *L = m.boxL + 3 * m.cbox[i];
 
-    // M = 1/2 sum A n (x) d,  b_k = 1/2 sum A (W_o - W_i)_k n
+    // M = 1/2 sum A n (x) d,  b_k = 1/2 sum A (W_o - W_i)_k n; the signs of
+    // A n and d flip together on side j, so M takes the stored vectors as
+    // they are and b takes the sign on W_o - W_i.  (Both are summed without
+    // the factor 1/2, which cancels exactly in M^-1 b.)
     double M[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     double b[3 * NG];
-    double wmax[NG], wmin[NG];
+    long long kx[NG], kn[NG];  // running max / min of W over the cell and its neighbours
 #pragma unroll
-    for (int k = 0; k < NG; ++k) { wmax[k] = Wi[k]; wmin[k] = Wi[k]; }
+    for (int k = 0; k < NG; ++k) { kx[k] = okey(Wi[k]); kn[k] = kx[k]; }
 #pragma unroll
     for (int k = 0; k < 3 * NG; ++k) b[k] = 0.0;
-    // (M and b are summed with A rather than A/2: the factor 2 cancels
-    // exactly in M^-1 b)
     for (int e = e0; e < e1; ++e) {
-        const Nbr q = neighbour(m, e, L);
-        const double A = m.area[q.f];
-        const long long sm = q.sg > 0.0 ? 0LL : (long long)0x8000000000000000ULL;
-        const double nx = flip(m.normal[q.f], sm), ny = flip(m.normal[m.fs + q.f], sm),
-                     nz = flip(m.normal[2 * m.fs + q.f], sm);
-        const double dx = m.cen[q.o] + q.ox - cix, dy = m.cen[n + q.o] + q.oy - ciy, dz = m.cen[2 * n + q.o] + q.oz - ciz;
-        const double ax = A * nx, ay = A * ny, az = A * nz;
-        M[0] += ax * dx; M[1] += ax * dy; M[2] += ax * dz;
-        M[3] += ay * dx; M[4] += ay * dy; M[5] += ay * dz;
-        M[6] += az * dx; M[7] += az * dy; M[8] += az * dz;
-        const double ivo = FROM_CHARGES ? 1.0 / m.vol[q.o] : 1.0;
+        int f = m.inc_face[e];
+        const bool fwd = f >= 0;
+        if (!fwd) f = ~f;
+        const int o = fwd ? m.face_j[f] : m.face_i[f];
+        const long long sm = fwd ? 0LL : (long long)0x8000000000000000ULL;
+        const double ax = geo[f], ay = geo[fs + f], az = geo[2 * fs + f];
+        if (!MINV_IN) {
+            const double dx = geo[3 * fs + f], dy = geo[4 * fs + f], dz = geo[5 * fs + f];
+            M[0] += ax * dx; M[1] += ax * dy; M[2] += ax * dz;
+            M[3] += ay * dx; M[4] += ay * dy; M[5] += ay * dz;
+            M[6] += az * dx; M[7] += az * dy; M[8] += az * dz;
+        }
 #pragma unroll
         for (int k = 0; k < NG; ++k) {
-            const double wo = S[k * n + q.o] * ivo;
-            const double dw = wo - Wi[k];
+            const double wo = S[k * n + o];
+            const double dw = flip(wo - Wi[k], sm);
             b[3 * k + 0] += ax * dw;
             b[3 * k + 1] += ay * dw;
             b[3 * k + 2] += az * dw;
-            wmax[k] = fmax(wmax[k], wo);
-            wmin[k] = fmin(wmin[k], wo);
+            const long long kw = okey(wo);
+            kx[k] = kmax(kx[k], kw);
+            kn[k] = kmin(kn[k], kw);
         }
     }
-    // g = M^-1 b by the adjugate
-    const double c00 = M[4] * M[8] - M[5] * M[7], c01 = M[5] * M[6] - M[3] * M[8], c02 = M[3] * M[7] - M[4] * M[6];
-    const double c10 = M[2] * M[7] - M[1] * M[8], c11 = M[0] * M[8] - M[2] * M[6], c12 = M[1] * M[6] - M[0] * M[7];
-    const double c20 = M[1] * M[5] - M[2] * M[4], c21 = M[2] * M[3] - M[0] * M[5], c22 = M[0] * M[4] - M[1] * M[3];
-    const double idet = 1.0 / (M[0] * c00 + M[1] * c01 + M[2] * c02);
+    double mi[9];
+    if (MINV_IN) {
+#pragma unroll
+        for (int r = 0; r < 9; ++r) mi[r] = minv[r * n + i];
+    } else {
+        // M^-1 by the adjugate
+        const double c00 = M[4] * M[8] - M[5] * M[7], c01 = M[5] * M[6] - M[3] * M[8], c02 = M[3] * M[7] - M[4] * M[6];
+        const double c10 = M[2] * M[7] - M[1] * M[8], c11 = M[0] * M[8] - M[2] * M[6], c12 = M[1] * M[6] - M[0] * M[7];
+        const double c20 = M[1] * M[5] - M[2] * M[4], c21 = M[2] * M[3] - M[0] * M[5], c22 = M[0] * M[4] - M[1] * M[3];
+        const double idet = 1.0 / (M[0] * c00 + M[1] * c01 + M[2] * c02);
+        mi[0] = c00 * idet; mi[1] = c10 * idet; mi[2] = c20 * idet;
+        mi[3] = c01 * idet; mi[4] = c11 * idet; mi[5] = c21 * idet;
+        mi[6] = c02 * idet; mi[7] = c12 * idet; mi[8] = c22 * idet;
+        if (PREDICT) {
+#pragma unroll
+            for (int r = 0; r < 9; ++r) minv[r * n + i] = mi[r];
+        }
+    }
     double g[3 * NG];
 #pragma unroll
     for (int k = 0; k < NG; ++k) {
         const double b0 = b[3 * k], b1 = b[3 * k + 1], b2 = b[3 * k + 2];
-        g[3 * k + 0] = (c00 * b0 + c10 * b1 + c20 * b2) * idet;
-        g[3 * k + 1] = (c01 * b0 + c11 * b1 + c21 * b2) * idet;
-        g[3 * k + 2] = (c02 * b0 + c12 * b1 + c22 * b2) * idet;
+        g[3 * k + 0] = mi[0] * b0 + mi[1] * b1 + mi[2] * b2;
+        g[3 * k + 1] = mi[3] * b0 + mi[4] * b1 + mi[5] * b2;
+        g[3 * k + 2] = mi[6] * b0 + mi[7] * b1 + mi[8] * b2;
     }
     if (c.limiter >= 1) {
         // S10: alpha = min(1, min_j psi_ij); with c_max = W_max - W_i >= 0 and
@@ -145,31 +200,39 @@ __global__ void __launch_bounds__(128, MM_GRAD_MINBLOCKS) k_gradient(MeshDev m, 
         // largest positive and the most negative Delta_ij = g . d_ij.
         // DM: min_j max(0, theta (W_j - W_i) / Delta_ij), tracked as a
         // fraction (num, den > 0) to avoid a division per face.
-        double dmax[NG], dmin[NG], rn[NG], rd[NG];
+        long long kdx[NG], kdn[NG];  // max / min of Delta, starting from 0
+        double rn[NG], rd[NG];
 #pragma unroll
-        for (int k = 0; k < NG; ++k) { dmax[k] = 0.0; dmin[k] = 0.0; rn[k] = 1.0; rd[k] = 1.0; }
+        for (int k = 0; k < NG; ++k) { kdx[k] = 0; kdn[k] = 0; rn[k] = 1.0; rd[k] = 1.0; }
+        const double cix = m.cen[i], ciy = m.cen[n + i], ciz = m.cen[2 * n + i];
+        const double *L = m.boxL + 3 * m.cbox[i];
         for (int e = e0; e < e1; ++e) {
-            const Nbr q = neighbour(m, e, L);
+            int f = m.inc_face[e];
+            const bool fwd = f >= 0;
+            if (!fwd) f = ~f;
             double dx, dy, dz;
             if (c.limiter == 3) {
                 // to the face centroid, in this cell's frame (subtract the image offset on the j side)
-                const double sh = q.sg > 0.0 ? 0.0 : 1.0;
-                dx = m.fcen[q.f] + sh * q.ox - cix;
-                dy = m.fcen[m.fs + q.f] + sh * q.oy - ciy;
-                dz = m.fcen[2 * m.fs + q.f] + sh * q.oz - ciz;
+                const int code = m.face_shift[f];
+                const double sh = fwd ? 0.0 : 1.0;
+                dx = m.fcen[f] - sh * image_axis(code % 3, L[0]) - cix;
+                dy = m.fcen[fs + f] - sh * image_axis((code / 3) % 3, L[1]) - ciy;
+                dz = m.fcen[2 * fs + f] - sh * image_axis(code / 9, L[2]) - ciz;
             } else {
-                dx = m.cen[q.o] + q.ox - cix;
-                dy = m.cen[n + q.o] + q.oy - ciy;
-                dz = m.cen[2 * n + q.o] + q.oz - ciz;
+                const long long sm = fwd ? 0LL : (long long)0x8000000000000000ULL;
+                dx = flip(geo[3 * fs + f], sm);
+                dy = flip(geo[4 * fs + f], sm);
+                dz = flip(geo[5 * fs + f], sm);
             }
-            const double ivo = FROM_CHARGES ? 1.0 / m.vol[q.o] : 1.0;
 #pragma unroll
             for (int k = 0; k < NG; ++k) {
                 const double del = g[3 * k] * dx + g[3 * k + 1] * dy + g[3 * k + 2] * dz;
-                dmax[k] = fmax(dmax[k], del);
-                dmin[k] = fmin(dmin[k], del);
+                const long long kd = okey(del);
+                kdx[k] = kmax(kdx[k], kd);
+                kdn[k] = kmin(kdn[k], kd);
                 if (c.limiter == 2 && del != 0.0) {
-                    double num = c.theta * (S[k * n + q.o] * ivo - Wi[k]);
+                    const int o = fwd ? m.face_j[f] : m.face_i[f];
+                    double num = c.theta * (S[k * n + o] - Wi[k]);
                     double den = del;
                     if (den < 0.0) { num = -num; den = -den; }
                     if (num < 0.0) num = 0.0;
@@ -182,9 +245,10 @@ __global__ void __launch_bounds__(128, MM_GRAD_MINBLOCKS) k_gradient(MeshDev m, 
             // the ratios matter only below 1 (min(1, x)), so most cells skip the
             // FP64 divisions: x < 1 exactly when the numerator is the smaller
             double a = 1.0;
-            const double up = wmax[k] - Wi[k], dn = wmin[k] - Wi[k];
-            if (dmax[k] > 0.0 && up < dmax[k]) a = fmin(a, up / dmax[k]);
-            if (dmin[k] < 0.0 && dn > dmin[k]) a = fmin(a, dn / dmin[k]);
+            const double up = okey_value(kx[k]) - Wi[k], dn = okey_value(kn[k]) - Wi[k];
+            const double dmax = okey_value(kdx[k]), dmin = okey_value(kdn[k]);
+            if (kdx[k] > 0 && up < dmax) a = fmin(a, up / dmax);
+            if (kdn[k] < 0 && dn > dmin) a = fmin(a, dn / dmin);
             if (c.limiter == 2) a *= fmin(1.0, rn[k] / rd[k]);
             g[3 * k] *= a;
             g[3 * k + 1] *= a;
@@ -242,24 +306,20 @@ __global__ void __launch_bounds__(128, MM_GRAD_MINBLOCKS) k_gradient(MeshDev m, 
 }
 
 template <int NG>
-static void launch_gradient_t(const MeshDev &m, const HydroCfg &c, const double *S, bool from_charges, double *grad,
-                              double *W_half, const double *dt, cudaStream_t s)
+static void launch_gradient_t(const MeshDev &m, const HydroCfg &c, const double *W, const double *geo, double *minv,
+                              bool minv_in, double *grad, double *W_half, const double *dt, cudaStream_t s)
 {
-    int nb = (int)((m.n + 127) / 128);
-    if (W_half) {
-        if (from_charges) k_gradient<true, true, NG><<<nb, 128, 0, s>>>(m, c, S, grad, W_half, dt);
-        else k_gradient<false, true, NG><<<nb, 128, 0, s>>>(m, c, S, grad, W_half, dt);
-    } else {
-        if (from_charges) k_gradient<true, false, NG><<<nb, 128, 0, s>>>(m, c, S, grad, W_half, dt);
-        else k_gradient<false, false, NG><<<nb, 128, 0, s>>>(m, c, S, grad, W_half, dt);
-    }
+    const int nb = (int)((m.n + 127) / 128);
+    if (W_half) k_gradient<true, false, NG><<<nb, 128, 0, s>>>(m, c, W, geo, minv, grad, W_half, dt);
+    else if (minv_in) k_gradient<false, true, NG><<<nb, 128, 0, s>>>(m, c, W, geo, minv, grad, W_half, dt);
+    else k_gradient<false, false, NG><<<nb, 128, 0, s>>>(m, c, W, geo, minv, grad, W_half, dt);
 }
 
-void launch_gradient(const MeshDev &m, const HydroCfg &c, const double *S, bool from_charges, double *grad,
-                     double *W_half, const double *dt, cudaStream_t s)
+void launch_gradient(const MeshDev &m, const HydroCfg &c, const double *W, const double *geo, double *minv,
+                     bool minv_in, double *grad, double *W_half, const double *dt, cudaStream_t s)
 {
-    if (c.entropy) launch_gradient_t<6>(m, c, S, from_charges, grad, W_half, dt, s);
-    else launch_gradient_t<5>(m, c, S, from_charges, grad, W_half, dt, s);
+    if (c.entropy) launch_gradient_t<6>(m, c, W, geo, minv, minv_in, grad, W_half, dt, s);
+    else launch_gradient_t<5>(m, c, W, geo, minv, minv_in, grad, W_half, dt, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -278,10 +338,10 @@ __global__ void __launch_bounds__(128) k_face_flux(MeshDev m, HydroCfg c, const 
     if (f >= face_count(m)) return;
     const int64_t n = m.n, fs = m.fs;
     const int i = m.face_i[f], j = m.face_j[f];
-    double sx, sy, sz;
-    decode_shift(m.face_shift[f], sx, sy, sz);
+    const int code = m.face_shift[f];
     const double *Lb = m.boxL + 3 * m.cbox[i];
-    const double ox = sx * Lb[0], oy = sy * Lb[1], oz = sz * Lb[2];
+    const double ox = image_axis(code % 3, Lb[0]), oy = image_axis((code / 3) % 3, Lb[1]),
+                 oz = image_axis(code / 9, Lb[2]);
     const double fx = m.fcen[f], fy = m.fcen[fs + f], fz = m.fcen[2 * fs + f];
     const double nx = m.normal[f], ny = m.normal[fs + f], nz = m.normal[2 * fs + f];
     // reconstruction to the face centroid: W_face = W_half + (x_f - c) . grad

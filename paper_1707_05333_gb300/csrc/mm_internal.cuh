@@ -127,8 +127,12 @@ struct Mixed {
 // device (graph mode).
 void launch_mixed_step(const MeshDev &m, const HydroCfg &c, const double *pos, const double *w, const double *dt,
                        Mixed x, double *U, cudaStream_t s, void (*mark)(void *, int, bool), void *mark_arg);
-void launch_gradient(const MeshDev &m, const HydroCfg &c, const double *U_or_W, bool from_charges,
-                     double *grad, double *W_half, const double *dt, cudaStream_t s);
+// geo [6][fs]: A n and d per face (launch_face_geom).  With W_half the
+// half-step predictor runs and M^-1 is stored in minv [9][n]; otherwise the
+// limited gradient goes to grad, with M^-1 read from minv when minv_in.
+void launch_face_geom(const MeshDev &m, double *geo, cudaStream_t s);
+void launch_gradient(const MeshDev &m, const HydroCfg &c, const double *W, const double *geo, double *minv,
+                     bool minv_in, double *grad, double *W_half, const double *dt, cudaStream_t s);
 void launch_face_flux(const MeshDev &m, const HydroCfg &c, const double *pos, const double *w,
                       const double *Wh, const double *grad, double *flux, cudaStream_t s);
 void launch_states(const MeshDev &m, const HydroCfg &c, const double *U, double *W, cudaStream_t s);
