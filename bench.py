@@ -240,10 +240,16 @@ def run_reference(args, world, rank):
 def algorithmic_bytes(stage, n, F):
     I = 2 * F
     if stage == "gradient_half_step":
-        # U, V, c of every cell + per incidence (face id, A, n, shift, i/j) + neighbour U,V,c gathers; write W_half
-        return n * (5 * 8 + 8 + 24) + n * 4 + I * 4 + F * (8 + 24 + 12) + n * 5 * 8
+        # states W = U / V (read U, V; write W); face geometry (read i, j, image, A, n and the
+        # centroids; write A n and d); predictor pass (read W, the CSR, the other cell and the
+        # geometry of each face; write W_half and M^-1)
+        states = n * (5 * 8 + 8) + n * 5 * 8
+        geom = F * (12 + 8 + 24) + n * 24 + F * 48
+        pred = n * 5 * 8 + n * 4 + I * 4 + F * (8 + 48) + n * 4 + n * (5 + 9) * 8
+        return states + geom + pred
     if stage == "gradient":
-        return n * (5 * 8 + 24) + n * 4 + I * 4 + F * (8 + 24 + 12) + n * 15 * 8
+        # read W_half, M^-1, the CSR, the other cell and the geometry; write the 15 gradient rows
+        return n * (5 + 9) * 8 + n * 4 + I * 4 + F * (8 + 48) + n * 15 * 8
     if stage == "face_flux":
         return F * (12 + 8 + 24 + 24) + n * (5 + 15 + 3 + 3 + 3) * 8 + F * 5 * 8
     if stage == "update":

@@ -184,6 +184,7 @@ static HydroCfg hydro_cfg(const mm_config &g)
     h.riemann = g.riemann;
     h.entropy = g.entropy;
     h.mach_th = g.mach_th;
+    h.igm1 = 1.0 / (g.gamma - 1.0);
     return h;
 }
 

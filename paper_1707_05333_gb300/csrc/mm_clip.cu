@@ -98,11 +98,35 @@ __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : 
 
 __device__ __forceinline__ unsigned lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
 
-__device__ __forceinline__ double warp_sum(double v)
+// Warp-wide sums of four values, on every lane, in a fixed order.  Each
+// exchange halves the number of partial sums a lane keeps (lanes with bit 4
+// clear keep a and b, the others c and d; then bit 3 splits those), so a
+// lane does six FP64 additions instead of twenty.
+__device__ __forceinline__ void warp_sum4(double &a, double &b, double &c, double &d, int lane)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-    return v;
+    const bool h4 = (lane & 16) != 0;
+    double k0 = h4 ? c : a, k1 = h4 ? d : b;
+    const double s0 = h4 ? a : c, s1 = h4 ? b : d;
+    k0 += __shfl_xor_sync(FULL, s0, 16);
+    k1 += __shfl_xor_sync(FULL, s1, 16);
+    const bool h3 = (lane & 8) != 0;
+    double k = h3 ? k1 : k0;
+    k += __shfl_xor_sync(FULL, h3 ? k0 : k1, 8);
+    k += __shfl_xor_sync(FULL, k, 4);
+    k += __shfl_xor_sync(FULL, k, 2);
+    k += __shfl_xor_sync(FULL, k, 1);
+    // lanes 0-7 hold the sum of a, 8-15 of b, 16-23 of c, 24-31 of d
+    a = __shfl_sync(FULL, k, 0);
+    b = __shfl_sync(FULL, k, 8);
+    c = __shfl_sync(FULL, k, 16);
+    d = __shfl_sync(FULL, k, 24);
+}
+
+// Magnitude order of doubles by their bit patterns (non-negative values, or
+// absolute values): an integer comparison in place of an FP64 one.
+__device__ __forceinline__ long long abs_bits(double x)
+{
+    return __double_as_longlong(x) & 0x7fffffffffffffffLL;
 }
 // Warp-wide maximum of a non-negative 64-bit value: the high words first,
 // then the low words of the lanes holding the largest high word.
@@ -853,7 +877,7 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
             // equation q . offset = 0.  Offsets from v0 keep the rounding
             // relative to the face's own size.
             const double qx = S.px[p], qy = S.py[p], qz = S.pz[p];
-            const double aqx = fabs(qx), aqy = fabs(qy), aqz = fabs(qz);
+            const long long aqx = abs_bits(qx), aqy = abs_bits(qy), aqz = abs_bits(qz);
             const int k = (aqx >= aqy && aqx >= aqz) ? 0 : (aqy >= aqz ? 1 : 2);
             const double *T1 = k == 0 ? S.ty : S.tx;  // kept coordinates (u, v)
             const double *T2 = k == 2 ? S.ty : S.tz;
@@ -895,9 +919,14 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
             if (!ok) { C.err |= ST_EDEGEN; continue; }
             const double aw = fabs(W);
             const double qn2 = 2.0 * S.po[p];  // |q|^2
-            const double iq = 1.0 / qk, iqk = fabs(iq);
+            // 1 / q_k and 1 / (3 W) from one reciprocal of 3 W q_k; a face
+            // of zero fan weight (area 0) takes 0 for both
+            const double w3 = 3.0 * W;
+            const bool nz = abs_bits(W) != 0;
+            const double r = nz ? 1.0 / (w3 * qk) : 0.0;
+            const double iq = w3 * r, iqk = fabs(iq);
             const double area = 0.5 * aw * (qn2 * rsqrt(qn2)) * iqk;
-            const double i3w = W != 0.0 ? 1.0 / (3.0 * W) : 0.0;
+            const double i3w = qk * r;
             const double du = su * i3w, dv = sv * i3w;
             const double dk = -(q1 * du + q2 * dv) * iq;
             const double fx = S.tx[t0] + (k == 0 ? dk : du);
@@ -916,17 +945,14 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
     __syncwarp();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) fan += __shfl_xor_sync(FULL, fan, o);
-    vl = warp_sum(vl);
-    vcx = warp_sum(vcx);
-    vcy = warp_sum(vcy);
-    vcz = warp_sum(vcz);
+    warp_sum4(vl, vcx, vcy, vcz, lane);
 
     int nface = 0;
     if (!C.err) {
         const int64_t sbase = (int64_t)self * MAXF;
         for (int p0 = 0; p0 < C.np; p0 += 32) {
             const int p = p0 + lane;
-            const bool keep = p < C.np && S.u.f.a[p] > amin;
+            const bool keep = p < C.np && abs_bits(S.u.f.a[p]) > abs_bits(amin);  // both >= 0
             const unsigned km = __ballot_sync(FULL, keep);
             if (keep) {
                 const int k = nface + __popc(km & lanemask_lt());

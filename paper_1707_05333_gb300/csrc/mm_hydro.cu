@@ -95,20 +95,8 @@ void launch_face_geom(const MeshDev &m, double *geo, cudaStream_t s)
     k_face_geom<<<(int)((nfl + 255) / 256), 256, 0, s>>>(m, geo);
 }
 
-// Order-preserving map of a double onto a signed 64-bit integer (the
-// sign-magnitude bit pattern turned into two's complement), its own inverse.
-// The running minima and maxima of the limiter are kept as such integers: the
-// comparisons then take integer instructions instead of FP64 ones, and the
-// extremum found is the same double bit for bit.
-__device__ __forceinline__ long long okey(double x)
-{
-    const long long b = __double_as_longlong(x);
-    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
-}
-__device__ __forceinline__ double okey_value(long long k)
-{
-    return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
-}
+// The running minima and maxima of the limiter are kept as order-preserving
+// integers (okey): integer comparisons in place of FP64 min/max.
 __device__ __forceinline__ long long kmax(long long a, long long b) { return a > b ? a : b; }
 __device__ __forceinline__ long long kmin(long long a, long long b) { return a < b ? a : b; }
 
@@ -396,7 +384,7 @@ __global__ void __launch_bounds__(128) k_face_flux(MeshDev m, HydroCfg c, const 
         R.vx = WR[1] * ir - wfx; R.vy = WR[2] * ir - wfy; R.vz = WR[3] * ir - wfz;
     }
     double F[5];
-    riemann_t<double>(c.riemann, L, R, nx, ny, nz, c.gamma, F);
+    riemann_t<double>(c.riemann, L, R, nx, ny, nz, c.gamma, c.igm1, F);
     // back to the lab frame: p -> p + m w, E -> E + p.w + |w|^2/2 m
     const double A = m.area[f];
     const double fm = F[0];

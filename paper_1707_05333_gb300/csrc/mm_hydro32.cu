@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(128) k_face_flux32(MeshDev m, HydroCfg c, Mixe
         R.vx = WR[1] * ir - wfx; R.vy = WR[2] * ir - wfy; R.vz = WR[3] * ir - wfz;
     }
     float F[5];
-    riemann_t<float>(c.riemann, L, R, fa.y, fa.z, fa.w, gam, F);
+    riemann_t<float>(c.riemann, L, R, fa.y, fa.z, fa.w, gam, 1.0f / gm1, F);
     const float A = fa.x, fm = F[0];
     const float fe = F[4] + F[1] * wfx + F[2] * wfy + F[3] * wfz + 0.5f * (wfx * wfx + wfy * wfy + wfz * wfz) * fm;
     x.flux[2 * f] = make_float4(A * fm, A * (F[1] + fm * wfx), A * (F[2] + fm * wfy), A * (F[3] + fm * wfz));

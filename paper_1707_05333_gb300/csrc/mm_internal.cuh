@@ -105,6 +105,7 @@ struct MeshDev {
 struct HydroCfg {
     double gamma, cfl, eta, chi, zeta, theta, rho_floor, eps_floor;
     double mach_th;  // energy/entropy switch threshold (Sec. 4.3)
+    double igm1;     // 1 / (gamma - 1), formed once on the host
     int limiter, regularize, riemann;
     int entropy;     // 1: a sixth state column rho A and the switch
 };

@@ -10,12 +10,35 @@ struct FaceStateT {
     T irho;                // 1 / rho (formed once per face state)
 };
 
+// Order-preserving map of a double onto a signed 64-bit integer (the
+// sign-magnitude bit pattern turned into two's complement), its own inverse:
+// comparisons of doubles as integers take integer instructions instead of
+// FP64 ones, the scarce unit, and select the same double bit for bit.
+__device__ __forceinline__ long long okey(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double okey_value(long long k)
+{
+    return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+}
+
 __device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
 __device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
-__device__ __forceinline__ double min_t(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ double min_t(double a, double b) { return okey(a) < okey(b) ? a : b; }
 __device__ __forceinline__ float min_t(float a, float b) { return fminf(a, b); }
-__device__ __forceinline__ double max_t(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ double max_t(double a, double b) { return okey(a) < okey(b) ? b : a; }
 __device__ __forceinline__ float max_t(float a, float b) { return fmaxf(a, b); }
+// x >= 0 (either zero included) and x > 0 for non-NaN x, by the sign bit
+__device__ __forceinline__ bool nonneg_t(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b >= 0 || b == (long long)0x8000000000000000ULL;
+}
+__device__ __forceinline__ bool nonneg_t(float x) { return x >= 0.0f; }
+__device__ __forceinline__ bool pos_t(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool pos_t(float x) { return x > 0.0f; }
 
 // HLLC in vector form along the unit normal (nx,ny,nz): the tangential
 // velocity rides along with the normal mass flux, so no explicit tangent
@@ -24,21 +47,19 @@ __device__ __forceinline__ float max_t(float a, float b) { return fmaxf(a, b); }
 // S_R > 0 -> F*_R; else F_R.
 template <class T>
 __device__ __forceinline__ void hllc_t(const FaceStateT<T> &L, const FaceStateT<T> &R, T nx, T ny, T nz, T gamma,
-                                       T F[5])
+                                       T igm1, T F[5])
 {
-    const T gm1 = gamma - T(1);
     const T ul = L.vx * nx + L.vy * ny + L.vz * nz;
     const T ur = R.vx * nx + R.vy * ny + R.vz * nz;
     const T cl = sqrt_t(gamma * L.P * L.irho), cr = sqrt_t(gamma * R.P * R.irho);
-    const T igm1 = T(1) / gm1;
     const T El = L.P * igm1 + T(0.5) * L.rho * (L.vx * L.vx + L.vy * L.vy + L.vz * L.vz);
     const T Er = R.P * igm1 + T(0.5) * R.rho * (R.vx * R.vx + R.vy * R.vy + R.vz * R.vz);
     const T sl = min_t(ul - cl, ur - cr);
     const T sr = max_t(ul + cl, ur + cr);
     const T ml = L.rho * (sl - ul), mr = R.rho * (sr - ur);
     const T ss = (R.P - L.P + ul * ml - ur * mr) / (ml - mr);
-    const bool left = (sl >= T(0)) || (ss >= T(0));
-    const bool star = (sl < T(0)) && (left || sr > T(0));
+    const bool left = nonneg_t(sl) || nonneg_t(ss);
+    const bool star = !nonneg_t(sl) && (left || pos_t(sr));
     const FaceStateT<T> &K = left ? L : R;
     const T uk = left ? ul : ur;
     const T Ek = left ? El : Er;
@@ -67,13 +88,11 @@ __device__ __forceinline__ void hllc_t(const FaceStateT<T> &L, const FaceStateT<
 // form of the conservation laws (no contact wave).
 template <class T>
 __device__ __forceinline__ void hll_t(const FaceStateT<T> &L, const FaceStateT<T> &R, T nx, T ny, T nz, T gamma,
-                                      T F[5])
+                                      T igm1, T F[5])
 {
-    const T gm1 = gamma - T(1);
     const T ul = L.vx * nx + L.vy * ny + L.vz * nz;
     const T ur = R.vx * nx + R.vy * ny + R.vz * nz;
     const T cl = sqrt_t(gamma * L.P * L.irho), cr = sqrt_t(gamma * R.P * R.irho);
-    const T igm1 = T(1) / gm1;
     const T El = L.P * igm1 + T(0.5) * L.rho * (L.vx * L.vx + L.vy * L.vy + L.vz * L.vz);
     const T Er = R.P * igm1 + T(0.5) * R.rho * (R.vx * R.vx + R.vy * R.vy + R.vz * R.vz);
     const T sl = min_t(ul - cl, ur - cr);
@@ -147,10 +166,10 @@ __device__ __forceinline__ T passive_flux_t(int kind, const FaceStateT<T> &L, co
 // The configured solver: 0 HLLC, 1 HLL.
 template <class T>
 __device__ __forceinline__ void riemann_t(int kind, const FaceStateT<T> &L, const FaceStateT<T> &R, T nx, T ny, T nz,
-                                          T gamma, T F[5])
+                                          T gamma, T igm1, T F[5])
 {
-    if (kind == 1) hll_t<T>(L, R, nx, ny, nz, gamma, F);
-    else hllc_t<T>(L, R, nx, ny, nz, gamma, F);
+    if (kind == 1) hll_t<T>(L, R, nx, ny, nz, gamma, igm1, F);
+    else hllc_t<T>(L, R, nx, ny, nz, gamma, igm1, F);
 }
 
 // The same floors for a face state, also returning 1 / rho of the result
