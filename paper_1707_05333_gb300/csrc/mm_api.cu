@@ -316,6 +316,9 @@ static mm_status setup_boxes(mm_ctx *c, int64_t n, const int64_t *box_off, const
             g.bs[d] = L[d] / (double)gd;
             g.ibs[d] = (double)gd / L[d];
             g.L[d] = L[d];
+            g.Lf[d] = (float)g.L[d];
+            g.bsf[d] = (float)g.bs[d];
+            g.ibsf[d] = (float)g.ibs[d];
             c->boxL_host[3 * b + d] = L[d];
             nbb *= gd;
         }
@@ -441,7 +444,8 @@ static mm_status tess_enqueue(mm_ctx *c, const double *pos, bool fixed)
     launch_face_write(n, pos, boxes, cbox, sl, P<unsigned long long>(c->emit_mask), P<unsigned long long>(c->conf_mask),
                       P<signed char>(c->partner), P<int>(c->face_off), P<int>(c->inc_off), P<int>(c->face_i),
                       P<int>(c->face_j), P<int>(c->face_shift), P<double>(c->face_area), P<double>(c->face_normal),
-                      P<double>(c->face_cen), c->fcap, P<int>(c->inc_face), c->icap, c->st, s);
+                      P<double>(c->face_cen), c->fcap, P<int>(c->inc_face), c->icap, P<double>(c->vol),
+                      P<double>(c->cen), c->st, s);
     CKLAUNCH();
     stage_mark(c, MM_STAGE_FACES, false);
     c->launches += 1;

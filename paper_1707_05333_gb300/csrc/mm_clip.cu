@@ -89,6 +89,8 @@ struct ClipSmem : VertStore<PREC> {
     unsigned tv[TMAX];                    // a | b << 8 | c << 16
     unsigned bm[2 * PMAX];                // removed directed edges x -> y: bit y % 32 of word 2x + y / 32
     unsigned stage[NSTAGE];               // triangles created by the current cut
+    double off[9];               // image offsets s L - p: off[3 d + s + 1], s = -1, 0, +1
+    float offf[9];               // their FP32 roundings (the gather filter)
     float4 pf[PREC ? PMAX : 1];  // FP32 planes (q, o)
     float pfn[PREC ? PMAX : 1];  // FP32 |q| = sqrt(2 o) of each plane (for the vertex error bound)
 };
@@ -120,6 +122,17 @@ __device__ __forceinline__ void warp_sum4(double &a, double &b, double &c, doubl
     b = __shfl_sync(FULL, k, 8);
     c = __shfl_sync(FULL, k, 16);
     d = __shfl_sync(FULL, k, 24);
+}
+
+// Bit pattern of (double) f for a finite f >= 0: a normal float's exponent
+// moved to the double bias (integer operations), else the conversion.
+__device__ __forceinline__ long long dbits_of_float(float f)
+{
+    const unsigned fb = __float_as_uint(f);
+    const unsigned e = fb >> 23;
+    if (e != 0u && e < 255u)
+        return (long long)(((unsigned long long)(e + (1023u - 127u)) << 52) | ((unsigned long long)(fb & 0x7fffffu) << 29));
+    return __double_as_longlong((double)f);
 }
 
 // Magnitude order of doubles by their bit patterns (non-negative values, or
@@ -566,7 +579,6 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
 // generators, this generator and the box.
 struct Gather {
     const double4_32a *sorted;
-    double px, py, pz, Lx, Ly, Lz;
 };
 
 template <int PREC>
@@ -579,10 +591,7 @@ __device__ void flush_batch(ClipSmem<PREC> &S, int &ncand, CellState &C, int lan
         const int code = S.csh[k];
         const double4_32a P = G.sorted[S.cid[k]];
         const int dx = code % 3, dy = (code / 3) % 3, dz = code / 9;
-        const double ox = dx == 0 ? -G.Lx - G.px : (dx == 2 ? G.Lx - G.px : -G.px);
-        const double oy = dy == 0 ? -G.Ly - G.py : (dy == 2 ? G.Ly - G.py : -G.py);
-        const double oz = dz == 0 ? -G.Lz - G.pz : (dz == 2 ? G.Lz - G.pz : -G.pz);
-        const double qx = P.x + ox, qy = P.y + oy, qz = P.z + oz;
+        const double qx = P.x + S.off[dx], qy = P.y + S.off[3 + dy], qz = P.z + S.off[6 + dz];
         S.u.c.x[k] = qx; S.u.c.y[k] = qy; S.u.c.z[k] = qz;
         S.u.c.d2[k] = __double_as_longlong(__fma_rn(qx, qx, __fma_rn(qy, qy, __dmul_rn(qz, qz))));
         S.cid[k] = (int)__double_as_longlong(P.w);
@@ -646,31 +655,41 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
     // A box's cells occupy the same range of indices in the input order and in
     // the binned order (the bins are laid out box by box), so the box of
     // binned entry w is cbox[w]: no need to wait for the generator's id.
-    const BoxDev g = boxes[cbox[w]];
-    const double4_32a me = sorted[w];
-    const double px = me.x, py = me.y, pz = me.z;
-    const int self = (int)__double_as_longlong(me.w);
+    const BoxDev *const gp = boxes + cbox[w];  // for the lane-indexed fields
+    const BoxDev g = *gp;
+    const int self = (int)__double_as_longlong(sorted[w].w);
     const double amin = g.amin;
-    const double Lx = g.L[0], Ly = g.L[1], Lz = g.L[2];
+    // The setup runs in FP32 and integer arithmetic wherever a bound, not an
+    // exact value, is needed: on this part FP64 is the scarce unit.
 
     // starting box: planes 0..5 = +x,-x,+y,-y,+z,-z self-image bisectors
     if (lane < 6) {
         const int d = lane >> 1;
-        const double sg = (lane & 1) ? -1.0 : 1.0;
-        const double L = d == 0 ? Lx : (d == 1 ? Ly : Lz);
-        S.px[lane] = d == 0 ? sg * L : 0.0;
-        S.py[lane] = d == 1 ? sg * L : 0.0;
-        S.pz[lane] = d == 2 ? sg * L : 0.0;
-        S.po[lane] = 0.5 * L * L;
+        const double L = gp->L[d];
+        const double sL = (lane & 1) ? -L : L;
+        S.px[lane] = d == 0 ? sL : 0.0;
+        S.py[lane] = d == 1 ? sL : 0.0;
+        S.pz[lane] = d == 2 ? sL : 0.0;
+        S.po[lane] = half_of(__double_as_longlong(L * L));  // L^2 / 2
         S.pnb[lane] = self;
         int s3[3] = {0, 0, 0};
         s3[d] = (lane & 1) ? -1 : 1;
         S.psh[lane] = (s3[0] + 1) + 3 * (s3[1] + 1) + 9 * (s3[2] + 1);
         if constexpr (PREC == 1) {
             const float fo = (float)S.po[lane];
-            S.pf[lane] = make_float4((float)S.px[lane], (float)S.py[lane], (float)S.pz[lane], fo);
+            const float Lf = gp->Lf[d];
+            const float sLf = (lane & 1) ? -Lf : Lf;  // (float)(+-L)
+            S.pf[lane] = make_float4(d == 0 ? sLf : 0.0f, d == 1 ? sLf : 0.0f, d == 2 ? sLf : 0.0f, fo);
             S.pfn[lane] = sqrtf(2.0f * fo);
         }
+    } else if (lane < 15) {
+        // image offsets s L - p of the three axes (lanes 6..14: axis, s)
+        const int d = (lane - 6) / 3, s = (lane - 6) % 3;
+        const double p = d == 0 ? sorted[w].x : (d == 1 ? sorted[w].y : sorted[w].z);
+        const double L = gp->L[d];
+        const double o = s == 1 ? -p : (s == 0 ? -L - p : L - p);
+        S.off[lane - 6] = o;
+        S.offf[lane - 6] = (float)o;
     }
     if (lane < 8) {
         // corner (sx, sy, sz): planes chosen by sign, ordered so det > 0
@@ -679,46 +698,51 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
         // det(sign_x e_x, sign_y e_y, sign_z e_z) = product of signs
         if ((sx ^ sy ^ sz) & 1) { unsigned t = b; b = c; c = t; }
         S.tv[lane] = a | (b << 8) | (c << 16);
-        const double x = sx ? -0.5 * Lx : 0.5 * Lx, y = sy ? -0.5 * Ly : 0.5 * Ly, z = sz ? -0.5 * Lz : 0.5 * Lz;
-        if constexpr (PREC == 0) S.tr2[lane] = r2_bits64(x, y, z);
-        else S.tr2[lane] = (long long)__float_as_int((float)(x * x + y * y + z * z) * 1.000001f);
-        if constexpr (PREC == 0) { S.tx[lane] = x; S.ty[lane] = y; S.tz[lane] = z; }
-        else S.tf[lane] = make_float4((float)x, (float)y, (float)z, 0.0f);
+        if constexpr (PREC == 0) {
+            const double x = sx ? -0.5 * g.L[0] : 0.5 * g.L[0], y = sy ? -0.5 * g.L[1] : 0.5 * g.L[1],
+                         z = sz ? -0.5 * g.L[2] : 0.5 * g.L[2];
+            S.tr2[lane] = r2_bits64(x, y, z);
+            S.tx[lane] = x; S.ty[lane] = y; S.tz[lane] = z;
+        } else {
+            // (float)(+-L/2) = +-Lf/2 exactly; |v|^2 from them in FP32, widened
+            // past its rounding (an upper bound is all the limit needs)
+            const float x = 0.5f * (sx ? -g.Lf[0] : g.Lf[0]), y = 0.5f * (sy ? -g.Lf[1] : g.Lf[1]),
+                        z = 0.5f * (sz ? -g.Lf[2] : g.Lf[2]);
+            S.tr2[lane] = (long long)__float_as_int(fmaf(x, x, fmaf(y, y, z * z)) * 1.000001f);
+            S.tf[lane] = make_float4(x, y, z, 0.0f);
+        }
     }
     for (int r = lane; r < 2 * PMAX; r += 32) S.bm[r] = 0u;
     __syncwarp();
     CellState C;
     C.np = 6;
     C.nt = 8;
-    C.lim = __double_as_longlong(Lx * Lx + Ly * Ly + Lz * Lz);
+    // 4 r_max^2 of the starting box is |L|^2: an FP32 upper bound of it
+    C.lim = dbits_of_float(fmaf(g.Lf[0], g.Lf[0], fmaf(g.Lf[1], g.Lf[1], g.Lf[2] * g.Lf[2])) * 1.000001f);
     C.limk = __int_as_float(0x7f800000);  // keep everything until the first cut
-    C.slack = 2e-6f * (float)fmax(Lx, fmax(Ly, Lz));
+    C.slack = 2e-6f * fmaxf(g.Lf[0], fmaxf(g.Lf[1], g.Lf[2]));
     C.err = 0;
     C.cuts = 0;
     C.pred64 = C.solve64 = C.fan64 = C.tested = 0;
 
+    // Home bin of p in FP32 (the FP32 copy of p from the bin sort), and the
+    // distance from p to the nearer wall of that bin per axis, lowered by the
+    // slack (which exceeds the FP32 rounding of the whole computation): the
+    // bins of rings 0..r then cover at least the radius min_d (edge_d + r bs_d),
+    // also where rounding puts p just outside the bin.
     int cb[3];
+    float edge[3];
     {
-        const double pp[3] = {px, py, pz};
+        const float4 mf = sortedf[w];
+        const float pp[3] = {mf.x, mf.y, mf.z};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            const int c = (int)floor(pp[d] * g.ibs[d]);  // the binning kernel's formula
+            const int c = (int)floorf(pp[d] * g.ibsf[d]);
             cb[d] = c < 0 ? 0 : (c >= g.g[d] ? g.g[d] - 1 : c);
+            edge[d] = fminf(pp[d] - (float)cb[d] * g.bsf[d], (float)(cb[d] + 1) * g.bsf[d] - pp[d]) - C.slack;
         }
     }
-    // image offsets s L - p for s = -1, 0, +1 (selected, not recomputed, per bin)
-    const Gather G{sorted, px, py, pz, Lx, Ly, Lz};
-    const double omx = -Lx - px, o0x = -px, opx = Lx - px;
-    const double omy = -Ly - py, o0y = -py, opy = Ly - py;
-    const double omz = -Lz - pz, o0z = -pz, opz = Lz - pz;
-    // distance from p to the nearer wall of its own bin, per axis: the block of
-    // rings 0..r then covers the radius min_d (edge_d + r bs_d)
-    double edge[3];
-    {
-        const double pp[3] = {px, py, pz};
-#pragma unroll
-        for (int d = 0; d < 3; ++d) edge[d] = fmin(pp[d] - cb[d] * g.bs[d], (cb[d] + 1) * g.bs[d] - pp[d]);
-    }
+    const Gather G{sorted};
     // The candidate gather is resumable: each lane walks the bins of the
     // current ring 32 at a time, the buffer is flushed (sorted and clipped)
     // whenever it cannot take another 32 candidates and at the end of every
@@ -765,9 +789,10 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
                     }
                 }
                 // FP32 offsets for the gather filter (the exact ones are formed at flush time)
-                offx = (float)(shx < 0 ? omx : (shx > 0 ? opx : o0x));
-                offy = (float)(shy < 0 ? omy : (shy > 0 ? opy : o0y));
-                offz = (float)(shz < 0 ? omz : (shz > 0 ? opz : o0z));
+                // (images two or more boxes away gather nothing: any offset will do)
+                offx = S.offf[shx < 0 ? 0 : (shx > 0 ? 2 : 1)];
+                offy = S.offf[3 + (shy < 0 ? 0 : (shy > 0 ? 2 : 1))];
+                offz = S.offf[6 + (shz < 0 ? 0 : (shz > 0 ? 2 : 1))];
                 code = (shx + 1) + 3 * (shy + 1) + 9 * (shz + 1);
                 selfimg = (abs(shx) + abs(shy) + abs(shz)) <= 1;
                 continue;
@@ -795,9 +820,10 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
         if (C.err || !ring_done) continue;
         ++rings;
         // radius the gathered rings are guaranteed to cover
-        const double rr = (double)rh;
-        const double R = fmin(fmin(fma(rr, g.bs[0], edge[0]), fma(rr, g.bs[1], edge[1])), fma(rr, g.bs[2], edge[2]));
-        if (C.lim <= __double_as_longlong(R * R)) break;
+        const float rr = (float)rh;
+        const float R = fmaxf(fminf(fminf(fmaf(rr, g.bsf[0], edge[0]), fmaf(rr, g.bsf[1], edge[1])),
+                                    fmaf(rr, g.bsf[2], edge[2])), 0.0f);
+        if (C.lim <= dbits_of_float(R * R * 0.999999f)) break;  // R^2 rounded down
         rl = rh + 1;
         rh = rl;
         if (rh > MAXRING) { C.err |= ST_ECAP_RING; break; }
@@ -962,9 +988,9 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
                     sl.sh[s] = (unsigned char)S.psh[p];
                     sl.area[s] = S.u.f.a[p];
                     const int64_t ns = n * (int64_t)MAXF;
-                    sl.fc[s] = px + S.u.f.x[p];
-                    sl.fc[ns + s] = py + S.u.f.y[p];
-                    sl.fc[2 * ns + s] = pz + S.u.f.z[p];
+                    sl.fc[s] = S.u.f.x[p];  // relative to the generator
+                    sl.fc[ns + s] = S.u.f.y[p];
+                    sl.fc[2 * ns + s] = S.u.f.z[p];
                 }
             }
             nface += __popc(km);
@@ -978,11 +1004,12 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
             nface = 0;
         }
         sl.cnt[self] = nface;
+        // volume and first moment about the generator; the face kernel turns
+        // the moment into the centroid (one thread per cell, off this warp)
         vol[self] = vl;
-        const double ivl = 1.0 / vl;
-        cen[self] = px + vcx * ivl;
-        cen[n + self] = py + vcy * ivl;
-        cen[2 * n + self] = pz + vcz * ivl;
+        cen[self] = vcx;
+        cen[n + self] = vcy;
+        cen[2 * n + self] = vcz;
         if (collect) {
             atomicMax(&st->max_cand, maxcand);
             atomicMax(&st->max_planes, C.np);

@@ -52,10 +52,20 @@ __global__ void k_face_write(int64_t n, const double *__restrict__ pos, const Bo
                              const int *__restrict__ inc_off, int *__restrict__ face_i, int *__restrict__ face_j,
                              int *__restrict__ face_shift, double *__restrict__ face_area,
                              double *__restrict__ face_normal, double *__restrict__ face_cen, int64_t fcap,
-                             int *__restrict__ inc_face, int64_t icap, DevStatus *st)
+                             int *__restrict__ inc_face, int64_t icap, const double *__restrict__ vol,
+                             double *__restrict__ cen, DevStatus *st)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const double pix = pos[i], piy = pos[n + i], piz = pos[2 * n + i];
+    {
+        // the cell centroid from the clipper's volume and first moment about
+        // the generator
+        const double ivl = 1.0 / vol[i];
+        cen[i] = pix + cen[i] * ivl;
+        cen[n + i] = piy + cen[n + i] * ivl;
+        cen[2 * n + i] = piz + cen[2 * n + i] * ivl;
+    }
     const double *L = boxes[cbox[i]].L;
     // a fixed capacity (graph mode) that is too small is reported, never overrun
     if ((int64_t)face_off[i + 1] > fcap || (int64_t)inc_off[i + 1] > icap) {
@@ -81,9 +91,9 @@ __global__ void k_face_write(int64_t n, const double *__restrict__ pos, const Bo
                 const double ox = cx == 1 ? 0.0 : (cx == 2 ? L[0] : -L[0]);
                 const double oy = cy == 1 ? 0.0 : (cy == 2 ? L[1] : -L[1]);
                 const double oz = cz == 1 ? 0.0 : (cz == 2 ? L[2] : -L[2]);
-                const double qx = pos[j] + ox - pos[i];
-                const double qy = pos[n + j] + oy - pos[n + i];
-                const double qz = pos[2 * n + j] + oz - pos[2 * n + i];
+                const double qx = pos[j] + ox - pix;
+                const double qy = pos[n + j] + oy - piy;
+                const double qz = pos[2 * n + j] + oz - piz;
                 const double inv = rsqrt(qx * qx + qy * qy + qz * qz);
                 face_i[f] = (int)i;
                 face_j[f] = j;
@@ -92,9 +102,9 @@ __global__ void k_face_write(int64_t n, const double *__restrict__ pos, const Bo
                 face_normal[f] = qx * inv;
                 face_normal[fcap + f] = qy * inv;
                 face_normal[2 * fcap + f] = qz * inv;
-                face_cen[f] = sl.fc[s];
-                face_cen[fcap + f] = sl.fc[ns + s];
-                face_cen[2 * fcap + f] = sl.fc[2 * ns + s];
+                face_cen[f] = pix + sl.fc[s];  // the slots hold it relative to the generator
+                face_cen[fcap + f] = piy + sl.fc[ns + s];
+                face_cen[2 * fcap + f] = piz + sl.fc[2 * ns + s];
             }
             inc_face[e++] = f;
         } else {
@@ -117,12 +127,13 @@ void launch_face_write(int64_t n, const double *pos, const BoxDev *boxes, const 
                        const unsigned long long *emit_mask, const unsigned long long *conf_mask,
                        const signed char *partner, const int *face_off, const int *inc_off, int *face_i,
                        int *face_j, int *face_shift, double *face_area, double *face_normal, double *face_cen,
-                       int64_t fcap, int *inc_face, int64_t icap, DevStatus *st, cudaStream_t s)
+                       int64_t fcap, int *inc_face, int64_t icap, const double *vol, double *cen, DevStatus *st,
+                       cudaStream_t s)
 {
     int nb = (int)((n + 127) / 128);
     k_face_write<<<nb, 128, 0, s>>>(n, pos, boxes, cbox, sl, emit_mask, conf_mask, partner, face_off, inc_off,
                                     face_i, face_j, face_shift, face_area, face_normal, face_cen, fcap, inc_face,
-                                    icap, st);
+                                    icap, vol, cen, st);
 }
 
 }  // namespace mm

@@ -55,6 +55,7 @@ struct BoxDev {
     double ibs[3]; // 1 / bin edge (bin of x: floor(x * ibs))
     double L[3];   // box size
     double amin;   // faces with area <= amin are dropped
+    float Lf[3], bsf[3], ibsf[3];  // FP32 roundings of L, bs, ibs (the clipper's setup arithmetic)
 };
 
 struct Slots {         // per-cell face slots written by the clipper
@@ -62,7 +63,7 @@ struct Slots {         // per-cell face slots written by the clipper
     int *nb;           // [n*MAXF]
     unsigned char *sh; // [n*MAXF] shift code
     double *area;      // [n*MAXF]
-    double *fc;        // [3][n*MAXF] face centroid, absolute, cell frame
+    double *fc;        // [3][n*MAXF] face centroid relative to the generator
 };
 
 // kernels' host launchers (stream-ordered, no syncs)
@@ -76,6 +77,8 @@ void launch_bin_sort(const int *start, int64_t nbins, double4_32a *sorted, float
 size_t scan_tmp_size(int64_t n);
 void launch_scan(const int *in, int *out, int64_t n, int *tmp, cudaStream_t s);
 
+// vol receives each cell's volume and cen its first moment about the
+// generator ([3][n]); launch_face_write turns the moment into the centroid.
 void launch_clip(const double4_32a *sorted, const float4 *sortedf, const int *start, int64_t n, const BoxDev *boxes,
                  const int *cbox,
                  int precision, int collect, int warps, int cand_cap, double *vol, double *cen, Slots sl,
@@ -87,7 +90,8 @@ void launch_face_write(int64_t n, const double *pos, const BoxDev *boxes, const 
                        const unsigned long long *emit_mask, const unsigned long long *conf_mask,
                        const signed char *partner, const int *face_off, const int *inc_off,
                        int *face_i, int *face_j, int *face_shift, double *face_area, double *face_normal,
-                       double *face_cen, int64_t fcap, int *inc_face, int64_t icap, DevStatus *st, cudaStream_t s);
+                       double *face_cen, int64_t fcap, int *inc_face, int64_t icap, const double *vol,
+                       double *cen, DevStatus *st, cudaStream_t s);
 
 struct MeshDev {
     int64_t n;           // cells
