@@ -416,6 +416,14 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
             }
         }
         outm.put(c, __ballot_sync(FULL, o));
+        if (o) {
+            // mark the directed edges of the removed triangle
+            const unsigned v = S.tv[t];
+            const unsigned a = v & 255u, b = (v >> 8) & 255u, cc = (v >> 16) & 255u;
+            atomicOr(&S.bm[2 * a + (b >> 5)], 1u << (b & 31u));
+            atomicOr(&S.bm[2 * b + (cc >> 5)], 1u << (cc & 31u));
+            atomicOr(&S.bm[2 * cc + (a >> 5)], 1u << (a & 31u));
+        }
     }
     if ((outm.lo | outm.hi) == 0ull) return;
     // the new plane takes a fresh slot while fewer than 32 are in use (one
@@ -447,17 +455,6 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
         if constexpr (PREC == 1) {
             S.pf[kp] = make_float4(fqx, fqy, fqz, foff);
             S.pfn[kp] = sqrtf(2.0f * foff);
-        }
-    }
-    // mark the directed edges of the removed triangles
-#pragma unroll 1
-    for (int c = 0; c < nchunk; ++c) {
-        if ((outm.get(c) >> lane) & 1u) {
-            unsigned v = S.tv[c * 32 + lane];
-            unsigned a = v & 255u, b = (v >> 8) & 255u, cc = (v >> 16) & 255u;
-            atomicOr(&S.bm[2 * a + (b >> 5)], 1u << (b & 31u));
-            atomicOr(&S.bm[2 * b + (cc >> 5)], 1u << (cc & 31u));
-            atomicOr(&S.bm[2 * cc + (a >> 5)], 1u << (a & 31u));
         }
     }
     __syncwarp();
@@ -505,8 +502,40 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
     const int nrem = outm.count();
     const int nkept = C.nt - nrem;
     if (nkept + nnew > TMAX) { C.err |= ST_ECAP_TRI; return; }
-    // compact the kept triangles in place (destinations never pass sources)
+    // the new vertices first, one per lane (nnew <= 32), kept in registers:
+    // their arithmetic then overlaps the compaction's shared-memory traffic
     long long mr = 0;  // this lane's largest |v|^2 bound, for the new limit
+    const bool mk = lane < nnew;
+    unsigned nvt = 0;
+    long long nr2 = 0;
+    double nX = 0.0, nY = 0.0, nZ = 0.0;
+    float4 nf = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (mk) {
+        nvt = S.stage[lane];
+        if constexpr (PREC == 0) {
+            vertex64(S, nvt & 255u, (nvt >> 8) & 255u, kp, nX, nY, nZ);
+            nr2 = r2_bits64(nX, nY, nZ);
+        } else {
+            float x, y, z, er;
+            vertex32(S, nvt & 255u, (nvt >> 8) & 255u, kp, x, y, z, er);
+            if (!(er < 1e30f)) {
+                // ill-conditioned intersection: solve it in FP64 now and keep
+                // its FP32 rounding, whose error is then one rounding per axis
+                double X, Y, Z;
+                vertex64_call(S, nvt & 255u, (nvt >> 8) & 255u, kp, X, Y, Z);
+                x = (float)X; y = (float)Y; z = (float)Z;
+                er = 1.2e-7f * (fabsf(x) + fabsf(y) + fabsf(z)) + 1e-38f;
+            }
+            nf = make_float4(x, y, z, er);
+            // an FP32 upper bound of (|v| + er)^2 <= |v|^2 + er (2 |v|_1 + er),
+            // kept as the bit pattern of a positive float
+            const float s2 = fmaf(x, x, fmaf(y, y, z * z));
+            const float l1 = fabsf(x) + fabsf(y) + fabsf(z);
+            nr2 = (long long)__float_as_int(fmaf(er, fmaf(2.0f, l1, er), s2) * 1.00001f);
+        }
+        mr = nr2;
+    }
+    // compact the kept triangles in place (destinations never pass sources)
     int dst = 0;
 #pragma unroll 1
     for (int c = 0; c < nchunk; ++c) {
@@ -536,36 +565,12 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
         __syncwarp();
     }
     // append the new vertices
-    for (int e = lane; e < nnew; e += 32) {
-        const unsigned v = S.stage[e];
-        const int t = nkept + e;
-        S.tv[t] = v;
-        if constexpr (PREC == 0) {
-            double x, y, z;
-            vertex64(S, v & 255u, (v >> 8) & 255u, kp, x, y, z);
-            S.tx[t] = x; S.ty[t] = y; S.tz[t] = z;
-            S.tr2[t] = r2_bits64(x, y, z);
-            mr = max(mr, S.tr2[t]);
-        } else {
-            float x, y, z, er;
-            vertex32(S, v & 255u, (v >> 8) & 255u, kp, x, y, z, er);
-            if (!(er < 1e30f)) {
-                // ill-conditioned intersection: solve it in FP64 now and keep
-                // its FP32 rounding, whose error is then one rounding per axis
-                double X, Y, Z;
-                vertex64_call(S, v & 255u, (v >> 8) & 255u, kp, X, Y, Z);
-                x = (float)X; y = (float)Y; z = (float)Z;
-                er = 1.2e-7f * (fabsf(x) + fabsf(y) + fabsf(z)) + 1e-38f;
-            }
-            S.tf[t] = make_float4(x, y, z, er);
-            // an FP32 upper bound of (|v| + er)^2 <= |v|^2 + er (2 |v|_1 + er),
-            // kept as the bit pattern of a positive float
-            const float s2 = fmaf(x, x, fmaf(y, y, z * z));
-            const float l1 = fabsf(x) + fabsf(y) + fabsf(z);
-            const long long r2n = (long long)__float_as_int(fmaf(er, fmaf(2.0f, l1, er), s2) * 1.00001f);
-            S.tr2[t] = r2n;
-            mr = max(mr, r2n);
-        }
+    if (mk) {
+        const int t = nkept + lane;
+        S.tv[t] = nvt;
+        S.tr2[t] = nr2;
+        if constexpr (PREC == 0) { S.tx[t] = nX; S.ty[t] = nY; S.tz[t] = nZ; }
+        else S.tf[t] = nf;
     }
     __syncwarp();
     if (PREC == 0) C.solve64 += nnew;
