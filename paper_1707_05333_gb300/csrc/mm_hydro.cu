@@ -342,9 +342,9 @@ __global__ void __launch_bounds__(128) k_face_flux(MeshDev m, HydroCfg c, const 
         WR[k] = Wh[k * n + j] + drx * grad[(3 * k) * n + j] + dry * grad[(3 * k + 1) * n + j] + drz * grad[(3 * k + 2) * n + j];
     }
     const bool vac_l = !(WL[0] >= c.rho_floor), vac_r = !(WR[0] >= c.rho_floor);
-    double irl, irr;
-    apply_floor_ir_t<double>(WL, c.rho_floor, c.eps_floor, irl);
-    apply_floor_ir_t<double>(WR, c.rho_floor, c.eps_floor, irr);
+    double irl, irr, kel, ker;
+    apply_floor_ir_t<double>(WL, c.rho_floor, c.eps_floor, irl, kel);
+    apply_floor_ir_t<double>(WR, c.rho_floor, c.eps_floor, irr, ker);
     if constexpr (NG == 6) {
         // rho A at the face: a state reset to the density floor takes the
         // floor state's own A; otherwise the reconstruction, not below 0
@@ -373,14 +373,14 @@ __global__ void __launch_bounds__(128) k_face_flux(MeshDev m, HydroCfg c, const 
         const double ir = irl;
         L.rho = WL[0];
         L.irho = ir;
-        L.P = gm1 * (WL[4] - 0.5 * (WL[1] * WL[1] + WL[2] * WL[2] + WL[3] * WL[3]) * ir);
+        L.P = gm1 * (WL[4] - kel);
         L.vx = WL[1] * ir - wfx; L.vy = WL[2] * ir - wfy; L.vz = WL[3] * ir - wfz;
     }
     {
         const double ir = irr;
         R.rho = WR[0];
         R.irho = ir;
-        R.P = gm1 * (WR[4] - 0.5 * (WR[1] * WR[1] + WR[2] * WR[2] + WR[3] * WR[3]) * ir);
+        R.P = gm1 * (WR[4] - ker);
         R.vx = WR[1] * ir - wfx; R.vy = WR[2] * ir - wfy; R.vz = WR[3] * ir - wfz;
     }
     double F[5];

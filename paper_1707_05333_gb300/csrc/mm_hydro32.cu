@@ -249,9 +249,9 @@ __global__ void __launch_bounds__(128) k_face_flux32(MeshDev m, HydroCfg c, Mixe
         }
     }
     const float rf = (float)c.rho_floor, ef = (float)c.eps_floor;
-    float irl, irr;
-    apply_floor_ir_t<float>(WL, rf, ef, irl);
-    apply_floor_ir_t<float>(WR, rf, ef, irr);
+    float irl, irr, kel, ker;
+    apply_floor_ir_t<float>(WL, rf, ef, irl, kel);
+    apply_floor_ir_t<float>(WR, rf, ef, irr, ker);
     // face velocity (Sec. 4)
     const float4 wi = x.wv[i], wj = x.wv[j];
     const float mx = fx - 0.5f * qx, my = fy - 0.5f * qy, mz = fz - 0.5f * qz;
@@ -265,14 +265,14 @@ __global__ void __launch_bounds__(128) k_face_flux32(MeshDev m, HydroCfg c, Mixe
         const float ir = irl;
         L.rho = WL[0];
         L.irho = ir;
-        L.P = gm1 * (WL[4] - 0.5f * (WL[1] * WL[1] + WL[2] * WL[2] + WL[3] * WL[3]) * ir);
+        L.P = gm1 * (WL[4] - kel);
         L.vx = WL[1] * ir - wfx; L.vy = WL[2] * ir - wfy; L.vz = WL[3] * ir - wfz;
     }
     {
         const float ir = irr;
         R.rho = WR[0];
         R.irho = ir;
-        R.P = gm1 * (WR[4] - 0.5f * (WR[1] * WR[1] + WR[2] * WR[2] + WR[3] * WR[3]) * ir);
+        R.P = gm1 * (WR[4] - ker);
         R.vx = WR[1] * ir - wfx; R.vy = WR[2] * ir - wfy; R.vz = WR[3] * ir - wfz;
     }
     float F[5];

@@ -73,9 +73,14 @@ __device__ __forceinline__ void hllc_t(const FaceStateT<T> &L, const FaceStateT<
     F[4] = (Ek + K.P) * uk;
     if (star) {
         // U*_K = rho_K (S_K - u_K)/(S_K - S*) (1, v_K + (S* - u_K) n, E_K/rho_K + (S* - u_K)(S* + P_K/(rho_K (S_K - u_K))))
-        const T f = K.rho * (sk - uk) / (sk - ss);
+        // With f = rho_K (S_K - u_K) / (S_K - S*), the energy term
+        // f (S* - u_K) P_K / (rho_K (S_K - u_K)) equals (S* - u_K) P_K / (S_K - S*):
+        // written that way the star state needs one division, and stays finite
+        // where S_K rounds to u_K (a sound speed below the flow speed's ulp).
+        const T rb = T(1) / (sk - ss);
+        const T f = K.rho * (sk - uk) * rb;
         const T du = ss - uk;
-        const T es = f * (Ek * K.irho + du * (ss + K.P * K.irho / (sk - uk)));
+        const T es = f * (Ek * K.irho + du * ss) + du * K.P * rb;
         F[0] += sk * (f - K.rho);
         F[1] += sk * (f * (K.vx + du * nx) - K.rho * K.vx);
         F[2] += sk * (f * (K.vy + du * ny) - K.rho * K.vy);
@@ -172,20 +177,21 @@ __device__ __forceinline__ void riemann_t(int kind, const FaceStateT<T> &L, cons
     else hllc_t<T>(L, R, nx, ny, nz, gamma, igm1, F);
 }
 
-// The same floors for a face state, also returning 1 / rho of the result
-// (the kinetic energy is formed with it instead of a second division).
+// The same floors for a face state, also returning 1 / rho and the kinetic
+// energy density of the result (for the pressure, without a second division).
 template <class T>
-__device__ __forceinline__ void apply_floor_ir_t(T W[5], T rho_floor, T eps_floor, T &ir)
+__device__ __forceinline__ void apply_floor_ir_t(T W[5], T rho_floor, T eps_floor, T &ir, T &ke)
 {
     if (!(W[0] >= rho_floor)) {
         W[0] = rho_floor;
         W[1] = W[2] = W[3] = T(0);
         W[4] = rho_floor * eps_floor;
         ir = T(1) / rho_floor;
+        ke = T(0);
         return;
     }
     ir = T(1) / W[0];
-    const T ke = T(0.5) * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]) * ir;
+    ke = T(0.5) * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]) * ir;
     if (!(W[4] - ke >= W[0] * eps_floor)) W[4] = W[0] * eps_floor + ke;
 }
 
