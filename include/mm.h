@@ -38,6 +38,12 @@ extern "C" {
 #endif
 
 #define MM_MAX_CELLS 100000000LL /* index arithmetic is 32-bit per face/incidence */
+/* Box sizes accepted by the tessellation (every axis, every box): the
+ * clipper forms its bounds and limits in FP32 with explicit margins, which
+ * hold while squared lengths of a few box sizes stay normal FP32 numbers.
+ * Scale coordinates into this range (2^-40 .. 2^40). */
+#define MM_MIN_BOX 9.094947017729282e-13
+#define MM_MAX_BOX 1099511627776.0
 
 typedef enum {
     MM_OK = 0,
@@ -134,7 +140,9 @@ mm_status mm_set_config(mm_ctx *ctx, const mm_config *cfg);
  * bisectors with the generator's own images) and is clipped by the
  * bisector planes of neighbouring generators and images in increasing
  * distance, until every remaining generator is more than twice as far as
- * the farthest vertex.  pos[3][n] device.  Waits for completion. */
+ * the farthest vertex.  pos[3][n] device.  Box sizes outside
+ * [MM_MIN_BOX, MM_MAX_BOX] are MM_EINVAL (here, in mm_step, mm_step_batched
+ * and mm_autotune).  Waits for completion. */
 mm_status mm_tessellate(mm_ctx *ctx, const double *pos, int64_t n, const double box[3], mm_mesh *out);
 
 /* Limited cell-centred gradient of per-volume states W[5][n] (Sec. 4.1):

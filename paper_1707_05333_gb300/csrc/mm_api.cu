@@ -303,7 +303,8 @@ static mm_status setup_boxes(mm_ctx *c, int64_t n, const int64_t *box_off, const
         if (nb < 1) return fail(c, MM_EINVAL, "box %d holds no generator", b);
         const double *L = boxL + 3 * b;
         for (int d = 0; d < 3; ++d)
-            if (!(L[d] > 0.0) || !std::isfinite(L[d])) return fail(c, MM_EINVAL, "box %d size must be finite and > 0", b);
+            if (!(L[d] >= MM_MIN_BOX && L[d] <= MM_MAX_BOX))
+                return fail(c, MM_EINVAL, "box %d size %g outside [%g, %g]", b, L[d], MM_MIN_BOX, MM_MAX_BOX);
         BoxDev &g = c->boxes_host[b];
         const double vcell = L[0] * L[1] * L[2] / (double)nb;
         const double spacing = std::cbrt(vcell) * c->cfg.bin_scale;

@@ -225,7 +225,12 @@ __device__ __forceinline__ void vertex32(const ClipSmem<1> &S, int a, int b, int
     const float vn = fabsf(x) + fabsf(y) + fabsf(z);
     const float u = 5.9604645e-8f;
     err = 3.0f * u * H * (5.5f * (la + lb + lc) + 13.0f * vn);
-    if (!(u * H < 1e-3f) || !(err < 1e30f)) err = __int_as_float(0x7f800000);  // +inf
+    // The analysis assumes no FP32 underflow or overflow: the numerators grow
+    // like |q|^4 and the determinant like |q|^3, so planes much nearer than
+    // 2^-28 or farther than 2^28 (tiny or huge boxes) are solved exactly.
+    const float qlo = fminf(la, fminf(lb, lc)), qhi = fmaxf(la, fmaxf(lb, lc));
+    if (!(u * H < 1e-3f) || !(err < 1e30f) || !(qlo >= 3.7252903e-9f) || !(qhi <= 268435456.0f))
+        err = __int_as_float(0x7f800000);  // +inf
 }
 
 // The rare exact paths of the filtered clipper, kept out of line so that the

@@ -188,6 +188,10 @@ def test_rejects_bad_sizes_and_boxes(ctx):
         assert c.L.mm_tessellate(c.h, p, n, box, ctypes.byref(binding.MeshStruct())) == 1
     bad = (ctypes.c_double * 3)(1.0, 0.0, 1.0)
     assert c.L.mm_tessellate(c.h, p, 64, bad, ctypes.byref(binding.MeshStruct())) == 1
+    # box sizes outside [MM_MIN_BOX, MM_MAX_BOX] = [2^-40, 2^40] (the clipper's FP32 bounds)
+    for L in (2.0 ** -41, 2.0 ** 41, float("inf"), float("nan")):
+        big = (ctypes.c_double * 3)(1.0, L, 1.0)
+        assert c.L.mm_tessellate(c.h, p, 64, big, ctypes.byref(binding.MeshStruct())) == 1
     # a batch whose second box is empty
     off = (ctypes.c_int64 * 3)(0, 64, 64)
     boxes = (ctypes.c_double * 6)(1.0, 1.0, 1.0, 1.0, 1.0, 1.0)
@@ -200,3 +204,24 @@ def test_rejects_bad_sizes_and_boxes(ctx):
         b.close()
     _, _, G = H.gpu_tessellate(c, torch, WL.random_points(64, seed=12), np.ones(3))
     assert abs(G["cell_volume"].sum() - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("k", [-36, -12, 12, 36])
+def test_power_of_two_scaled_box_gives_the_scaled_mesh(ctx, k):
+    """Positions and box scaled by 2^k (within [2^-40, 2^40]): every FP64 and
+    FP32 operation of the tessellation scales exactly, so the mesh is the unit
+    box's with areas times 4^k, volumes times 8^k and centroids times 2^k.
+    Pins the scale handling of the FP32 bounds (bins, coverage radius,
+    security limit)."""
+    c, torch = ctx
+    pos = WL.random_points(700, box=(1.0, 0.5, 2.0), seed=21)
+    box = np.array([1.0, 0.5, 2.0])
+    _, _, A = H.gpu_tessellate(c, torch, pos, box)
+    s = 2.0 ** k
+    _, _, B = H.gpu_tessellate(c, torch, pos * s, box * s)
+    for key in ("face_i", "face_j", "face_shift", "inc_off", "inc_face"):
+        np.testing.assert_array_equal(A[key], B[key], err_msg=key)
+    np.testing.assert_allclose(B["cell_volume"], A["cell_volume"] * s ** 3, rtol=1e-14, atol=0)
+    np.testing.assert_allclose(B["face_area"], A["face_area"] * s ** 2, rtol=1e-14, atol=0)
+    np.testing.assert_allclose(B["cell_centroid"], A["cell_centroid"] * s, rtol=1e-14, atol=0)
+    np.testing.assert_allclose(B["face_normal"], A["face_normal"], rtol=1e-14, atol=1e-15)
