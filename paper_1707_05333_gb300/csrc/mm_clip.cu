@@ -95,8 +95,16 @@ struct ClipSmem : VertStore<PREC> {
     float pfn[PREC ? PMAX : 1];  // FP32 |q| = sqrt(2 o) of each plane (for the vertex error bound)
 };
 
-// floor(a / b) for b > 0 in integer arithmetic
-__device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+// Rarely taken integer work of the gather, kept out of line so that the hot
+// loop around it stays small (the kernel is sensitive to instruction-cache
+// misses): floor(a / b) for b > 0 (images beyond the neighbouring boxes), and
+// the bin offsets of entry t of ring block rh of side nb = 2 rh + 1 (rings 3
+// and beyond).
+__device__ __noinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+__device__ __noinline__ int3 ring_offset(int t, int nb, int rh)
+{
+    return make_int3(t % nb - rh, (t / nb) % nb - rh, t / (nb * nb) - rh);
+}
 
 __device__ __forceinline__ unsigned lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
 
@@ -779,7 +787,7 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
                     int ox, oy, oz;
                     if (rh == 1) { ox = t % 3 - 1; oy = (t / 3) % 3 - 1; oz = t / 9 - 1; }
                     else if (rh == 2) { ox = t % 5 - 2; oy = (t / 5) % 5 - 2; oz = t / 25 - 2; }
-                    else { ox = t % nb - rh; oy = (t / nb) % nb - rh; oz = t / (nb * nb) - rh; }
+                    else { const int3 o = ring_offset(t, nb, rh); ox = o.x; oy = o.y; oz = o.z; }
                     const int ch = max(abs(ox), max(abs(oy), abs(oz)));
                     if (ch >= rl) {
                         int bx = cb[0] + ox, by = cb[1] + oy, bz = cb[2] + oz;
