@@ -11,6 +11,8 @@
 
 namespace mm {
 
+static_assert(MAXF % 4 == 0, "slot rows are read as int4");
+
 // Per cell: find the partner slot of each face in the neighbour's list,
 // then mark which faces are confirmed and which this cell stores.
 __global__ void k_face_confirm(int64_t n, Slots sl, unsigned long long *__restrict__ emit_mask,
@@ -28,9 +30,16 @@ __global__ void k_face_confirm(int64_t n, Slots sl, unsigned long long *__restri
         const int want = 26 - code;  // the mirrored image seen from j
         const int cj = sl.cnt[j];
         int m = -1;
-        for (int t = 0; t < cj; ++t) {
-            const int64_t u = (int64_t)j * MAXF + t;
-            if (sl.nb[u] == (int)i && sl.sh[u] == want) { m = t; break; }
+        // the neighbour's slots four at a time (rows of MAXF ints are 16-byte aligned)
+        const int4 *row = reinterpret_cast<const int4 *>(sl.nb + (int64_t)j * MAXF);
+        for (int t0 = 0; t0 < cj && m < 0; t0 += 4) {
+            const int4 q = row[t0 >> 2];
+            const int c4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int t = t0 + a;
+                if (m < 0 && t < cj && c4[a] == (int)i && sl.sh[(int64_t)j * MAXF + t] == want) m = t;
+            }
         }
         partner[s] = (signed char)m;
         if (m >= 0) {
@@ -73,13 +82,15 @@ __global__ void k_face_write(int64_t n, const double *__restrict__ pos, const Bo
         return;
     }
     const unsigned long long em = emit_mask[i], cm = conf_mask[i];
-    const int fbase = face_off[i];
-    int e = inc_off[i];
+    const int fbase = face_off[i], e0 = inc_off[i];
     const int64_t ns = n * (int64_t)MAXF;
-    unsigned long long rest = cm;
-    while (rest) {
-        const int k = __ffsll((long long)rest) - 1;
-        rest &= rest - 1;
+    // slots are independent (each knows its place in the face and incidence
+    // lists from the masks), so the loop unrolls and their loads overlap
+    const int kend = 64 - __clzll((long long)cm);
+#pragma unroll 4
+    for (int k = 0; k < kend; ++k) {
+        if (!((cm >> k) & 1ull)) continue;
+        const int e = e0 + __popcll(cm & ((1ull << k) - 1ull));
         const int64_t s = i * MAXF + k;
         const int j = sl.nb[s];
         const int code = sl.sh[s];
@@ -106,12 +117,12 @@ __global__ void k_face_write(int64_t n, const double *__restrict__ pos, const Bo
                 face_cen[fcap + f] = piy + sl.fc[ns + s];
                 face_cen[2 * fcap + f] = piz + sl.fc[2 * ns + s];
             }
-            inc_face[e++] = f;
+            inc_face[e] = f;
         } else {
             const int m = partner[s];
             const unsigned long long ej = emit_mask[j];
             const int f = face_off[j] + __popcll(ej & ((1ull << m) - 1ull));
-            inc_face[e++] = ~f;
+            inc_face[e] = ~f;
         }
     }
 }
