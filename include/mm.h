@@ -72,7 +72,7 @@ typedef struct {
                       /*    FP64 update); the mesh is FP64-exact either way (clip_filter)   */
     int collect_stats;/* 1: the clipper records the counters read by mm_tess_stats          */
     int riemann;      /* 0 HLLC (the paper's default), 1 HLL (Sec. 4)                        */
-    int clip_warps;   /* cells (warps) per block of the clipping kernel, 1..8 (tunable)      */
+    int clip_warps;   /* cells (warps) per block of the clipping kernel, 1..8 (tunable; 2)   */
     int cand_cap;     /* candidates per sorted batch of the clipper, 32..64 (tunable)        */
     int clip_filter;  /* 1: clip with FP32 vertices, an error-bounded FP32 plane test and    */
                       /*    an exact FP64 test near ties, then FP64 vertices (same mesh, bit */

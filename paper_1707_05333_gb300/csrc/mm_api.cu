@@ -637,7 +637,7 @@ void mm_default_config(mm_config *g)
     g->regularize = 0;
     g->precision = 0;
     g->riemann = 0;
-    g->clip_warps = 4;
+    g->clip_warps = 2;  // fastest measured on the 256^3 shear layer (2: 367, 4: 378, 8: 414 ms)
     g->cand_cap = 64;
     g->clip_filter = 1;
     g->bin_scale = 1.0;

@@ -579,7 +579,8 @@ __global__ void __launch_bounds__(256) k_mesh_velocity(MeshDev m, HydroCfg c, co
         const double V = m.vol[i];
         double W[5];
         load5(U, n, i, 1.0 / V, W);
-        const double vx = U[n + i] / U[i], vy = U[2 * n + i] / U[i], vz = U[3 * n + i] / U[i];
+        const double irm = 1.0 / U[i];  // one division for the three velocity components
+        const double vx = U[n + i] * irm, vy = U[2 * n + i] * irm, vz = U[3 * n + i] * irm;
         double wx = c.eta * vx, wy = c.eta * vy, wz = c.eta * vz;
         const double cs = sound_speed(W, c.gamma);
         const double R = cbrt(3.0 * V / (4.0 * 3.14159265358979323846));

@@ -155,7 +155,7 @@ def test_tunable_settings_keep_the_mesh(oracle, ctx, warps, cap, scale):
     try:
         _, _, G = H.gpu_tessellate(c, torch, pos, np.ones(3))
     finally:
-        c.set_config(clip_warps=4, cand_cap=64, bin_scale=1.0)
+        c.set_config(clip_warps=2, cand_cap=64, bin_scale=1.0)
     H.compare_tessellations(oracle, T, G, pos, np.ones(3))
     H.check_incidence(G)
 
@@ -171,7 +171,7 @@ def test_autotune_picks_a_valid_setting(ctx):
         mesh = c.mm_tessellate(P, w.box)
         assert mesh.nfaces > 0
     finally:
-        c.set_config(clip_warps=4, cand_cap=64, bin_scale=1.0)
+        c.set_config(clip_warps=2, cand_cap=64, bin_scale=1.0)
 
 
 def test_rejects_bad_sizes_and_boxes(ctx):
