@@ -153,6 +153,29 @@ def clip_roofline(direct, filtered, ms, n, clip_filter):
             "launch_ms": ms}
 
 
+def clip_traffic(n, clip_filter):
+    """DRAM bytes (read + write) of one k_clip launch on this workload, from the
+    committed ncu capture (profiles/k_clip_dram_shear_layer_256.md: one
+    launch, dram__bytes_read.sum + dram__bytes_write.sum).  None when the
+    capture is absent or covers another cell count or clipper."""
+    path = os.path.join(ROOT, "profiles", "k_clip_dram_shear_layer_256.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip()
+    try:
+        if int(vals["cells"]) != n or int(vals["clip_filter"]) != clip_filter:
+            return None
+        return int(vals["dram bytes per launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -499,6 +522,7 @@ def run_ours(args, world, rank, local):
     roofline = None
     if dom == "clip":
         roofline = clip_roofline(tdirect, tstats, dom_ms, n, args.clip_filter)
+        roofline["traffic"] = clip_traffic(n, args.clip_filter)
     else:
         byts = algorithmic_bytes(dom, n, nf)
         if byts is not None:
