@@ -43,3 +43,13 @@ def test_single_rank_aggregation():
     import bench
     value, ms = bench.aggregate(50.0, cells_per_rank=10, steps=2, world=1)
     assert ms == 50.0 and value == pytest.approx(400.0)
+
+
+def test_clip_traffic_comes_from_the_matching_capture():
+    """roofline.traffic is the committed full-size capture's DRAM bytes, and
+    null for any other cell count or clipper."""
+    import bench
+    t = bench.clip_traffic(256 ** 3, 1)
+    assert t is not None and t > 256 ** 3 * 64  # at least the binned generators and the cell records
+    assert bench.clip_traffic(64 ** 3, 1) is None
+    assert bench.clip_traffic(256 ** 3, 0) is None
