@@ -124,7 +124,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # offsets, a 2-D cross product, three weighted sums -> 12 flops).
 FLOPS_PLANE_TEST, FLOPS_SOLVE, FLOPS_FAN = 5, 51, 12
 # FP32 lanes: 128 per SM per clock, so one FP32 flop costs 1/64 of an FP64
-# flop of issue time on this part.
+# flop of issue time on GB300.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 

@@ -593,8 +593,9 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
     update_limit<PREC>(C, mr);
 }
 
-// What a flush needs to form the exact candidate planes: the binned
-// generators, this generator and the box.
+// What a flush needs besides the warp's shared memory to form the exact
+// candidate planes: the binned generators (the image offsets s L - p of this
+// generator are in shared memory).
 struct Gather {
     const double4_32a *sorted;
 };
@@ -678,7 +679,8 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
     const int self = (int)__double_as_longlong(sorted[w].w);
     const double amin = g.amin;
     // The setup runs in FP32 and integer arithmetic wherever a bound, not an
-    // exact value, is needed: on this part FP64 is the scarce unit.
+    // exact value, is needed: on GB300 an FP64 instruction costs the issue
+    // time of dozens of FP32 ones.
 
     // starting box: planes 0..5 = +x,-x,+y,-y,+z,-z self-image bisectors
     if (lane < 6) {
