@@ -185,6 +185,8 @@ static HydroCfg hydro_cfg(const mm_config &g)
     h.entropy = g.entropy;
     h.mach_th = g.mach_th;
     h.igm1 = 1.0 / (g.gamma - 1.0);
+    h.kmach = (g.gamma + 1.0) / (2.0 * g.gamma);
+    h.rhoa_floor = g.rho_floor * (g.gamma - 1.0) * g.rho_floor * g.eps_floor / std::pow(g.rho_floor, g.gamma);
     return h;
 }
 

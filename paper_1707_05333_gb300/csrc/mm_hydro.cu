@@ -348,10 +348,8 @@ __global__ void __launch_bounds__(128) k_face_flux(MeshDev m, HydroCfg c, const 
     if constexpr (NG == 6) {
         // rho A at the face: a state reset to the density floor takes the
         // floor state's own A; otherwise the reconstruction, not below 0
-        const double rf = c.rho_floor;
-        const double a_floor = rf * (c.gamma - 1.0) * rf * c.eps_floor / pow(rf, c.gamma);
-        WL[5] = vac_l ? a_floor : fmax(WL[5], 0.0);
-        WR[5] = vac_r ? a_floor : fmax(WR[5], 0.0);
+        WL[5] = vac_l ? c.rhoa_floor : fmax(WL[5], 0.0);
+        WR[5] = vac_r ? c.rhoa_floor : fmax(WR[5], 0.0);
     }
     // face velocity (Sec. 4): mean generator velocity plus the correction for
     // the face centroid lying off the generators' midpoint
@@ -384,7 +382,8 @@ __global__ void __launch_bounds__(128) k_face_flux(MeshDev m, HydroCfg c, const 
         R.vx = WR[1] * ir - wfx; R.vy = WR[2] * ir - wfy; R.vz = WR[3] * ir - wfz;
     }
     double F[5];
-    riemann_t<double>(c.riemann, L, R, nx, ny, nz, c.gamma, c.igm1, F);
+    WavesT<double> wv;
+    riemann_t<double>(c.riemann, L, R, nx, ny, nz, c.gamma, c.igm1, F, NG == 6 ? &wv : nullptr);
     // back to the lab frame: p -> p + m w, E -> E + p.w + |w|^2/2 m
     const double A = m.area[f];
     const double fm = F[0];
@@ -396,7 +395,7 @@ __global__ void __launch_bounds__(128) k_face_flux(MeshDev m, HydroCfg c, const 
     flux[4 * fs + f] = A * fe;
     if constexpr (NG == 6) {
         double mach;
-        const double f5 = passive_flux_t<double>(c.riemann, L, R, nx, ny, nz, c.gamma, WL[5], WR[5], fm, mach);
+        const double f5 = passive_flux_t<double>(c.riemann, L, R, wv, c.kmach, WL[5], WR[5], fm, mach);
         flux[5 * fs + f] = A * f5;
         flux[6 * fs + f] = mach;
         flux[7 * fs + f] = A * (wfx * nx + wfy * ny + wfz * nz);

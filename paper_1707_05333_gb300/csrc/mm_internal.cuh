@@ -110,6 +110,8 @@ struct HydroCfg {
     double gamma, cfl, eta, chi, zeta, theta, rho_floor, eps_floor;
     double mach_th;  // energy/entropy switch threshold (Sec. 4.3)
     double igm1;     // 1 / (gamma - 1), formed once on the host
+    double kmach;    // (gamma + 1) / (2 gamma), the shock Mach relation's factor
+    double rhoa_floor;  // rho A of the floor state: rho_f (gamma-1) rho_f eps_f / rho_f^gamma
     int limiter, regularize, riemann;
     int entropy;     // 1: a sixth state column rho A and the switch
 };

@@ -4,6 +4,14 @@
 
 namespace mm {
 
+// Wave speeds of a face's Riemann problem along the unit normal, for the
+// entropy column's flux and shock Mach number (Sec. 4.3): Davis S_L, S_R, the
+// contact speed S* and the normal velocities u_L, u_R.
+template <class T>
+struct WavesT {
+    T sl, sr, ss, ul, ur;
+};
+
 template <class T>
 struct FaceStateT {
     T rho, vx, vy, vz, P;  // velocity already in the face frame
@@ -47,7 +55,7 @@ __device__ __forceinline__ bool pos_t(float x) { return x > 0.0f; }
 // S_R > 0 -> F*_R; else F_R.
 template <class T>
 __device__ __forceinline__ void hllc_t(const FaceStateT<T> &L, const FaceStateT<T> &R, T nx, T ny, T nz, T gamma,
-                                       T igm1, T F[5])
+                                       T igm1, T F[5], WavesT<T> *wv = nullptr)
 {
     const T ul = L.vx * nx + L.vy * ny + L.vz * nz;
     const T ur = R.vx * nx + R.vy * ny + R.vz * nz;
@@ -58,6 +66,7 @@ __device__ __forceinline__ void hllc_t(const FaceStateT<T> &L, const FaceStateT<
     const T sr = max_t(ul + cl, ur + cr);
     const T ml = L.rho * (sl - ul), mr = R.rho * (sr - ur);
     const T ss = (R.P - L.P + ul * ml - ur * mr) / (ml - mr);
+    if (wv) *wv = WavesT<T>{sl, sr, ss, ul, ur};
     const bool left = nonneg_t(sl) || nonneg_t(ss);
     const bool star = !nonneg_t(sl) && (left || pos_t(sr));
     const FaceStateT<T> &K = left ? L : R;
@@ -93,7 +102,7 @@ __device__ __forceinline__ void hllc_t(const FaceStateT<T> &L, const FaceStateT<
 // form of the conservation laws (no contact wave).
 template <class T>
 __device__ __forceinline__ void hll_t(const FaceStateT<T> &L, const FaceStateT<T> &R, T nx, T ny, T nz, T gamma,
-                                      T igm1, T F[5])
+                                      T igm1, T F[5], WavesT<T> *wv = nullptr)
 {
     const T ul = L.vx * nx + L.vy * ny + L.vz * nz;
     const T ur = R.vx * nx + R.vy * ny + R.vz * nz;
@@ -102,6 +111,12 @@ __device__ __forceinline__ void hll_t(const FaceStateT<T> &L, const FaceStateT<T
     const T Er = R.P * igm1 + T(0.5) * R.rho * (R.vx * R.vx + R.vy * R.vy + R.vz * R.vz);
     const T sl = min_t(ul - cl, ur - cr);
     const T sr = max_t(ul + cl, ur + cr);
+    if (wv) {
+        // the contact speed of the same wave model, for the shock Mach number
+        const T ss = (R.P - L.P + L.rho * ul * (sl - ul) - R.rho * ur * (sr - ur)) /
+                     (L.rho * (sl - ul) - R.rho * (sr - ur));
+        *wv = WavesT<T>{sl, sr, ss, ul, ur};
+    }
     const T ml = L.rho * ul, mr = R.rho * ur;
     const T Fl[5] = {ml, ml * L.vx + L.P * nx, ml * L.vy + L.P * ny, ml * L.vz + L.P * nz, (El + L.P) * ul};
     const T Fr[5] = {mr, mr * R.vx + R.P * nx, mr * R.vy + R.P * ny, mr * R.vz + R.P * nz, (Er + R.P) * ur};
@@ -119,29 +134,13 @@ __device__ __forceinline__ void hll_t(const FaceStateT<T> &L, const FaceStateT<T
     for (int k = 0; k < 5; ++k) F[k] = (sr * Fl[k] - sl * Fr[k] + sl * sr * (Ur[k] - Ul[k])) * id;
 }
 
-// Wave speeds of the HLLC model along the unit normal: Davis S_L, S_R, the
-// contact speed S* and the star pressure P* (from the left wave's jump
-// condition), with the normal velocities u_L, u_R.
-template <class T>
-__device__ __forceinline__ void star_state_t(const FaceStateT<T> &L, const FaceStateT<T> &R, T nx, T ny, T nz,
-                                             T gamma, T &sl, T &ss, T &sr, T &ps, T &ul, T &ur)
-{
-    ul = L.vx * nx + L.vy * ny + L.vz * nz;
-    ur = R.vx * nx + R.vy * ny + R.vz * nz;
-    const T cl = sqrt_t(gamma * L.P * L.irho), cr = sqrt_t(gamma * R.P * R.irho);
-    sl = min_t(ul - cl, ur - cr);
-    sr = max_t(ul + cl, ur + cr);
-    ss = (R.P - L.P + L.rho * ul * (sl - ul) - R.rho * ur * (sr - ur)) / (L.rho * (sl - ul) - R.rho * (sr - ur));
-    ps = L.P + L.rho * (sl - ul) * (ss - ul);
-}
-
 // Mach number of the shock that raises the pressure of either side to the
-// star pressure (Rankine-Hugoniot: M^2 = 1 + (gamma+1)/(2 gamma) (P*/P - 1)),
-// the larger of the two, 0 where neither side is compressed (Sec. 4.3).
+// star pressure (Rankine-Hugoniot: M^2 = 1 + k (P*/P - 1) with
+// k = (gamma+1)/(2 gamma)), the larger of the two, 0 where neither side is
+// compressed (Sec. 4.3).
 template <class T>
-__device__ __forceinline__ T shock_mach_t(T pl, T pr, T ps, T gamma)
+__device__ __forceinline__ T shock_mach_t(T pl, T pr, T ps, T k)
 {
-    const T k = (gamma + T(1)) / (T(2) * gamma);
     T m = T(0);
     if (ps > pl) m = max_t(m, sqrt_t(T(1) + k * (ps / pl - T(1))));
     if (ps > pr) m = max_t(m, sqrt_t(T(1) + k * (ps / pr - T(1))));
@@ -151,13 +150,16 @@ __device__ __forceinline__ T shock_mach_t(T pl, T pr, T ps, T gamma)
 // Flux of a passive charge rho a (the entropy column, Sec. 4.3) carried by
 // the Riemann solution: HLLC takes a from the side of the contact times the
 // mass flux fm; HLL averages rho a like any conserved column.
+// The wave speeds are the solver's own (riemann_t with wv); the star pressure
+// P* = P_L + rho_L (S_L - u_L)(S* - u_L) comes from the left wave's jump
+// condition; kmach = (gamma+1)/(2 gamma).
 template <class T>
-__device__ __forceinline__ T passive_flux_t(int kind, const FaceStateT<T> &L, const FaceStateT<T> &R, T nx, T ny,
-                                            T nz, T gamma, T rhoa_l, T rhoa_r, T fm, T &mach)
+__device__ __forceinline__ T passive_flux_t(int kind, const FaceStateT<T> &L, const FaceStateT<T> &R,
+                                            const WavesT<T> &wv, T kmach, T rhoa_l, T rhoa_r, T fm, T &mach)
 {
-    T sl, ss, sr, ps, ul, ur;
-    star_state_t<T>(L, R, nx, ny, nz, gamma, sl, ss, sr, ps, ul, ur);
-    mach = shock_mach_t<T>(L.P, R.P, ps, gamma);
+    const T sl = wv.sl, ss = wv.ss, sr = wv.sr, ul = wv.ul, ur = wv.ur;
+    const T ps = L.P + L.rho * (sl - ul) * (ss - ul);
+    mach = shock_mach_t<T>(L.P, R.P, ps, kmach);
     const T al = rhoa_l * L.irho, ar = rhoa_r * R.irho;
     if (kind == 1) {
         const T fl = L.rho * ul * al, fr = R.rho * ur * ar;
@@ -171,10 +173,10 @@ __device__ __forceinline__ T passive_flux_t(int kind, const FaceStateT<T> &L, co
 // The configured solver: 0 HLLC, 1 HLL.
 template <class T>
 __device__ __forceinline__ void riemann_t(int kind, const FaceStateT<T> &L, const FaceStateT<T> &R, T nx, T ny, T nz,
-                                          T gamma, T igm1, T F[5])
+                                          T gamma, T igm1, T F[5], WavesT<T> *wv = nullptr)
 {
-    if (kind == 1) hll_t<T>(L, R, nx, ny, nz, gamma, igm1, F);
-    else hllc_t<T>(L, R, nx, ny, nz, gamma, igm1, F);
+    if (kind == 1) hll_t<T>(L, R, nx, ny, nz, gamma, igm1, F, wv);
+    else hllc_t<T>(L, R, nx, ny, nz, gamma, igm1, F, wv);
 }
 
 // The same floors for a face state, also returning 1 / rho and the kinetic
