@@ -492,7 +492,7 @@ static mm_status ensure_hydro(mm_ctx *c, int64_t n, int64_t fs)
         // flux, each face's shock Mach number and its swept-volume rate)
         const int64_t ng = c->cfg.entropy ? 6 : 5, nfr = c->cfg.entropy ? 8 : 5;
         if ((r = ensure(c, c->Wh, ng * n * sizeof(double))) || (r = ensure(c, c->grad, 3 * ng * n * sizeof(double))) ||
-            (r = ensure(c, c->flux, nfr * F * sizeof(double))) || (r = ensure(c, c->fgeo, 6 * F * sizeof(double))) ||
+            (r = ensure(c, c->flux, nfr * F * sizeof(double))) || (r = ensure(c, c->fgeo, 8 * F * sizeof(double))) ||
             (r = ensure(c, c->minv, 9 * n * sizeof(double))))
             return r;
     }
@@ -736,7 +736,7 @@ mm_status mm_gradients(mm_ctx *c, const mm_mesh *mesh, const double *W, double *
     if ((r = check_mesh(c, mesh))) return r;
     if (!W || !grad) return fail(c, MM_EINVAL, "null pointer argument");
     MeshDev m = mesh_from(mesh);
-    if ((r = ensure(c, c->fgeo, 6 * (m.fs > 0 ? m.fs : 1) * sizeof(double)))) return r;
+    if ((r = ensure(c, c->fgeo, 8 * (m.fs > 0 ? m.fs : 1) * sizeof(double)))) return r;
     launch_face_geom(m, P<double>(c->fgeo), c->stream);
     launch_gradient(m, hydro_cfg(c->cfg), W, P<double>(c->fgeo), nullptr, false, grad, nullptr, nullptr, c->stream);
     CKLAUNCH();

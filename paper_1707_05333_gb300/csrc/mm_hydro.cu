@@ -83,9 +83,17 @@ __global__ void __launch_bounds__(256) k_face_geom(MeshDev m, double *__restrict
     geo[f] = A * m.normal[f];
     geo[fs + f] = A * m.normal[fs + f];
     geo[2 * fs + f] = A * m.normal[2 * fs + f];
-    geo[3 * fs + f] = m.cen[j] + image_axis(code % 3, L[0]) - m.cen[i];
-    geo[4 * fs + f] = m.cen[n + j] + image_axis((code / 3) % 3, L[1]) - m.cen[n + i];
-    geo[5 * fs + f] = m.cen[2 * n + j] + image_axis(code / 9, L[2]) - m.cen[2 * n + i];
+    const double dx = m.cen[j] + image_axis(code % 3, L[0]) - m.cen[i];
+    const double dy = m.cen[n + j] + image_axis((code / 3) % 3, L[1]) - m.cen[n + i];
+    const double dz = m.cen[2 * n + j] + image_axis(code / 9, L[2]) - m.cen[2 * n + i];
+    geo[3 * fs + f] = dx;
+    geo[4 * fs + f] = dy;
+    geo[5 * fs + f] = dz;
+    // FP32 roundings of d after the six FP64 rows, for the limiter's screening
+    float *g32 = reinterpret_cast<float *>(geo + 6 * fs);
+    g32[f] = (float)dx;
+    g32[fs + f] = (float)dy;
+    g32[2 * fs + f] = (float)dz;
 }
 
 void launch_face_geom(const MeshDev &m, double *geo, cudaStream_t s)
@@ -98,6 +106,12 @@ void launch_face_geom(const MeshDev &m, double *geo, cudaStream_t s)
 // The running minima and maxima of the limiter are kept as order-preserving
 // integers (okey): integer comparisons in place of FP64 min/max.
 __device__ __forceinline__ long long kmax(long long a, long long b) { return a > b ? a : b; }
+// Delta = g . d with explicitly rounded operations, so the screened and the
+// exhaustive limiter paths form the same bits
+__device__ __forceinline__ double deldot(double g0, double g1, double g2, double dx, double dy, double dz)
+{
+    return __fma_rn(g2, dz, __fma_rn(g1, dy, __dmul_rn(g0, dx)));
+}
 __device__ __forceinline__ long long kmin(long long a, long long b) { return a < b ? a : b; }
 
 // ---------------------------------------------------------------------------
@@ -192,8 +206,67 @@ __global__ void __launch_bounds__(128, MM_GRAD_MINBLOCKS) k_gradient(MeshDev m, 
         double rn[NG], rd[NG];
 #pragma unroll
         for (int k = 0; k < NG; ++k) { kdx[k] = 0; kdn[k] = 0; rn[k] = 1.0; rd[k] = 1.0; }
+        bool exhaustive = c.limiter != 1;
+        if (c.limiter == 1) {
+            // S10 with centroid separations: Delta in FP32 from FP32 copies of
+            // g and d, whose error is below B = 8e-7 |g|_1 max_j |d_j|_1 (five
+            // roundings of 2^-24 plus margin).  Where the largest Delta leads
+            // the runner-up by more than 2B (the value 0 competing too), the
+            // FP32 leader is the exact maximum and only its Delta is formed in
+            // FP64; likewise for the minimum.  Otherwise (ties, lattices) the
+            // exhaustive FP64 pass below decides.  The result is the same bits.
+            const float *g32 = reinterpret_cast<const float *>(geo + 6 * fs);
+            float gf[3 * NG];
+#pragma unroll
+            for (int k = 0; k < 3 * NG; ++k) gf[k] = (float)g[k];
+            float m1[NG], m2[NG], n1[NG], n2[NG];
+            int i1[NG], j1[NG];
+#pragma unroll
+            for (int k = 0; k < NG; ++k) {
+                m1[k] = 0.0f; n1[k] = 0.0f; i1[k] = -1; j1[k] = -1;
+                m2[k] = -__int_as_float(0x7f800000); n2[k] = __int_as_float(0x7f800000);
+            }
+            float dl1 = 0.0f;
+            for (int e = e0; e < e1; ++e) {
+                int f = m.inc_face[e];
+                const unsigned sm = f >= 0 ? 0u : 0x80000000u;
+                if (f < 0) f = ~f;
+                const float dx = __uint_as_float(__float_as_uint(g32[f]) ^ sm);
+                const float dy = __uint_as_float(__float_as_uint(g32[fs + f]) ^ sm);
+                const float dz = __uint_as_float(__float_as_uint(g32[2 * fs + f]) ^ sm);
+                dl1 = fmaxf(dl1, fabsf(dx) + fabsf(dy) + fabsf(dz));
+#pragma unroll
+                for (int k = 0; k < NG; ++k) {
+                    const float del = fmaf(gf[3 * k], dx, fmaf(gf[3 * k + 1], dy, gf[3 * k + 2] * dz));
+                    if (del > m1[k]) { m2[k] = m1[k]; m1[k] = del; i1[k] = e; } else m2[k] = fmaxf(m2[k], del);
+                    if (del < n1[k]) { n2[k] = n1[k]; n1[k] = del; j1[k] = e; } else n2[k] = fminf(n2[k], del);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NG; ++k) {
+                const float b2 = 2.0f * (8e-7f * (fabsf(gf[3 * k]) + fabsf(gf[3 * k + 1]) + fabsf(gf[3 * k + 2])) * dl1 + 1e-36f);
+                if (!(m1[k] - m2[k] > b2) || !(n2[k] - n1[k] > b2)) exhaustive = true;
+                if (i1[k] >= 0) {
+                    int f = m.inc_face[i1[k]];
+                    const long long sm = f >= 0 ? 0LL : (long long)0x8000000000000000ULL;
+                    if (f < 0) f = ~f;
+                    kdx[k] = okey(deldot(g[3 * k], g[3 * k + 1], g[3 * k + 2], flip(geo[3 * fs + f], sm),
+                                         flip(geo[4 * fs + f], sm), flip(geo[5 * fs + f], sm)));
+                }
+                if (j1[k] >= 0) {
+                    int f = m.inc_face[j1[k]];
+                    const long long sm = f >= 0 ? 0LL : (long long)0x8000000000000000ULL;
+                    if (f < 0) f = ~f;
+                    kdn[k] = okey(deldot(g[3 * k], g[3 * k + 1], g[3 * k + 2], flip(geo[3 * fs + f], sm),
+                                         flip(geo[4 * fs + f], sm), flip(geo[5 * fs + f], sm)));
+                }
+            }
+        }
         const double cix = m.cen[i], ciy = m.cen[n + i], ciz = m.cen[2 * n + i];
         const double *L = m.boxL + 3 * m.cbox[i];
+        if (exhaustive) {
+#pragma unroll
+        for (int k = 0; k < NG; ++k) { kdx[k] = 0; kdn[k] = 0; }
         for (int e = e0; e < e1; ++e) {
             int f = m.inc_face[e];
             const bool fwd = f >= 0;
@@ -214,7 +287,7 @@ __global__ void __launch_bounds__(128, MM_GRAD_MINBLOCKS) k_gradient(MeshDev m, 
             }
 #pragma unroll
             for (int k = 0; k < NG; ++k) {
-                const double del = g[3 * k] * dx + g[3 * k + 1] * dy + g[3 * k + 2] * dz;
+                const double del = deldot(g[3 * k], g[3 * k + 1], g[3 * k + 2], dx, dy, dz);
                 const long long kd = okey(del);
                 kdx[k] = kmax(kdx[k], kd);
                 kdn[k] = kmin(kdn[k], kd);
@@ -227,6 +300,7 @@ __global__ void __launch_bounds__(128, MM_GRAD_MINBLOCKS) k_gradient(MeshDev m, 
                     if (num * rd[k] < rn[k] * den) { rn[k] = num; rd[k] = den; }
                 }
             }
+        }
         }
 #pragma unroll
         for (int k = 0; k < NG; ++k) {

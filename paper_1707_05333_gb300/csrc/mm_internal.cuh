@@ -134,7 +134,8 @@ struct Mixed {
 // device (graph mode).
 void launch_mixed_step(const MeshDev &m, const HydroCfg &c, const double *pos, const double *w, const double *dt,
                        Mixed x, double *U, cudaStream_t s, void (*mark)(void *, int, bool), void *mark_arg);
-// geo [6][fs]: A n and d per face (launch_face_geom).  With W_half the
+// geo [6][fs] doubles: A n and d per face (launch_face_geom), followed by
+// [3][fs] floats: d rounded to FP32.  With W_half the
 // half-step predictor runs and M^-1 is stored in minv [9][n]; otherwise the
 // limited gradient goes to grad, with M^-1 read from minv when minv_in.
 void launch_face_geom(const MeshDev &m, double *geo, cudaStream_t s);
