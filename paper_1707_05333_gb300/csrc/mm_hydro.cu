@@ -245,7 +245,10 @@ __global__ void __launch_bounds__(128, MM_GRAD_MINBLOCKS) k_gradient(MeshDev m, 
 #pragma unroll
             for (int k = 0; k < NG; ++k) {
                 const float b2 = 2.0f * (8e-7f * (fabsf(gf[3 * k]) + fabsf(gf[3 * k + 1]) + fabsf(gf[3 * k + 2])) * dl1 + 1e-36f);
-                if (!(m1[k] - m2[k] > b2) || !(n2[k] - n1[k] > b2)) exhaustive = true;
+                // a zero gradient (a uniform column) stays zero whatever its extremes: no tie to settle
+                const bool gzero = ((__double_as_longlong(g[3 * k]) | __double_as_longlong(g[3 * k + 1]) |
+                                     __double_as_longlong(g[3 * k + 2])) << 1) == 0;
+                if (!gzero && (!(m1[k] - m2[k] > b2) || !(n2[k] - n1[k] > b2))) exhaustive = true;
                 if (i1[k] >= 0) {
                     int f = m.inc_face[i1[k]];
                     const long long sm = f >= 0 ? 0LL : (long long)0x8000000000000000ULL;
