@@ -13,14 +13,6 @@ constexpr unsigned FULL_MASK_HYDRO = 0xffffffffu;
 #define MM_GRAD_MINBLOCKS 1  // resident blocks per SM the gradient kernel is compiled for
 #endif
 
-// Neighbour across incident entry e of a cell: other cell, outward normal
-// scale (+1/-1) and the image offset s L of the neighbour in this cell's frame.
-struct Nbr {
-    int f, o;
-    double sg;
-    double ox, oy, oz;
-};
-
 // Flip the sign of x when the mask has the sign bit set (an integer op).
 __device__ __forceinline__ double flip(double x, long long smask)
 {
@@ -31,23 +23,6 @@ __device__ __forceinline__ double flip(double x, long long smask)
 __device__ __forceinline__ double image_axis(int digit, double L)
 {
     return digit == 1 ? 0.0 : (digit == 2 ? L : -L);
-}
-
-__device__ __forceinline__ Nbr neighbour(const MeshDev &m, int e, const double *L)
-{
-    Nbr r;
-    int f = m.inc_face[e];
-    bool fwd = f >= 0;
-    if (!fwd) f = ~f;
-    r.f = f;
-    r.o = fwd ? m.face_j[f] : m.face_i[f];
-    r.sg = fwd ? 1.0 : -1.0;
-    const long long sm = fwd ? 0LL : (long long)0x8000000000000000ULL;
-    const int code = m.face_shift[f];
-    r.ox = flip(image_axis(code % 3, L[0]), sm);
-    r.oy = flip(image_axis((code / 3) % 3, L[1]), sm);
-    r.oz = flip(image_axis(code / 9, L[2]), sm);
-    return r;
 }
 
 template <int NG>
