@@ -53,6 +53,10 @@ __global__ void k_face_confirm(int64_t n, Slots sl, unsigned long long *__restri
     conf_cnt[i] = __popcll(cm);
 }
 
+// One warp per cell, one lane per face slot: the slot rows are read and the
+// face records and incidences written with consecutive lanes on consecutive
+// addresses.  Each slot knows its place in the face and incidence lists from
+// the masks, so the results do not depend on the schedule.
 __global__ void k_face_write(int64_t n, const double *__restrict__ pos, const BoxDev *__restrict__ boxes,
                              const int *__restrict__ cbox, Slots sl,
                              const unsigned long long *__restrict__ emit_mask,
@@ -64,10 +68,11 @@ __global__ void k_face_write(int64_t n, const double *__restrict__ pos, const Bo
                              int *__restrict__ inc_face, int64_t icap, const double *__restrict__ vol,
                              double *__restrict__ cen, DevStatus *st)
 {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;  // whole warps
     const double pix = pos[i], piy = pos[n + i], piz = pos[2 * n + i];
-    {
+    if (lane == 0) {
         // the cell centroid from the clipper's volume and first moment about
         // the generator
         const double ivl = 1.0 / vol[i];
@@ -78,17 +83,14 @@ __global__ void k_face_write(int64_t n, const double *__restrict__ pos, const Bo
     const double *L = boxes[cbox[i]].L;
     // a fixed capacity (graph mode) that is too small is reported, never overrun
     if ((int64_t)face_off[i + 1] > fcap || (int64_t)inc_off[i + 1] > icap) {
-        atomicOr(&st->flags, ST_ECAP_MESH);
+        if (lane == 0) atomicOr(&st->flags, ST_ECAP_MESH);
         return;
     }
     const unsigned long long em = emit_mask[i], cm = conf_mask[i];
     const int fbase = face_off[i], e0 = inc_off[i];
     const int64_t ns = n * (int64_t)MAXF;
-    // slots are independent (each knows its place in the face and incidence
-    // lists from the masks), so the loop unrolls and their loads overlap
     const int kend = 64 - __clzll((long long)cm);
-#pragma unroll 4
-    for (int k = 0; k < kend; ++k) {
+    for (int k = lane; k < kend; k += 32) {
         if (!((cm >> k) & 1ull)) continue;
         const int e = e0 + __popcll(cm & ((1ull << k) - 1ull));
         const int64_t s = i * MAXF + k;
@@ -141,7 +143,7 @@ void launch_face_write(int64_t n, const double *pos, const BoxDev *boxes, const 
                        int64_t fcap, int *inc_face, int64_t icap, const double *vol, double *cen, DevStatus *st,
                        cudaStream_t s)
 {
-    int nb = (int)((n + 127) / 128);
+    const int nb = (int)((n + 3) / 4);  // four cells (warps) per block
     k_face_write<<<nb, 128, 0, s>>>(n, pos, boxes, cbox, sl, emit_mask, conf_mask, partner, face_off, inc_off,
                                     face_i, face_j, face_shift, face_area, face_normal, face_cen, fcap, inc_face,
                                     icap, vol, cen, st);
