@@ -208,6 +208,46 @@ def test_full_size_shear_layer_step_properties(gpu):
     assert 0 < float(dt.item()) < 1e-2
 
 
+def test_full_size_shear_layer_sampled_cells_match_oracle(oracle, gpu):
+    """The bench workload (256^3 generators, FP64 path, S10 limiter): one
+    whole step on the device against the oracle on sampled cells, each
+    computed from the oracle's own tessellation of the cell's rings 0..3 (see
+    helpers.oracle_local_step).  Inputs are identical on both sides: the
+    shear-layer primitives turned into charges with the nominal volume 1/n
+    (so W = U / V carries each cell's volume jitter), a fixed dt below the
+    CFL value.  Charges to 1e-10 of each component's scale (momentum: the
+    largest component's), positions to 1e-12."""
+    c, torch = gpu
+    w = WL.shear_layer(256)
+    n = w.n
+    U0 = oracle.charges_from_prims(np.full(n, 1.0 / n), w.rho, w.vel, w.pres, w.gamma)
+    dt = 2e-4
+    ocfg, gcfg = cfg_pair(oracle, w.gamma, cfl=w.cfl, limiter=1)
+    c.set_config(**{f: getattr(gcfg, f) for f, _ in gcfg._fields_})
+    pos = H.to_dev(torch, w.pos.T)
+    Ud = H.to_dev(torch, U0.T)
+    del U0
+    c.mm_step(pos, Ud, w.box, dt_fixed=torch.tensor([dt], dtype=torch.float64, device="cuda"))
+    rng = np.random.default_rng(1)
+    # random cells, plus cells on the two shear interfaces |y - 0.5| = 0.25
+    y = w.pos[:, 1]
+    near = np.nonzero(np.abs(np.abs(y - 0.5) - 0.25) < 0.5 / 256)[0]
+    cells = np.concatenate([rng.choice(n, 12, replace=False), rng.choice(near, 4, replace=False)])
+    G = Ud[:, torch.as_tensor(cells, device="cuda")].cpu().numpy().T
+    GP = pos[:, torch.as_tensor(cells, device="cuda")].cpu().numpy().T
+    del Ud, pos
+    U0 = oracle.charges_from_prims(np.full(n, 1.0 / n), w.rho, w.vel, w.pres, w.gamma)
+    O, OP, _, m = H.oracle_local_step(oracle, w.pos, U0, w.box, ocfg, cells, dt)
+    print(f"[256^3 one-step parity] {len(cells)} sampled cells, {m} cells tessellated by the oracle")
+    scale = np.abs(O).max(axis=0)
+    scale[1:4] = scale[1:4].max()
+    for k in range(5):
+        np.testing.assert_allclose(G[:, k], O[:, k], rtol=0, atol=RTOL_STEP * scale[k], err_msg=f"component {k}")
+    dp = GP - OP
+    dp -= np.round(dp / w.box) * w.box
+    assert np.abs(dp).max() <= 1e-12
+
+
 MIXED_CASES = {
     "smooth_wave_16^3": lambda: WL.smooth_wave(16),
     "shear_layer_32^3": lambda: WL.shear_layer(32),
