@@ -45,11 +45,24 @@ def test_single_rank_aggregation():
     assert ms == 50.0 and value == pytest.approx(400.0)
 
 
-def test_clip_traffic_comes_from_the_matching_capture():
-    """roofline.traffic is the committed full-size capture's DRAM bytes, and
-    null for any other cell count or clipper."""
+def test_clip_traffic_is_scaled_from_the_capture_of_the_same_clipper(monkeypatch):
+    """roofline.traffic is the DRAM bytes per cell of the 64^3 k_clip capture
+    times the cells of the launch, and null once the clipper's sources differ
+    from those the capture was taken on, or for the direct FP64 clipper."""
     import bench
-    t = bench.clip_traffic(256 ** 3, 1)
-    assert t is not None and t > 256 ** 3 * 64  # at least the binned generators and the cell records
-    assert bench.clip_traffic(64 ** 3, 1) is None
+    digest = bench.clip_sources_digest()
+    monkeypatch.setitem(bench.CLIP_TRAFFIC, "bytes_per_cell", 900.0)
+    monkeypatch.setitem(bench.CLIP_TRAFFIC, "sha256_16", digest)
+    assert bench.clip_traffic(256 ** 3, 1) == int(900.0 * 256 ** 3)
+    assert bench.clip_traffic(64 ** 3, 1) == int(900.0 * 64 ** 3)
     assert bench.clip_traffic(256 ** 3, 0) is None
+    monkeypatch.setitem(bench.CLIP_TRAFFIC, "sha256_16", "0" * 16)
+    assert bench.clip_traffic(256 ** 3, 1) is None
+
+
+def test_committed_clip_traffic_matches_the_current_clipper_or_is_absent():
+    import bench
+    if bench.CLIP_TRAFFIC["bytes_per_cell"] is not None:
+        # a stale figure is withheld at run time; this flags it in review
+        assert bench.CLIP_TRAFFIC["sha256_16"] == bench.clip_sources_digest()
+        assert 64 <= bench.CLIP_TRAFFIC["bytes_per_cell"] <= 4000
