@@ -90,7 +90,7 @@ typedef struct {
 /* Fill a config with the defaults: gamma 5/3, cfl 0.3, eta 1, chi 1, zeta
  * 0.25, theta 0.49, floors 1e-10, area_rel 1e-10, S10 limiter, no
  * roundness correction, FP64 hydro, filtered clipping, no counters, HLLC,
- * 4 clip warps per block, batches of 64 candidates, bins one mean spacing
+ * 2 clip warps per block, batches of 64 candidates, bins one mean spacing
  * wide, no entropy column (mach_th 1.1 when it is switched on), half-step
  * time integration. */
 void mm_default_config(mm_config *cfg);

@@ -225,10 +225,26 @@ static mm_status read_status(mm_ctx *c)
     if (s.flags & ST_ECAP_MESH)
         return fail(c, MM_ECAPACITY, "the batch has more faces than its fixed capacity (%lld faces, %lld incidences)",
                     (long long)c->fcap, (long long)c->icap);
-    return fail(c, MM_ECAPACITY,
-                "cell %d exceeded a per-cell capacity (flags 0x%x: 4 planes (%d), 8 vertices (%d), 16 vertices per "
-                "cut (%d), 32 faces (%d), 64 search rings (%d))",
-                s.bad_cell, s.flags, PMAX, TMAX, NSTAGE, MAXF, MAXRING);
+    // name every per-cell capacity that overflowed, with its limit
+    struct Cap {
+        int bit;
+        const char *what;
+        int limit;
+    };
+    const Cap caps[] = {{ST_ECAP_CAND, "candidates per sorted batch", 64},
+                        {ST_ECAP_PLANE, "clipping planes per cell", PMAX},
+                        {ST_ECAP_TRI, "vertices per cell", TMAX},
+                        {ST_ECAP_STAGE, "vertices created by one cut", NSTAGE},
+                        {ST_ECAP_FACE, "faces written per cell", MAXF},
+                        {ST_ECAP_RING, "neighbour search rings", MAXRING}};
+    char list[320] = {0};
+    size_t used = 0;
+    for (const Cap &k : caps)
+        if ((s.flags & k.bit) && used < sizeof(list))
+            used += (size_t)snprintf(list + used, sizeof(list) - used, "%s%s (limit %d)", used ? ", " : "", k.what,
+                                     k.limit);
+    return fail(c, MM_ECAPACITY, "cell %d exceeded a per-cell capacity: %s", s.bad_cell,
+                used ? list : "unknown");
 }
 
 static void fill_mesh(const mm_ctx *c, mm_mesh *out)

@@ -128,11 +128,20 @@ extern "C" mm_status mm_totals_noalloc(const double *U, int64_t n, double *total
     }
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const int ntiles = (int)((n + NA_TILE - 1) / NA_TILE);
+    // An earlier, unrelated call may have left a launch error pending; take
+    // it off first so that the checks below report only this call's launches
+    // (an error that persists, a sticky one, shows up again at the launch).
+    (void)cudaGetLastError();
     k_totals_tiles<<<ntiles, 256, 0, s>>>(U, n, scratch, ntiles);
-    k_totals_tiles_final<<<1, 32, 0, s>>>(scratch, ntiles, totals);
     e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        k_totals_tiles_final<<<1, 32, 0, s>>>(scratch, ntiles, totals);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) {
-        put_err(err, err_len, cudaGetErrorString(e));
+        char msg[200];
+        snprintf(msg, sizeof(msg), "mm_totals_noalloc: kernel launch failed: %s", cudaGetErrorString(e));
+        put_err(err, err_len, msg);
         return MM_ECUDA;
     }
     return MM_OK;
