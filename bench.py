@@ -169,12 +169,13 @@ def clip_roofline(direct, filtered, ms, n, clip_filter):
 
 
 # DRAM traffic of one k_clip launch, from an ncu capture of one launch on the
-# 64^3 shear layer (dram__bytes_read.sum + dram__bytes_write.sum, filtered
-# clipping, two warps per block), per cell; it scales with the cells of the
-# launch.  Valid only for the clipper source it was taken on: the digest of
-# the clipping kernel's sources must match, else the figure is withheld.
-CLIP_TRAFFIC = {"sources": ("csrc/mm_clip.cu", "csrc/mm_internal.cuh"), "sha256_16": None,
-                "bytes_per_cell": None, "cells_captured": 262144}
+# 128^3 shear layer (dram__bytes_read.sum + dram__bytes_write.sum = 460,677,376
+# + 1,439,818,496 bytes over 2,097,152 cells; filtered clipping, two warps per
+# block), per cell; it scales with the cells of the launch.  Valid only for the
+# clipper source it was taken on: the digest of the clipping kernel's sources
+# must match, else the figure is withheld.
+CLIP_TRAFFIC = {"sources": ("csrc/mm_clip.cu", "csrc/mm_internal.cuh"), "sha256_16": "7020642fab6ee46e",
+                "bytes_per_cell": 1900495872 / 2097152, "cells_captured": 2097152}
 
 
 def clip_sources_digest():
@@ -187,7 +188,7 @@ def clip_sources_digest():
 
 
 def clip_traffic(n, clip_filter):
-    """DRAM bytes of one k_clip launch on n cells, scaled from the 64^3
+    """DRAM bytes of one k_clip launch on n cells, scaled from the 128^3
     capture by cell count; None when the capture does not cover the current
     clipper source or clipper variant."""
     if not clip_filter or CLIP_TRAFFIC["bytes_per_cell"] is None:
@@ -800,7 +801,7 @@ def run_ours(args, world, rank, local):
         roofline["traffic"] = clip_traffic(n, args.clip_filter)
         if roofline["traffic"] is not None:
             roofline["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_clip launch "
-                                          "at 64^3, scaled by cells")
+                                          "at 128^3, scaled by cells")
     else:
         byts = algorithmic_bytes(dom, n, nf)
         if byts is not None:
