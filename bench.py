@@ -169,13 +169,13 @@ def clip_roofline(direct, filtered, ms, n, clip_filter):
 
 
 # DRAM traffic of one k_clip launch, from an ncu capture of one launch on the
-# 128^3 shear layer (dram__bytes_read.sum + dram__bytes_write.sum = 460,677,376
-# + 1,439,818,496 bytes over 2,097,152 cells; filtered clipping, two warps per
-# block), per cell; it scales with the cells of the launch.  Valid only for the
-# clipper source it was taken on: the digest of the clipping kernel's sources
-# must match, else the figure is withheld.
-CLIP_TRAFFIC = {"sources": ("csrc/mm_clip.cu", "csrc/mm_internal.cuh"), "sha256_16": "7020642fab6ee46e",
-                "bytes_per_cell": 1900495872 / 2097152, "cells_captured": 2097152}
+# 128^3 shear layer (dram__bytes_read.sum + dram__bytes_write.sum over the
+# launch's cells; filtered clipping, two warps per block), per cell; it scales
+# with the cells of the launch.  Valid only for the clipper source it was
+# taken on: the digest of the clipping kernel's sources must match, else the
+# figure is withheld (None: not yet taken on the current source).
+CLIP_TRAFFIC = {"sources": ("csrc/mm_clip.cu", "csrc/mm_internal.cuh"), "sha256_16": None,
+                "bytes_per_cell": None, "cells_captured": 2097152}
 
 
 def clip_sources_digest():

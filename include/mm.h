@@ -49,7 +49,8 @@ typedef enum {
     MM_OK = 0,
     MM_EINVAL = 1,      /* bad argument, position outside the box, non-finite value */
     MM_ENOMEM = 2,      /* device allocation failed                                  */
-    MM_ECAPACITY = 3,   /* a cell exceeded a fixed per-cell list (see mm_config)     */
+    MM_ECAPACITY = 3,   /* a cell exceeded a fixed per-cell list even when re-clipped  */
+                        /* with the large lists (see mm_tessellate)                   */
     MM_EDEGENERATE = 4, /* clipping met an inconsistent (numerically degenerate) cut */
     MM_ECUDA = 5,       /* a CUDA runtime call failed                               */
     MM_ETIMEOUT = 6     /* reserved: a bounded device wait gave up                   */
@@ -142,7 +143,16 @@ mm_status mm_set_config(mm_ctx *ctx, const mm_config *cfg);
  * distance, until every remaining generator is more than twice as far as
  * the farthest vertex.  pos[3][n] device.  Box sizes outside
  * [MM_MIN_BOX, MM_MAX_BOX] are MM_EINVAL (here, in mm_step, mm_step_batched
- * and mm_autotune).  Waits for completion. */
+ * and mm_autotune).  Waits for completion.
+ * Capacities: a cell is first clipped with lists of 64 planes, 128 vertices,
+ * 32 new vertices per cut, 48 faces and 48 search rings; a cell that
+ * overflows one is clipped again by a large instance of the clipper (128
+ * planes, 256 vertices, 64 new vertices per cut, 128 faces, 128 rings)
+ * whose faces go to an overflow row of that cell.  Only a cell beyond the
+ * large lists fails the call with MM_ECAPACITY.  Overflow rows are grown to
+ * the number of such cells here; a captured batch (mm_step_batched) has 256
+ * and reports more through mm_sync_status.  Two generators at the same
+ * position (or at the same periodic image) are MM_EDEGENERATE. */
 mm_status mm_tessellate(mm_ctx *ctx, const double *pos, int64_t n, const double box[3], mm_mesh *out);
 
 /* Limited cell-centred gradient of per-volume states W[5][n] (Sec. 4.1):
@@ -265,8 +275,9 @@ mm_status mm_copy(mm_ctx *ctx, void *dst, const void *src, int64_t bytes);
  * [0] max candidates in one sorted batch, [1] max planes of a cell,
  * [2] max vertices of a cell, [3] cells needing more than one search ring,
  * [4] total cuts, [5] FP64 plane tests, [6] FP64 three-plane solves,
- * [7] FP64 face-fan terms, [8] candidates tested. */
-#define MM_NSTATS 9
+ * [7] FP64 face-fan terms, [8] candidates tested, [9] cells re-clipped by the
+ * large-capacity clipper (counted with or without collect_stats). */
+#define MM_NSTATS 10
 mm_status mm_tess_stats(mm_ctx *ctx, int64_t stats[MM_NSTATS]);
 
 /* Stages of a step, for per-stage device timing. */

@@ -63,7 +63,7 @@ EXPORTS = ["mm_default_config", "mm_create", "mm_destroy", "mm_last_error", "mm_
            "mm_sync_status", "mm_current_mesh", "mm_get_config", "mm_autotune"]
 
 STATS = ["max_candidates", "max_planes", "max_vertices", "multi_ring_cells", "cuts", "fp64_plane_tests",
-         "fp64_vertex_solves", "fp64_fan_terms", "candidates_tested"]
+         "fp64_vertex_solves", "fp64_fan_terms", "candidates_tested", "retried_cells"]
 
 STAGES = ["bin", "clip", "faces", "mesh_velocity", "gradient_half_step", "gradient", "face_flux", "update",
           "drift"]

@@ -61,6 +61,9 @@ struct mm_ctx {
     Buf bin_of, bin_count, bin_start, bin_cursor, sorted, sortedf, scan_tmp;
     // clipping output
     Buf vol, cen, s_cnt, s_nb, s_sh, s_area, s_fc;
+    // cells re-clipped by the large clipper: the retry list and their overflow rows
+    Buf retry, o_cnt, o_nb, o_sh, o_area, o_fc, o_emit, o_conf, o_partner;
+    int64_t orows = 0;
     // face compaction
     Buf emit_mask, conf_mask, partner, emit_cnt, conf_cnt, face_off, inc_off;
     Buf face_i, face_j, face_shift, face_area, face_normal, face_cen, inc_face;
@@ -225,6 +228,11 @@ static mm_status read_status(mm_ctx *c)
     if (s.flags & ST_ECAP_MESH)
         return fail(c, MM_ECAPACITY, "the batch has more faces than its fixed capacity (%lld faces, %lld incidences)",
                     (long long)c->fcap, (long long)c->icap);
+    if (s.flags & ST_ECAP_RETRY)
+        return fail(c, MM_ECAPACITY,
+                    "%d cells overflowed the main clipper's per-cell lists, more than the %lld overflow rows "
+                    "reserved for a captured batch",
+                    s.nretry, (long long)c->orows);
     // name every per-cell capacity that overflowed, with its limit
     struct Cap {
         int bit;
@@ -238,6 +246,8 @@ static mm_status read_status(mm_ctx *c)
                         {ST_ECAP_FACE, "faces written per cell", MAXF},
                         {ST_ECAP_RING, "neighbour search rings", MAXRING}};
     char list[320] = {0};
+    // a cell reported here overflowed the large clipper too (planes 128,
+    // vertices 256, faces 128), after the main one's capacities below
     size_t used = 0;
     for (const Cap &k : caps)
         if ((s.flags & k.bit) && used < sizeof(list))
@@ -391,6 +401,20 @@ static mm_status ensure_faces(mm_ctx *c, int64_t nf, int64_t ni)
     return MM_OK;
 }
 
+// Overflow rows for `rows` cells re-clipped by the large clipper.
+static mm_status ensure_overflow(mm_ctx *c, int64_t rows)
+{
+    mm_status r;
+    const int64_t ns = rows * (int64_t)MAXF_BIG;
+    if ((r = ensure(c, c->o_cnt, rows * sizeof(int))) || (r = ensure(c, c->o_nb, ns * sizeof(int))) ||
+        (r = ensure(c, c->o_sh, ns)) || (r = ensure(c, c->o_area, ns * sizeof(double))) ||
+        (r = ensure(c, c->o_fc, 3 * ns * sizeof(double))) || (r = ensure(c, c->o_emit, 2 * rows * 8)) ||
+        (r = ensure(c, c->o_conf, 2 * rows * 8)) || (r = ensure(c, c->o_partner, ns)))
+        return r;
+    c->orows = rows;
+    return MM_OK;
+}
+
 static mm_status ensure_tess_buffers(mm_ctx *c, int64_t n)
 {
     mm_status r;
@@ -406,8 +430,10 @@ static mm_status ensure_tess_buffers(mm_ctx *c, int64_t n)
         (r = ensure(c, c->s_area, ns * sizeof(double))) || (r = ensure(c, c->s_fc, 3 * ns * sizeof(double))) ||
         (r = ensure(c, c->emit_mask, n * 8)) || (r = ensure(c, c->conf_mask, n * 8)) || (r = ensure(c, c->partner, ns)) ||
         (r = ensure(c, c->emit_cnt, n * sizeof(int))) || (r = ensure(c, c->conf_cnt, n * sizeof(int))) ||
-        (r = ensure(c, c->face_off, (n + 1) * sizeof(int))) || (r = ensure(c, c->inc_off, (n + 1) * sizeof(int))))
+        (r = ensure(c, c->face_off, (n + 1) * sizeof(int))) || (r = ensure(c, c->inc_off, (n + 1) * sizeof(int))) ||
+        (r = ensure(c, c->retry, n * sizeof(int))))
         return r;
+    if (c->orows < RETRY_ROWS_FIXED && (r = ensure_overflow(c, RETRY_ROWS_FIXED))) return r;
     return MM_OK;
 }
 
@@ -432,16 +458,30 @@ static mm_status tess_enqueue(mm_ctx *c, const double *pos, bool fixed)
     stage_mark(c, MM_STAGE_BIN, false);
     c->launches += 6;
 
-    Slots sl{P<int>(c->s_cnt), P<int>(c->s_nb), P<unsigned char>(c->s_sh), P<double>(c->s_area), P<double>(c->s_fc)};
+    auto slots = [c]() {
+        return Slots{P<int>(c->s_cnt), P<int>(c->s_nb), P<unsigned char>(c->s_sh), P<double>(c->s_area),
+                     P<double>(c->s_fc), c->orows, P<int>(c->o_cnt), P<int>(c->o_nb), P<unsigned char>(c->o_sh),
+                     P<double>(c->o_area), P<double>(c->o_fc), P<int>(c->retry)};
+    };
+    auto ovf = [c]() {
+        return OvfFaces{P<unsigned long long>(c->o_emit), P<unsigned long long>(c->o_conf),
+                        P<signed char>(c->o_partner)};
+    };
+    Slots sl = slots();
+    const int prec = c->cfg.clip_filter ? 1 : 0;
     stage_mark(c, MM_STAGE_CLIP, true);
-    launch_clip(P<double4_32a>(c->sorted), P<float4>(c->sortedf), P<int>(c->bin_start), n, boxes, cbox, c->cfg.clip_filter ? 1 : 0,
+    launch_clip(P<double4_32a>(c->sorted), P<float4>(c->sortedf), P<int>(c->bin_start), n, boxes, cbox, prec,
                 c->cfg.collect_stats,
                 c->cfg.clip_warps, c->cfg.cand_cap, P<double>(c->vol), P<double>(c->cen), sl, c->st, s);
+    // cells over a capacity of the main clipper, again with the large one
+    // (one warp per overflow row; nothing to do when no cell overflowed)
+    launch_clip_big(P<double4_32a>(c->sorted), P<float4>(c->sortedf), P<int>(c->bin_start), n, boxes, cbox, prec,
+                    c->cfg.collect_stats, c->cfg.cand_cap, P<double>(c->vol), P<double>(c->cen), sl, c->st, s);
     CKLAUNCH();
     stage_mark(c, MM_STAGE_CLIP, false);
-    c->launches += 1;
+    c->launches += 2;
     stage_mark(c, MM_STAGE_FACES, true);
-    launch_face_confirm(n, sl, P<unsigned long long>(c->emit_mask), P<unsigned long long>(c->conf_mask),
+    launch_face_confirm(n, sl, ovf(), P<unsigned long long>(c->emit_mask), P<unsigned long long>(c->conf_mask),
                         P<signed char>(c->partner), P<int>(c->emit_cnt), P<int>(c->conf_cnt), s);
     launch_scan(P<int>(c->emit_cnt), P<int>(c->face_off), n, P<int>(c->scan_tmp), s);
     launch_scan(P<int>(c->conf_cnt), P<int>(c->inc_off), n, P<int>(c->scan_tmp), s);
@@ -450,17 +490,35 @@ static mm_status tess_enqueue(mm_ctx *c, const double *pos, bool fixed)
     int64_t nf = 0, ni = 0;
     if (!fixed) {
         stage_mark(c, MM_STAGE_FACES, false);
-        CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(&c->cnt_host[0], P<int>(c->face_off) + n, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(&c->cnt_host[1], P<int>(c->inc_off) + n, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
+        for (int attempt = 0;; ++attempt) {
+            CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(&c->cnt_host[0], P<int>(c->face_off) + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(&c->cnt_host[1], P<int>(c->inc_off) + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (attempt > 0 || c->st_host->flags != ST_ECAP_RETRY) break;
+            // more cells overflowed than there were overflow rows: grow them to
+            // the count and re-clip the list (its first rows again, harmlessly)
+            if ((r = ensure_overflow(c, c->st_host->nretry))) return r;
+            sl = slots();
+            CK(cudaMemsetAsync(&c->st->flags, 0, sizeof(int), s));
+            launch_clip_big(P<double4_32a>(c->sorted), P<float4>(c->sortedf), P<int>(c->bin_start), n, boxes, cbox,
+                            prec, c->cfg.collect_stats, c->cfg.cand_cap, P<double>(c->vol), P<double>(c->cen), sl,
+                            c->st, s);
+            launch_face_confirm(n, sl, ovf(), P<unsigned long long>(c->emit_mask),
+                                P<unsigned long long>(c->conf_mask), P<signed char>(c->partner), P<int>(c->emit_cnt),
+                                P<int>(c->conf_cnt), s);
+            launch_scan(P<int>(c->emit_cnt), P<int>(c->face_off), n, P<int>(c->scan_tmp), s);
+            launch_scan(P<int>(c->conf_cnt), P<int>(c->inc_off), n, P<int>(c->scan_tmp), s);
+            CKLAUNCH();
+            c->launches += 8;
+        }
         if ((r = read_status(c))) return r;
         nf = c->cnt_host[0];
         ni = c->cnt_host[1];
         if ((r = ensure_faces(c, nf, ni))) return r;
         stage_mark(c, MM_STAGE_FACES, true);
     }
-    launch_face_write(n, pos, boxes, cbox, sl, P<unsigned long long>(c->emit_mask), P<unsigned long long>(c->conf_mask),
+    launch_face_write(n, pos, boxes, cbox, sl, ovf(), P<unsigned long long>(c->emit_mask), P<unsigned long long>(c->conf_mask),
                       P<signed char>(c->partner), P<int>(c->face_off), P<int>(c->inc_off), P<int>(c->face_i),
                       P<int>(c->face_j), P<int>(c->face_shift), P<double>(c->face_area), P<double>(c->face_normal),
                       P<double>(c->face_cen), c->fcap, P<int>(c->inc_face), c->icap, P<double>(c->vol),
@@ -699,6 +757,8 @@ void mm_destroy(mm_ctx *c)
                    &c->s_area, &c->s_fc, &c->emit_mask, &c->conf_mask, &c->partner, &c->emit_cnt, &c->conf_cnt,
                    &c->face_off, &c->inc_off, &c->face_i, &c->face_j, &c->face_shift, &c->face_area,
                    &c->face_normal, &c->face_cen, &c->inc_face, &c->Wh, &c->grad, &c->flux, &c->w_int, &c->dt_int,
+                   &c->retry, &c->o_cnt, &c->o_nb, &c->o_sh, &c->o_area, &c->o_fc, &c->o_emit, &c->o_conf,
+                   &c->o_partner,
                    &c->tot_partial, &c->drift_box, &c->drift_cbox, &c->x_fij, &c->x_fa, &c->x_fq, &c->x_ff,
                    &c->x_cw, &c->x_ch, &c->x_grad, &c->x_wv, &c->x_flux, &c->heun_U0, &c->fgeo, &c->minv};
     for (Buf *b : bufs)
@@ -1067,6 +1127,7 @@ mm_status mm_tess_stats(mm_ctx *c, int64_t stats[MM_NSTATS])
     stats[6] = (int64_t)c->st_host->solve64;
     stats[7] = (int64_t)c->st_host->fan64;
     stats[8] = (int64_t)c->st_host->tested;
+    stats[9] = (int64_t)c->st_host->nretry;
     return MM_OK;
 }
 

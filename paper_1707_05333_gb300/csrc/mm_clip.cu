@@ -41,36 +41,53 @@ constexpr unsigned FULL = 0xffffffffu;
 #define MM_CLIP_MAXNREG 128  // registers per thread of the clipping kernel
 #endif
 constexpr int CBATCH = 64;  // candidate buffer; flushed (sorted + clipped) when full
-constexpr int ETAB = 256;   // edge hash table slots used by the face walk
-static_assert(CBATCH == PMAX, "the candidate buffer doubles as per-face storage");
+
+// Per-cell capacities of one instance of the clipper: planes, vertices, new
+// vertices per cut, faces written, search rings and edge-table slots.  The
+// main instance runs every cell; the large one re-clips the cells that
+// overflowed the main one's lists.
+template <int PM_, int TM_, int NS_, int MF_, int MR_, int ETAB_, bool BIG_>
+struct Caps {
+    static constexpr int PM = PM_, TM = TM_, NS = NS_, MF = MF_, MR = MR_, ETAB = ETAB_;
+    static constexpr bool BIG = BIG_;
+    static constexpr int BMW = PM_ / 32;                  // bit-matrix words per plane row
+    static constexpr int PB = PM_ == 64 ? 6 : 7;          // bits of a plane index (edge-table keys)
+    static constexpr int TB = TM_ == 128 ? 7 : 8;         // bits of a triangle index (edge-table entries)
+    static constexpr int EH = ETAB_ == 256 ? 24 : 22;     // hash shift, 32 - log2(ETAB)
+    static constexpr int CID = PM_ > CBATCH ? PM_ : CBATCH;  // candidate ids, reused as first[plane]
+};
+using CapMain = Caps<PMAX, TMAX, NSTAGE, MAXF, MAXRING, 256, false>;
+using CapBig = Caps<PMAX_BIG, TMAX_BIG, NSTAGE_BIG, MAXF_BIG, MAXRING_BIG, 1024, true>;
+static_assert(CBATCH <= PMAX, "the candidate buffer shares its storage with the per-face arrays");
+static_assert(3 * TMAX_BIG <= 1024 * 3 / 4, "the large edge table holds every corner");
 
 // Vertex storage.  PREC 0 keeps FP64 vertices throughout.  PREC 1 keeps FP32
 // vertices with their error bounds while clipping and solves the FP64
 // vertices only at the end, when the FP32 copies and |v|^2 bounds are dead:
 // the two sets share the same bytes.
-template <int PREC>
+template <int PREC, class CAP>
 struct VertStore;
-template <>
-struct VertStore<0> {
-    double tx[TMAX], ty[TMAX], tz[TMAX];
-    long long tr2[TMAX];  // bits of |v|^2
+template <class CAP>
+struct VertStore<0, CAP> {
+    double tx[CAP::TM], ty[CAP::TM], tz[CAP::TM];
+    long long tr2[CAP::TM];  // bits of |v|^2
     float4 tf[1];
 };
-template <>
-struct VertStore<1> {
+template <class CAP>
+struct VertStore<1, CAP> {
     union {
         struct {
-            double tx[TMAX], ty[TMAX], tz[TMAX];  // after clipping
+            double tx[CAP::TM], ty[CAP::TM], tz[CAP::TM];  // after clipping
         };
         struct {
-            long long tr2[TMAX];  // bits of an FP32 upper bound of |v|^2
-            float4 tf[TMAX];      // FP32 vertex (x, y, z) and its error bound (w)
+            long long tr2[CAP::TM];  // bits of an FP32 upper bound of |v|^2
+            float4 tf[CAP::TM];      // FP32 vertex (x, y, z) and its error bound (w)
         };
     };
 };
 
-template <int PREC>
-struct ClipSmem : VertStore<PREC> {
+template <int PREC, class CAP>
+struct ClipSmem : VertStore<PREC, CAP> {
     union {
         struct {
             double x[CBATCH], y[CBATCH], z[CBATCH];
@@ -78,21 +95,44 @@ struct ClipSmem : VertStore<PREC> {
             float4 cf[CBATCH];     // FP32 copies (q, |q|^2 / 2) for filtered clipping
         } c;
         struct {
-            double a[PMAX], x[PMAX], y[PMAX], z[PMAX];  // per-face area and centroid
-            unsigned etab[ETAB];                        // directed edge -> (triangle, third corner)
+            double a[CAP::PM], x[CAP::PM], y[CAP::PM], z[CAP::PM];  // per-face area and centroid
+            unsigned etab[CAP::ETAB];                               // directed edge -> (triangle, third corner)
         } f;
     } u;
-    int cid[CBATCH], csh[CBATCH];
+    int cid[CAP::CID], csh[CBATCH];
     unsigned char perm[CBATCH];  // clipping order of the buffered candidates
-    double px[PMAX], py[PMAX], pz[PMAX], po[PMAX];  // planes x.q <= po
-    int pnb[PMAX], psh[PMAX];
-    unsigned tv[TMAX];                    // a | b << 8 | c << 16
-    unsigned bm[2 * PMAX];                // removed directed edges x -> y: bit y % 32 of word 2x + y / 32
-    unsigned stage[NSTAGE];               // triangles created by the current cut
+    double px[CAP::PM], py[CAP::PM], pz[CAP::PM], po[CAP::PM];  // planes x.q <= po
+    int pnb[CAP::PM], psh[CAP::PM];
+    unsigned tv[CAP::TM];                  // a | b << 8 | c << 16
+    unsigned bm[CAP::BMW * CAP::PM];       // removed directed edges x -> y: bit y % 32 of word BMW x + y / 32
+    unsigned stage[CAP::NS];               // triangles created by the current cut
     double off[9];               // image offsets s L - p: off[3 d + s + 1], s = -1, 0, +1
     float offf[9];               // their FP32 roundings (the gather filter)
-    float4 pf[PREC ? PMAX : 1];  // FP32 planes (q, o)
-    float pfn[PREC ? PMAX : 1];  // FP32 |q| = sqrt(2 o) of each plane (for the vertex error bound)
+    float4 pf[PREC ? CAP::PM : 1];  // FP32 planes (q, o)
+    float pfn[PREC ? CAP::PM : 1];  // FP32 |q| = sqrt(2 o) of each plane (for the vertex error bound)
+};
+
+// Sets of plane indices (one bit per plane slot) for the rim check and the
+// slot recycling: one 64-bit word for the main instance, two for the large.
+template <int PM>
+struct PMask;
+template <>
+struct PMask<64> {
+    unsigned long long w = 0ull;
+    __device__ __forceinline__ void set(unsigned b) { w |= 1ull << b; }
+    __device__ __forceinline__ int popc() const { return __popcll(w); }
+    __device__ __forceinline__ bool operator!=(const PMask &o) const { return w != o.w; }
+};
+template <>
+struct PMask<128> {
+    unsigned long long w = 0ull, h = 0ull;
+    __device__ __forceinline__ void set(unsigned b)
+    {
+        if (b < 64u) w |= 1ull << b;
+        else h |= 1ull << (b - 64u);
+    }
+    __device__ __forceinline__ int popc() const { return __popcll(w) + __popcll(h); }
+    __device__ __forceinline__ bool operator!=(const PMask &o) const { return w != o.w || h != o.h; }
 };
 
 // Rarely taken integer work of the gather, kept out of line so that the hot
@@ -164,6 +204,32 @@ __device__ __forceinline__ unsigned long long warp_or64(unsigned long long v)
     const unsigned hi = __reduce_or_sync(FULL, (unsigned)(v >> 32));
     return ((unsigned long long)hi << 32) | lo;
 }
+__device__ __forceinline__ PMask<64> warp_or(PMask<64> m)
+{
+    m.w = warp_or64(m.w);
+    return m;
+}
+__device__ __forceinline__ PMask<128> warp_or(PMask<128> m)
+{
+    m.w = warp_or64(m.w);
+    m.h = warp_or64(m.h);
+    return m;
+}
+// The lowest plane slot below np that no vertex refers to, or -1.
+__device__ __forceinline__ int first_free(const PMask<64> &live, int np)
+{
+    const unsigned long long used = np >= 64 ? ~0ull : ((1ull << np) - 1ull);
+    const unsigned long long freeb = used & ~live.w;
+    return freeb ? __ffsll((long long)freeb) - 1 : -1;
+}
+__device__ __forceinline__ int first_free(const PMask<128> &live, int np)
+{
+    const unsigned long long u0 = np >= 64 ? ~0ull : ((1ull << np) - 1ull);
+    const unsigned long long u1 = np >= 128 ? ~0ull : (np <= 64 ? 0ull : ((1ull << (np - 64)) - 1ull));
+    const unsigned long long f0 = u0 & ~live.w, f1 = u1 & ~live.h;
+    if (f0) return __ffsll((long long)f0) - 1;
+    return f1 ? 64 + __ffsll((long long)f1) - 1 : -1;
+}
 
 // Intersection of planes a, b, c in FP64 with explicitly rounded operations
 // (so every caller gets the same bits):
@@ -212,7 +278,8 @@ __device__ __forceinline__ long long r2_bits64(double x, double y, double z)
 // to FP32, cross products, determinant, numerator, scaling) gives
 // |v~ - v| <= u H (5.5 sum|q| + 13 |v|); the bound used is three times that.
 // Ill-conditioned intersections get an infinite bound (always checked in FP64).
-__device__ __forceinline__ void vertex32(const ClipSmem<1> &S, int a, int b, int c, float &x, float &y, float &z,
+template <class S_t>
+__device__ __forceinline__ void vertex32(const S_t &S, int a, int b, int c, float &x, float &y, float &z,
                                          float &err)
 {
     const float4 Pa = S.pf[a], Pb = S.pf[b], Pc = S.pf[c];
@@ -284,16 +351,16 @@ __device__ __noinline__ int scan_next(const unsigned *tv, int nt, unsigned p, un
 }
 
 // Candidate order: (|q|^2, id, image code).
-template <int PREC>
-__device__ __forceinline__ bool cand_less(const ClipSmem<PREC> &S, int a, int b)
+template <class S_t>
+__device__ __forceinline__ bool cand_less(const S_t &S, int a, int b)
 {
     if (S.u.c.d2[a] != S.u.c.d2[b]) return S.u.c.d2[a] < S.u.c.d2[b];
     if (S.cid[a] != S.cid[b]) return S.cid[a] < S.cid[b];
     return S.csh[a] < S.csh[b];
 }
 
-template <int PREC>
-__device__ __forceinline__ void cand_swap(ClipSmem<PREC> &S, int a, int b)
+template <class S_t>
+__device__ __forceinline__ void cand_swap(S_t &S, int a, int b)
 {
     double t;
     t = S.u.c.x[a]; S.u.c.x[a] = S.u.c.x[b]; S.u.c.x[b] = t;
@@ -306,8 +373,8 @@ __device__ __forceinline__ void cand_swap(ClipSmem<PREC> &S, int a, int b)
 }
 
 // Warp bitonic sort of the first m candidates (padded to a power of two).
-template <int PREC>
-__device__ void sort_candidates(ClipSmem<PREC> &S, int m, int lane)
+template <class S_t>
+__device__ void sort_candidates(S_t &S, int m, int lane)
 {
     int P = 1;
     while (P < m) P <<= 1;
@@ -373,7 +440,10 @@ __device__ __forceinline__ void update_limit(CellState &C, long long m)
 // The removed-vertex masks of a cut, one 32-bit ballot per chunk of 32
 // vertices, held in two 64-bit registers: the chunk loops then need no
 // unrolling to keep them out of local memory (a smaller kernel body).
-struct ChunkMask {
+template <int TM>
+struct ChunkMask;
+template <>
+struct ChunkMask<128> {
     unsigned long long lo = 0ull, hi = 0ull;
     __device__ __forceinline__ unsigned get(int c) const
     {
@@ -385,16 +455,67 @@ struct ChunkMask {
         if (c < 2) lo |= v;
         else hi |= v;
     }
+    __device__ __forceinline__ bool any() const { return (lo | hi) != 0ull; }
     __device__ __forceinline__ int count() const { return __popcll(lo) + __popcll(hi); }
 };
+template <>
+struct ChunkMask<256> {
+    unsigned long long w0 = 0ull, w1 = 0ull, w2 = 0ull, w3 = 0ull;
+    __device__ __forceinline__ unsigned get(int c) const
+    {
+        const unsigned long long w = c < 2 ? w0 : (c < 4 ? w1 : (c < 6 ? w2 : w3));
+        return (unsigned)(w >> (32 * (c & 1)));
+    }
+    __device__ __forceinline__ void put(int c, unsigned m)
+    {
+        const unsigned long long v = (unsigned long long)m << (32 * (c & 1));
+        if (c < 2) w0 |= v;
+        else if (c < 4) w1 |= v;
+        else if (c < 6) w2 |= v;
+        else w3 |= v;
+    }
+    __device__ __forceinline__ bool any() const { return (w0 | w1 | w2 | w3) != 0ull; }
+    __device__ __forceinline__ int count() const { return __popcll(w0) + __popcll(w1) + __popcll(w2) + __popcll(w3); }
+};
 
-template <int PREC>
-__device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
+// A new vertex of the cut by plane kp: the intersection of the rim edge's two
+// planes with kp, FP64 (PREC 0) or FP32 with its error bound (PREC 1), and the
+// bits of (a bound of) |v|^2.
+template <int PREC, class S_t>
+__device__ __forceinline__ void new_vertex(const S_t &S, unsigned nvt, int kp, long long &nr2, double &nX, double &nY,
+                                           double &nZ, float4 &nf)
 {
+    if constexpr (PREC == 0) {
+        vertex64(S, nvt & 255u, (nvt >> 8) & 255u, kp, nX, nY, nZ);
+        nr2 = r2_bits64(nX, nY, nZ);
+    } else {
+        float x, y, z, er;
+        vertex32(S, nvt & 255u, (nvt >> 8) & 255u, kp, x, y, z, er);
+        if (!(er < 1e30f)) {
+            // ill-conditioned intersection: solve it in FP64 now and keep
+            // its FP32 rounding, whose error is then one rounding per axis
+            double X, Y, Z;
+            vertex64_call(S, nvt & 255u, (nvt >> 8) & 255u, kp, X, Y, Z);
+            x = (float)X; y = (float)Y; z = (float)Z;
+            er = 1.2e-7f * (fabsf(x) + fabsf(y) + fabsf(z)) + 1e-38f;
+        }
+        nf = make_float4(x, y, z, er);
+        // an FP32 upper bound of (|v| + er)^2 <= |v|^2 + er (2 |v|_1 + er),
+        // kept as the bit pattern of a positive float
+        const float s2 = fmaf(x, x, fmaf(y, y, z * z));
+        const float l1 = fabsf(x) + fabsf(y) + fabsf(z);
+        nr2 = (long long)__float_as_int(fmaf(er, fmaf(2.0f, l1, er), s2) * 1.00001f);
+    }
+}
+
+template <int PREC, class CAP>
+__device__ void clip_by(ClipSmem<PREC, CAP> &S, int k, CellState &C, int lane)
+{
+    constexpr int BMW = CAP::BMW;
     const double qx = S.u.c.x[k], qy = S.u.c.y[k], qz = S.u.c.z[k];
     const double off = half_of(S.u.c.d2[k]);
     const int nchunk = (C.nt + 31) >> 5;
-    ChunkMask outm;
+    ChunkMask<CAP::TM> outm;
     C.tested++;
     if (PREC == 0) C.pred64 += C.nt;
     float fqx = 0.f, fqy = 0.f, fqz = 0.f, foff = 0.f, fqn = 0.f;
@@ -433,12 +554,12 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
             // mark the directed edges of the removed triangle
             const unsigned v = S.tv[t];
             const unsigned a = v & 255u, b = (v >> 8) & 255u, cc = (v >> 16) & 255u;
-            atomicOr(&S.bm[2 * a + (b >> 5)], 1u << (b & 31u));
-            atomicOr(&S.bm[2 * b + (cc >> 5)], 1u << (cc & 31u));
-            atomicOr(&S.bm[2 * cc + (a >> 5)], 1u << (a & 31u));
+            atomicOr(&S.bm[BMW * a + (b >> 5)], 1u << (b & 31u));
+            atomicOr(&S.bm[BMW * b + (cc >> 5)], 1u << (cc & 31u));
+            atomicOr(&S.bm[BMW * cc + (a >> 5)], 1u << (a & 31u));
         }
     }
-    if ((outm.lo | outm.hi) == 0ull) return;
+    if (!outm.any()) return;
     // the new plane takes a fresh slot while fewer than 32 are in use (one
     // lane per face when the faces are summed); beyond that, the lowest slot
     // no vertex refers to (a face that has vanished frees its slot), else a
@@ -447,18 +568,17 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
     if (C.np < 32) {
         kp = C.np;
     } else {
-        unsigned long long live = 0ull;
+        PMask<CAP::PM> live;
         for (int t = lane; t < C.nt; t += 32) {
             const unsigned v = S.tv[t];
-            live |= (1ull << (v & 255u)) | (1ull << ((v >> 8) & 255u)) | (1ull << ((v >> 16) & 255u));
+            live.set(v & 255u);
+            live.set((v >> 8) & 255u);
+            live.set((v >> 16) & 255u);
         }
-        live = warp_or64(live);
-        const unsigned long long used = C.np >= 64 ? ~0ull : ((1ull << C.np) - 1ull);
-        const unsigned long long freeb = used & ~live;
-        if (freeb) {
-            kp = __ffsll((long long)freeb) - 1;
-        } else {
-            if (C.np >= PMAX) { C.err |= ST_ECAP_PLANE; return; }
+        live = warp_or(live);
+        kp = first_free(live, C.np);
+        if (kp < 0) {
+            if (C.np >= CAP::PM) { C.err |= ST_ECAP_PLANE; return; }
             kp = C.np;
         }
     }
@@ -473,7 +593,7 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
     __syncwarp();
     // rim edges: removed x->y whose reverse y->x is not removed
     int nnew = 0;
-    unsigned long long xs = 0, ys = 0;
+    PMask<CAP::PM> xs, ys;
 #pragma unroll 1
     for (int c = 0; c < nchunk; ++c) {
         const unsigned oc = outm.get(c);
@@ -485,15 +605,15 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
             const unsigned v = S.tv[c * 32 + lane];
             const unsigned a = v & 255u, b = (v >> 8) & 255u, cc = (v >> 16) & 255u;
             const unsigned hk = (unsigned)kp << 16;
-            f0 = !((S.bm[2 * b + (a >> 5)] >> (a & 31u)) & 1u);    // a -> b
-            f1 = !((S.bm[2 * cc + (b >> 5)] >> (b & 31u)) & 1u);   // b -> cc
-            f2 = !((S.bm[2 * a + (cc >> 5)] >> (cc & 31u)) & 1u);  // cc -> a
+            f0 = !((S.bm[BMW * b + (a >> 5)] >> (a & 31u)) & 1u);    // a -> b
+            f1 = !((S.bm[BMW * cc + (b >> 5)] >> (b & 31u)) & 1u);   // b -> cc
+            f2 = !((S.bm[BMW * a + (cc >> 5)] >> (cc & 31u)) & 1u);  // cc -> a
             e0 = a | (b << 8) | hk;
             e1 = b | (cc << 8) | hk;
             e2 = cc | (a << 8) | hk;
-            if (f0) { xs |= 1ull << a; ys |= 1ull << b; }
-            if (f1) { xs |= 1ull << b; ys |= 1ull << cc; }
-            if (f2) { xs |= 1ull << cc; ys |= 1ull << a; }
+            if (f0) { xs.set(a); ys.set(b); }
+            if (f1) { xs.set(b); ys.set(cc); }
+            if (f2) { xs.set(cc); ys.set(a); }
         }
         const int cnt = (int)f0 + (int)f1 + (int)f2;
         // exclusive prefix of cnt (0..3) from the ballots of its two bits
@@ -501,20 +621,20 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
         const unsigned lt = lanemask_lt();
         const int tot = __popc(b0) + 2 * __popc(b1);
         int o = nnew + __popc(b0 & lt) + 2 * __popc(b1 & lt);
-        if (f0) { if (o < NSTAGE) S.stage[o] = e0; ++o; }
-        if (f1) { if (o < NSTAGE) S.stage[o] = e1; ++o; }
-        if (f2) { if (o < NSTAGE) S.stage[o] = e2; ++o; }
+        if (f0) { if (o < CAP::NS) S.stage[o] = e0; ++o; }
+        if (f1) { if (o < CAP::NS) S.stage[o] = e1; ++o; }
+        if (f2) { if (o < CAP::NS) S.stage[o] = e2; ++o; }
         nnew += tot;
     }
     __syncwarp();
-    for (int r = lane; r < 2 * C.np; r += 32) S.bm[r] = 0u;
-    xs = warp_or64(xs);
-    ys = warp_or64(ys);
-    if (nnew > NSTAGE) { C.err |= ST_ECAP_STAGE; return; }
-    if (nnew < 3 || xs != ys || __popcll(xs) != nnew) { C.err |= ST_EDEGEN; return; }
+    for (int r = lane; r < BMW * C.np; r += 32) S.bm[r] = 0u;
+    xs = warp_or(xs);
+    ys = warp_or(ys);
+    if (nnew > CAP::NS) { C.err |= ST_ECAP_STAGE; return; }
+    if (nnew < 3 || xs != ys || xs.popc() != nnew) { C.err |= ST_EDEGEN; return; }
     const int nrem = outm.count();
     const int nkept = C.nt - nrem;
-    if (nkept + nnew > TMAX) { C.err |= ST_ECAP_TRI; return; }
+    if (nkept + nnew > CAP::TM) { C.err |= ST_ECAP_TRI; return; }
     // the new vertices first, one per lane (nnew <= 32), kept in registers:
     // their arithmetic then overlaps the compaction's shared-memory traffic
     long long mr = 0;  // this lane's largest |v|^2 bound, for the new limit
@@ -525,27 +645,7 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
     float4 nf = make_float4(0.f, 0.f, 0.f, 0.f);
     if (mk) {
         nvt = S.stage[lane];
-        if constexpr (PREC == 0) {
-            vertex64(S, nvt & 255u, (nvt >> 8) & 255u, kp, nX, nY, nZ);
-            nr2 = r2_bits64(nX, nY, nZ);
-        } else {
-            float x, y, z, er;
-            vertex32(S, nvt & 255u, (nvt >> 8) & 255u, kp, x, y, z, er);
-            if (!(er < 1e30f)) {
-                // ill-conditioned intersection: solve it in FP64 now and keep
-                // its FP32 rounding, whose error is then one rounding per axis
-                double X, Y, Z;
-                vertex64_call(S, nvt & 255u, (nvt >> 8) & 255u, kp, X, Y, Z);
-                x = (float)X; y = (float)Y; z = (float)Z;
-                er = 1.2e-7f * (fabsf(x) + fabsf(y) + fabsf(z)) + 1e-38f;
-            }
-            nf = make_float4(x, y, z, er);
-            // an FP32 upper bound of (|v| + er)^2 <= |v|^2 + er (2 |v|_1 + er),
-            // kept as the bit pattern of a positive float
-            const float s2 = fmaf(x, x, fmaf(y, y, z * z));
-            const float l1 = fabsf(x) + fabsf(y) + fabsf(z);
-            nr2 = (long long)__float_as_int(fmaf(er, fmaf(2.0f, l1, er), s2) * 1.00001f);
-        }
+        new_vertex<PREC>(S, nvt, kp, nr2, nX, nY, nZ, nf);
         mr = nr2;
     }
     // compact the kept triangles in place (destinations never pass sources)
@@ -585,6 +685,19 @@ __device__ void clip_by(ClipSmem<PREC> &S, int k, CellState &C, int lane)
         if constexpr (PREC == 0) { S.tx[t] = nX; S.ty[t] = nY; S.tz[t] = nZ; }
         else S.tf[t] = nf;
     }
+    if constexpr (CAP::NS > 32) {
+        // the large instance: new vertices beyond the first 32, one more per lane
+        if (lane + 32 < nnew) {
+            const unsigned v2 = S.stage[lane + 32];
+            new_vertex<PREC>(S, v2, kp, nr2, nX, nY, nZ, nf);
+            mr = max(mr, nr2);
+            const int t = nkept + lane + 32;
+            S.tv[t] = v2;
+            S.tr2[t] = nr2;
+            if constexpr (PREC == 0) { S.tx[t] = nX; S.ty[t] = nY; S.tz[t] = nZ; }
+            else S.tf[t] = nf;
+        }
+    }
     __syncwarp();
     if (PREC == 0) C.solve64 += nnew;
     C.nt = nkept + nnew;
@@ -600,20 +713,30 @@ struct Gather {
     const double4_32a *sorted;
 };
 
-template <int PREC>
-__device__ void flush_batch(ClipSmem<PREC> &S, int &ncand, CellState &C, int lane, const Gather &G)
+template <int PREC, class CAP>
+__device__ void flush_batch(ClipSmem<PREC, CAP> &S, int &ncand, CellState &C, int lane, const Gather &G)
 {
     if (ncand == 0) return;
     // exact planes, one lane per candidate: q = r_j + s L - p in FP64 and the
-    // bit pattern of |q|^2 (the sort key); the buffer held the sorted index
+    // bit pattern of |q|^2 (the sort key); the buffer held the sorted index.
+    // A candidate at distance 0 is another generator at the same position: the
+    // two cells coincide, which a Voronoi tessellation does not allow.
+    bool coincident = false;
     for (int k = lane; k < ncand; k += 32) {
         const int code = S.csh[k];
         const double4_32a P = G.sorted[S.cid[k]];
         const int dx = code % 3, dy = (code / 3) % 3, dz = code / 9;
         const double qx = P.x + S.off[dx], qy = P.y + S.off[3 + dy], qz = P.z + S.off[6 + dz];
         S.u.c.x[k] = qx; S.u.c.y[k] = qy; S.u.c.z[k] = qz;
-        S.u.c.d2[k] = __double_as_longlong(__fma_rn(qx, qx, __fma_rn(qy, qy, __dmul_rn(qz, qz))));
+        const long long d2 = __double_as_longlong(__fma_rn(qx, qx, __fma_rn(qy, qy, __dmul_rn(qz, qz))));
+        S.u.c.d2[k] = d2;
+        coincident |= d2 == 0;
         S.cid[k] = (int)__double_as_longlong(P.w);
+    }
+    if (__any_sync(FULL, coincident)) {
+        C.err |= ST_EDEGEN;
+        ncand = 0;
+        return;
     }
     __syncwarp();
     if (ncand <= 32) {
@@ -652,14 +775,18 @@ __device__ void flush_batch(ClipSmem<PREC> &S, int &ncand, CellState &C, int lan
     for (int k = 0; k < ncand; ++k) {
         const int kk = S.perm[k];
         if (S.u.c.d2[kk] > C.lim) break;
-        clip_by<PREC>(S, kk, C, lane);
+        clip_by<PREC, CAP>(S, kk, C, lane);
         if (C.err) break;
     }
     ncand = 0;
     __syncwarp();
 }
 
-template <int PREC>
+// The main instance (CAP::BIG false) clips binned entry w of every warp; a
+// cell that overflows one of its lists goes to the retry list instead of
+// failing.  The large instance (one warp per block) clips entry retry[r] of
+// block r and writes its faces to overflow row r.
+template <int PREC, class CAP>
 __global__ void __maxnreg__(MM_CLIP_MAXNREG)
 k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sortedf, const int *__restrict__ start,
        int64_t n,
@@ -668,9 +795,17 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
 {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
-    if (w >= n) return;
-    ClipSmem<PREC> &S = reinterpret_cast<ClipSmem<PREC> *>(dyn_smem)[wid];
+    int64_t w;
+    if constexpr (CAP::BIG) {
+        const int nr = *(volatile int *)&st->nretry;
+        if (blockIdx.x == 0 && threadIdx.x == 0 && nr > sl.orows) atomicOr(&st->flags, ST_ECAP_RETRY);
+        if ((int64_t)blockIdx.x >= (nr < sl.orows ? (int64_t)nr : sl.orows)) return;
+        w = sl.retry[blockIdx.x];
+    } else {
+        w = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
+        if (w >= n) return;
+    }
+    ClipSmem<PREC, CAP> &S = reinterpret_cast<ClipSmem<PREC, CAP> *>(dyn_smem)[wid];
     // A box's cells occupy the same range of indices in the input order and in
     // the binned order (the bins are laid out box by box), so the box of
     // binned entry w is cbox[w]: no need to wait for the generator's id.
@@ -732,7 +867,7 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
             S.tf[lane] = make_float4(x, y, z, 0.0f);
         }
     }
-    for (int r = lane; r < 2 * PMAX; r += 32) S.bm[r] = 0u;
+    for (int r = lane; r < CAP::BMW * CAP::PM; r += 32) S.bm[r] = 0u;
     __syncwarp();
     CellState C;
     C.np = 6;
@@ -836,7 +971,7 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
             maxcand = max(maxcand, ncand);
             __syncwarp();
         }
-        flush_batch<PREC>(S, ncand, C, lane, G);
+        flush_batch<PREC, CAP>(S, ncand, C, lane, G);
         if (C.err || !ring_done) continue;
         ++rings;
         // radius the gathered rings are guaranteed to cover
@@ -846,7 +981,7 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
         if (C.lim <= dbits_of_float(R * R * 0.999999f)) break;  // R^2 rounded down
         rl = rh + 1;
         rh = rl;
-        if (rh > MAXRING) { C.err |= ST_ECAP_RING; break; }
+        if (rh > CAP::MR) { C.err |= ST_ECAP_RING; break; }
         total = (2 * rh + 1) * (2 * rh + 1) * (2 * rh + 1);
         base = 0;
     }
@@ -869,6 +1004,7 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
     // around a face is one lookup.  Keys are unique in a closed
     // triangulation; the load stays below 3/4 (else the walk scans instead).
     // The first triangle of each face is the lowest index containing it.
+    constexpr int ETAB = CAP::ETAB, PB = CAP::PB, TB = CAP::TB;
     const bool use_tab = !C.err && 3 * C.nt <= (3 * ETAB) / 4;
     unsigned *etab = S.u.f.etab;
     int *first = S.cid;  // the candidate ids are dead after clipping
@@ -883,9 +1019,9 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
             const unsigned x = k == 0 ? a : (k == 1 ? b : c);
             const unsigned y = k == 0 ? b : (k == 1 ? c : a);
             const unsigned z = k == 0 ? c : (k == 1 ? a : b);
-            const unsigned key = x * 64u + y;
-            const unsigned ent = (key << 13) | (z << 7) | (unsigned)t;
-            unsigned h = (key * 2654435761u) >> 24;
+            const unsigned key = (x << PB) | y;
+            const unsigned ent = (key << (PB + TB)) | (z << TB) | (unsigned)t;
+            unsigned h = (key * 2654435761u) >> CAP::EH;
             for (int probe = 0; probe < ETAB; ++probe) {
                 if (atomicCAS(&etab[h], 0xffffffffu, ent) == 0xffffffffu) break;
                 h = (h + 1) & (ETAB - 1);
@@ -934,17 +1070,21 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
             double W = 0.0, su = 0.0, sv = 0.0;
             int cnt = 0;
             bool ok = false;
-            for (int guard = 0; guard < TMAX; ++guard) {
+            for (int guard = 0; guard < CAP::TM; ++guard) {
                 // next vertex around p: the triangle containing p -> y
                 int tn = -1;
                 unsigned z = 0;
                 if (use_tab) {
-                    const unsigned key = (unsigned)p * 64u + y;
-                    unsigned h = (key * 2654435761u) >> 24;
+                    const unsigned key = ((unsigned)p << PB) | y;
+                    unsigned h = (key * 2654435761u) >> CAP::EH;
                     for (int probe = 0; probe < ETAB; ++probe) {
                         const unsigned ent = etab[h];
                         if (ent == 0xffffffffu) break;
-                        if ((ent >> 13) == key) { tn = (int)(ent & 127u); z = (ent >> 7) & 63u; break; }
+                        if ((ent >> (PB + TB)) == key) {
+                            tn = (int)(ent & ((1u << TB) - 1u));
+                            z = (ent >> TB) & ((1u << PB) - 1u);
+                            break;
+                        }
                         h = (h + 1) & (ETAB - 1);
                     }
                 } else {
@@ -995,35 +1135,51 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
 
     int nface = 0;
     if (!C.err) {
-        const int64_t sbase = (int64_t)self * MAXF;
+        // the main instance writes row `self` of the per-cell slots, the large
+        // one overflow row blockIdx.x
+        int *const rnb = CAP::BIG ? sl.onb : sl.nb;
+        unsigned char *const rsh = CAP::BIG ? sl.osh : sl.sh;
+        double *const rarea = CAP::BIG ? sl.oarea : sl.area;
+        double *const rfc = CAP::BIG ? sl.ofc : sl.fc;
+        const int64_t sbase = CAP::BIG ? (int64_t)blockIdx.x * CAP::MF : (int64_t)self * CAP::MF;
+        const int64_t ns = CAP::BIG ? sl.orows * (int64_t)CAP::MF : n * (int64_t)CAP::MF;
         for (int p0 = 0; p0 < C.np; p0 += 32) {
             const int p = p0 + lane;
             const bool keep = p < C.np && abs_bits(S.u.f.a[p]) > abs_bits(amin);  // both >= 0
             const unsigned km = __ballot_sync(FULL, keep);
             if (keep) {
                 const int k = nface + __popc(km & lanemask_lt());
-                if (k < MAXF) {
+                if (k < CAP::MF) {
                     const int64_t s = sbase + k;
-                    sl.nb[s] = S.pnb[p];
-                    sl.sh[s] = (unsigned char)S.psh[p];
-                    sl.area[s] = S.u.f.a[p];
-                    const int64_t ns = n * (int64_t)MAXF;
-                    sl.fc[s] = S.u.f.x[p];  // relative to the generator
-                    sl.fc[ns + s] = S.u.f.y[p];
-                    sl.fc[2 * ns + s] = S.u.f.z[p];
+                    rnb[s] = S.pnb[p];
+                    rsh[s] = (unsigned char)S.psh[p];
+                    rarea[s] = S.u.f.a[p];
+                    rfc[s] = S.u.f.x[p];  // relative to the generator
+                    rfc[ns + s] = S.u.f.y[p];
+                    rfc[2 * ns + s] = S.u.f.z[p];
                 }
             }
             nface += __popc(km);
         }
-        if (nface > MAXF) C.err |= ST_ECAP_FACE;
+        if (nface > CAP::MF) C.err |= ST_ECAP_FACE;
     }
     if (lane == 0) {
         if (C.err) {
-            atomicOr(&st->flags, C.err);
-            atomicExch(&st->bad_cell, self);
             nface = 0;
+            if (!CAP::BIG && (C.err & ~ST_RETRYABLE) == 0) {
+                // over a capacity of this instance only: the large one clips it again
+                sl.retry[atomicAdd(&st->nretry, 1)] = (int)w;
+            } else {
+                atomicOr(&st->flags, C.err);
+                atomicExch(&st->bad_cell, self);
+            }
         }
-        sl.cnt[self] = nface;
+        if constexpr (CAP::BIG) {
+            sl.ocnt[blockIdx.x] = nface;
+            sl.cnt[self] = C.err ? 0 : -(int)blockIdx.x - 1;
+        } else {
+            sl.cnt[self] = nface;
+        }
         // volume and first moment about the generator; the face kernel turns
         // the moment into the centroid (one thread per cell, off this warp)
         vol[self] = vl;
@@ -1044,23 +1200,20 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
     }
 }
 
-template <int PREC>
+template <int PREC, class CAP>
 static void launch_clip_t(const double4_32a *sorted, const float4 *sortedf, const int *start, int64_t n,
-                          const BoxDev *boxes,
-                          const int *cbox, double *vol, double *cen, Slots sl, DevStatus *st, int collect,
-                          int warps, int cand_cap, cudaStream_t s)
+                          const BoxDev *boxes, const int *cbox, double *vol, double *cen, Slots sl, DevStatus *st,
+                          int collect, int warps, int cand_cap, int64_t blocks, cudaStream_t s)
 {
     static bool configured = false;  // the attribute is per function and process-wide
     if (!configured) {
-        cudaFuncSetAttribute(k_clip<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(ClipSmem<PREC>) * CLIP_MAX_WARPS));
+        cudaFuncSetAttribute(k_clip<PREC, CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(ClipSmem<PREC, CAP>) * (CAP::BIG ? 1 : CLIP_MAX_WARPS)));
         configured = true;
     }
-    const size_t smem = sizeof(ClipSmem<PREC>) * warps;
-    const int64_t nb = (n + warps - 1) / warps;
-    k_clip<PREC><<<(unsigned)nb, 32 * warps, smem, s>>>(sorted, sortedf, start, n, boxes, cbox, vol, cen, sl, st,
-                                                         collect,
-                                                         cand_cap);
+    const size_t smem = sizeof(ClipSmem<PREC, CAP>) * warps;
+    k_clip<PREC, CAP><<<(unsigned)blocks, 32 * warps, smem, s>>>(sorted, sortedf, start, n, boxes, cbox, vol, cen,
+                                                                 sl, st, collect, cand_cap);
 }
 
 void launch_clip(const double4_32a *sorted, const float4 *sortedf, const int *start, int64_t n, const BoxDev *boxes,
@@ -1070,8 +1223,23 @@ void launch_clip(const double4_32a *sorted, const float4 *sortedf, const int *st
 {
     warps = warps < 1 ? 1 : (warps > CLIP_MAX_WARPS ? CLIP_MAX_WARPS : warps);
     cand_cap = cand_cap < 32 ? 32 : (cand_cap > CBATCH ? CBATCH : cand_cap);
-    if (precision == 0) launch_clip_t<0>(sorted, sortedf, start, n, boxes, cbox, vol, cen, sl, st, collect, warps, cand_cap, s);
-    else launch_clip_t<1>(sorted, sortedf, start, n, boxes, cbox, vol, cen, sl, st, collect, warps, cand_cap, s);
+    const int64_t nb = (n + warps - 1) / warps;
+    if (precision == 0)
+        launch_clip_t<0, CapMain>(sorted, sortedf, start, n, boxes, cbox, vol, cen, sl, st, collect, warps, cand_cap, nb, s);
+    else
+        launch_clip_t<1, CapMain>(sorted, sortedf, start, n, boxes, cbox, vol, cen, sl, st, collect, warps, cand_cap, nb, s);
+}
+
+void launch_clip_big(const double4_32a *sorted, const float4 *sortedf, const int *start, int64_t n,
+                     const BoxDev *boxes, const int *cbox, int precision, int collect, int cand_cap, double *vol,
+                     double *cen, Slots sl, DevStatus *st, cudaStream_t s)
+{
+    if (sl.orows < 1) return;
+    cand_cap = cand_cap < 32 ? 32 : (cand_cap > CBATCH ? CBATCH : cand_cap);
+    if (precision == 0)
+        launch_clip_t<0, CapBig>(sorted, sortedf, start, n, boxes, cbox, vol, cen, sl, st, collect, 1, cand_cap, sl.orows, s);
+    else
+        launch_clip_t<1, CapBig>(sorted, sortedf, start, n, boxes, cbox, vol, cen, sl, st, collect, 1, cand_cap, sl.orows, s);
 }
 
 }  // namespace mm

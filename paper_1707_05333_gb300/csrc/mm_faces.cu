@@ -11,46 +11,114 @@
 
 namespace mm {
 
-static_assert(MAXF % 4 == 0, "slot rows are read as int4");
+static_assert(MAXF % 4 == 0 && MAXF_BIG % 4 == 0, "slot rows are read as int4");
+static_assert(MAXF <= 64 && MAXF_BIG <= 128, "face masks hold one word per 64 slots, at most two");
+
+// The face slots of one cell: its row of the main slot arrays, or, for a
+// cell the large clipper re-clipped, its overflow row.
+struct Row {
+    const int *nb;
+    const unsigned char *sh;
+    const double *area, *fc;
+    int64_t base, fstride;  // first slot; row stride of the [3][.] centroid array
+    int cnt, orow;          // faces; overflow row or -1
+};
+
+__device__ __forceinline__ Row row_of(const Slots &sl, int64_t n, int64_t i)
+{
+    Row r;
+    const int c = sl.cnt[i];
+    if (c >= 0) {
+        r.nb = sl.nb; r.sh = sl.sh; r.area = sl.area; r.fc = sl.fc;
+        r.base = i * MAXF;
+        r.fstride = n * (int64_t)MAXF;
+        r.cnt = c;
+        r.orow = -1;
+    } else {
+        const int k = -c - 1;
+        r.nb = sl.onb; r.sh = sl.osh; r.area = sl.oarea; r.fc = sl.ofc;
+        r.base = (int64_t)k * MAXF_BIG;
+        r.fstride = sl.orows * (int64_t)MAXF_BIG;
+        r.cnt = sl.ocnt[k];
+        r.orow = k;
+    }
+    return r;
+}
+
+// Number of set bits of the two-word mask below bit k.
+__device__ __forceinline__ int popc_below(unsigned long long m0, unsigned long long m1, int k)
+{
+    if (k < 64) return __popcll(m0 & ((1ull << k) - 1ull));
+    return __popcll(m0) + __popcll(m1 & ((1ull << (k - 64)) - 1ull));
+}
+
+// The slot of row (nb, sh) holding neighbour i seen through image `want`, or
+// -1; the row's ids are read four at a time (rows are 16-byte aligned).
+__device__ __forceinline__ int find_partner(const int *nb, const unsigned char *sh, int cnt, int i, int want)
+{
+    int m = -1;
+    const int4 *row = reinterpret_cast<const int4 *>(nb);
+    for (int t0 = 0; t0 < cnt && m < 0; t0 += 4) {
+        const int4 v = row[t0 >> 2];
+        const int c4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int t = t0 + a;
+            if (m < 0 && t < cnt && c4[a] == i && sh[t] == want) m = t;
+        }
+    }
+    return m;
+}
 
 // Per cell: find the partner slot of each face in the neighbour's list,
-// then mark which faces are confirmed and which this cell stores.
-__global__ void k_face_confirm(int64_t n, Slots sl, unsigned long long *__restrict__ emit_mask,
+// then mark which faces are confirmed and which this cell stores.  A cell in
+// an overflow row keeps two mask words there; the low word also goes to the
+// per-cell mask, which is all a neighbour's partner slot below 64 needs.
+__global__ void k_face_confirm(int64_t n, Slots sl, OvfFaces ov, unsigned long long *__restrict__ emit_mask,
                                unsigned long long *__restrict__ conf_mask, signed char *__restrict__ partner,
                                int *__restrict__ emit_cnt, int *__restrict__ conf_cnt)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int cnt = sl.cnt[i];
-    unsigned long long em = 0, cm = 0;
-    for (int k = 0; k < cnt; ++k) {
-        const int64_t s = i * MAXF + k;
-        const int j = sl.nb[s];
-        const int code = sl.sh[s];
+    const Row r = row_of(sl, n, i);
+    signed char *const part = r.orow < 0 ? partner : ov.partner;
+    unsigned long long em0 = 0, cm0 = 0, em1 = 0, cm1 = 0;
+    for (int k = 0; k < r.cnt; ++k) {
+        const int64_t s = r.base + k;
+        const int j = r.nb[s];
+        const int code = r.sh[s];
         const int want = 26 - code;  // the mirrored image seen from j
         const int cj = sl.cnt[j];
-        int m = -1;
-        // the neighbour's slots four at a time (rows of MAXF ints are 16-byte aligned)
-        const int4 *row = reinterpret_cast<const int4 *>(sl.nb + (int64_t)j * MAXF);
-        for (int t0 = 0; t0 < cj && m < 0; t0 += 4) {
-            const int4 q = row[t0 >> 2];
-            const int c4[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                const int t = t0 + a;
-                if (m < 0 && t < cj && c4[a] == (int)i && sl.sh[(int64_t)j * MAXF + t] == want) m = t;
+        int m;
+        if (cj >= 0) {
+            m = find_partner(sl.nb + (int64_t)j * MAXF, sl.sh + (int64_t)j * MAXF, cj, (int)i, want);
+        } else {
+            const int64_t ob = (int64_t)(-cj - 1) * MAXF_BIG;
+            m = find_partner(sl.onb + ob, sl.osh + ob, sl.ocnt[-cj - 1], (int)i, want);
+        }
+        part[s] = (signed char)m;
+        if (m >= 0) {
+            const unsigned long long bit = 1ull << (k & 63);
+            const bool mine = i < j || (i == j && code > 13);
+            if (k < 64) {
+                cm0 |= bit;
+                if (mine) em0 |= bit;
+            } else {
+                cm1 |= bit;
+                if (mine) em1 |= bit;
             }
         }
-        partner[s] = (signed char)m;
-        if (m >= 0) {
-            cm |= 1ull << k;
-            if (i < j || (i == j && code > 13)) em |= 1ull << k;
-        }
     }
-    emit_mask[i] = em;
-    conf_mask[i] = cm;
-    emit_cnt[i] = __popcll(em);
-    conf_cnt[i] = __popcll(cm);
+    emit_mask[i] = em0;
+    conf_mask[i] = cm0;
+    if (r.orow >= 0) {
+        ov.emit[2 * r.orow] = em0;
+        ov.emit[2 * r.orow + 1] = em1;
+        ov.conf[2 * r.orow] = cm0;
+        ov.conf[2 * r.orow + 1] = cm1;
+    }
+    emit_cnt[i] = __popcll(em0) + __popcll(em1);
+    conf_cnt[i] = __popcll(cm0) + __popcll(cm1);
 }
 
 // One warp per cell, one lane per face slot: the slot rows are read and the
@@ -58,7 +126,7 @@ __global__ void k_face_confirm(int64_t n, Slots sl, unsigned long long *__restri
 // addresses.  Each slot knows its place in the face and incidence lists from
 // the masks, so the results do not depend on the schedule.
 __global__ void k_face_write(int64_t n, const double *__restrict__ pos, const BoxDev *__restrict__ boxes,
-                             const int *__restrict__ cbox, Slots sl,
+                             const int *__restrict__ cbox, Slots sl, OvfFaces ov,
                              const unsigned long long *__restrict__ emit_mask,
                              const unsigned long long *__restrict__ conf_mask,
                              const signed char *__restrict__ partner, const int *__restrict__ face_off,
@@ -86,18 +154,23 @@ __global__ void k_face_write(int64_t n, const double *__restrict__ pos, const Bo
         if (lane == 0) atomicOr(&st->flags, ST_ECAP_MESH);
         return;
     }
-    const unsigned long long em = emit_mask[i], cm = conf_mask[i];
+    const Row r = row_of(sl, n, i);
+    const unsigned long long em0 = emit_mask[i], cm0 = conf_mask[i];
+    unsigned long long em1 = 0, cm1 = 0;
+    if (r.orow >= 0) {
+        em1 = ov.emit[2 * r.orow + 1];
+        cm1 = ov.conf[2 * r.orow + 1];
+    }
     const int fbase = face_off[i], e0 = inc_off[i];
-    const int64_t ns = n * (int64_t)MAXF;
-    const int kend = 64 - __clzll((long long)cm);
+    const int kend = cm1 ? 128 - __clzll((long long)cm1) : 64 - __clzll((long long)cm0);
     for (int k = lane; k < kend; k += 32) {
-        if (!((cm >> k) & 1ull)) continue;
-        const int e = e0 + __popcll(cm & ((1ull << k) - 1ull));
-        const int64_t s = i * MAXF + k;
-        const int j = sl.nb[s];
-        const int code = sl.sh[s];
-        if ((em >> k) & 1ull) {
-            const int f = fbase + __popcll(em & ((1ull << k) - 1ull));
+        if (!(((k < 64 ? cm0 : cm1) >> (k & 63)) & 1ull)) continue;
+        const int e = e0 + popc_below(cm0, cm1, k);
+        const int64_t s = r.base + k;
+        const int j = r.nb[s];
+        const int code = r.sh[s];
+        if ((((k < 64 ? em0 : em1) >> (k & 63)) & 1ull)) {
+            const int f = fbase + popc_below(em0, em1, k);
             if (f < fcap) {
                 // image offsets -L, 0, +L by selection (no FP64 arithmetic)
                 const int cx = code % 3, cy = (code / 3) % 3, cz = code / 9;
@@ -111,32 +184,38 @@ __global__ void k_face_write(int64_t n, const double *__restrict__ pos, const Bo
                 face_i[f] = (int)i;
                 face_j[f] = j;
                 face_shift[f] = code;
-                face_area[f] = sl.area[s];
+                face_area[f] = r.area[s];
                 face_normal[f] = qx * inv;
                 face_normal[fcap + f] = qy * inv;
                 face_normal[2 * fcap + f] = qz * inv;
-                face_cen[f] = pix + sl.fc[s];  // the slots hold it relative to the generator
-                face_cen[fcap + f] = piy + sl.fc[ns + s];
-                face_cen[2 * fcap + f] = piz + sl.fc[2 * ns + s];
+                face_cen[f] = pix + r.fc[s];  // the slots hold it relative to the generator
+                face_cen[fcap + f] = piy + r.fc[r.fstride + s];
+                face_cen[2 * fcap + f] = piz + r.fc[2 * r.fstride + s];
             }
             inc_face[e] = f;
         } else {
-            const int m = partner[s];
-            const unsigned long long ej = emit_mask[j];
-            const int f = face_off[j] + __popcll(ej & ((1ull << m) - 1ull));
-            inc_face[e] = ~f;
+            const int m = (r.orow < 0 ? partner : ov.partner)[s];
+            int pre;
+            if (m < 64) {
+                pre = __popcll(emit_mask[j] & ((1ull << m) - 1ull));
+            } else {  // a slot of the second word: j's faces are in an overflow row
+                const int kj = -sl.cnt[j] - 1;
+                pre = popc_below(ov.emit[2 * kj], ov.emit[2 * kj + 1], m);
+            }
+            inc_face[e] = ~(face_off[j] + pre);
         }
     }
 }
 
-void launch_face_confirm(int64_t n, Slots sl, unsigned long long *emit_mask, unsigned long long *conf_mask,
-                         signed char *partner, int *emit_cnt, int *conf_cnt, cudaStream_t s)
+void launch_face_confirm(int64_t n, Slots sl, OvfFaces ov, unsigned long long *emit_mask,
+                         unsigned long long *conf_mask, signed char *partner, int *emit_cnt, int *conf_cnt,
+                         cudaStream_t s)
 {
     int nb = (int)((n + 127) / 128);
-    k_face_confirm<<<nb, 128, 0, s>>>(n, sl, emit_mask, conf_mask, partner, emit_cnt, conf_cnt);
+    k_face_confirm<<<nb, 128, 0, s>>>(n, sl, ov, emit_mask, conf_mask, partner, emit_cnt, conf_cnt);
 }
 
-void launch_face_write(int64_t n, const double *pos, const BoxDev *boxes, const int *cbox, Slots sl,
+void launch_face_write(int64_t n, const double *pos, const BoxDev *boxes, const int *cbox, Slots sl, OvfFaces ov,
                        const unsigned long long *emit_mask, const unsigned long long *conf_mask,
                        const signed char *partner, const int *face_off, const int *inc_off, int *face_i,
                        int *face_j, int *face_shift, double *face_area, double *face_normal, double *face_cen,
@@ -144,7 +223,7 @@ void launch_face_write(int64_t n, const double *pos, const BoxDev *boxes, const 
                        cudaStream_t s)
 {
     const int nb = (int)((n + 3) / 4);  // four cells (warps) per block
-    k_face_write<<<nb, 128, 0, s>>>(n, pos, boxes, cbox, sl, emit_mask, conf_mask, partner, face_off, inc_off,
+    k_face_write<<<nb, 128, 0, s>>>(n, pos, boxes, cbox, sl, ov, emit_mask, conf_mask, partner, face_off, inc_off,
                                     face_i, face_j, face_shift, face_area, face_normal, face_cen, fcap, inc_face,
                                     icap, vol, cen, st);
 }

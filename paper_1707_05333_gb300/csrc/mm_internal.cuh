@@ -14,13 +14,20 @@
 namespace mm {
 
 // Per-cell fixed capacities of the clipping kernel (Sec. 3).  A cell that
-// exceeds one reports MM_ECAPACITY for the tessellation.
+// exceeds one is clipped again by the large instance of the same kernel
+// (twice the planes, vertices and faces, 128 search rings), whose faces
+// go to an overflow row of its own; only a cell that exceeds those too
+// reports MM_ECAPACITY.
 constexpr int PMAX = 64;    // planes that ever cut the cell (6 box planes included)
 constexpr int TMAX = 128;   // vertices (triangles of the dual) alive at once
 constexpr int NSTAGE = 32;  // vertices created by one cut
 constexpr int MAXF = 48;    // faces written per cell
 constexpr int MAXRING = 48; // search rings before giving up
+constexpr int PMAX_BIG = 128, TMAX_BIG = 256, NSTAGE_BIG = 64, MAXF_BIG = 128, MAXRING_BIG = 128;
 constexpr int CLIP_MAX_WARPS = 8;  // warps (cells) per block of the clipper, tunable at run time
+// Overflow rows reserved when the count of retried cells is not known in
+// advance (graph mode); mm_tessellate sizes them to the count it reads.
+constexpr int RETRY_ROWS_FIXED = 256;
 
 // Device status word, read by the host after a tessellation.
 enum : int {
@@ -33,7 +40,10 @@ enum : int {
     ST_ECAP_RING = 64,
     ST_EDEGEN = 128,
     ST_ECAP_MESH = 256,  // more unique faces or incidences than a fixed capacity (graph mode)
+    ST_ECAP_RETRY = 512, // more retried cells than overflow rows (graph mode)
 };
+// Capacity flags that send a cell to the large clipper instead of failing.
+constexpr int ST_RETRYABLE = ST_ECAP_CAND | ST_ECAP_PLANE | ST_ECAP_TRI | ST_ECAP_STAGE | ST_ECAP_FACE | ST_ECAP_RING;
 
 struct DevStatus {
     int flags;
@@ -45,6 +55,7 @@ struct DevStatus {
     unsigned long long solve64;  // FP64 three-plane solves (51 flops)
     unsigned long long fan64;    // FP64 fan terms of the face geometry
     unsigned long long tested;   // candidates tested against the cell
+    int nretry;                  // cells sent to the large clipper
 };
 
 // One periodic box of a batch.
@@ -59,11 +70,26 @@ struct BoxDev {
 };
 
 struct Slots {         // per-cell face slots written by the clipper
-    int *cnt;          // [n]
+    int *cnt;          // [n]: faces in the cell's row; -(k+1): they are in overflow row k
     int *nb;           // [n*MAXF]
     unsigned char *sh; // [n*MAXF] shift code
     double *area;      // [n*MAXF]
     double *fc;        // [3][n*MAXF] face centroid relative to the generator
+    // overflow rows of the cells retried by the large clipper, MAXF_BIG slots each
+    int64_t orows;      // rows reserved
+    int *ocnt;          // [orows] faces in the row
+    int *onb;           // [orows*MAXF_BIG]
+    unsigned char *osh; // [orows*MAXF_BIG]
+    double *oarea;      // [orows*MAXF_BIG]
+    double *ofc;        // [3][orows*MAXF_BIG]
+    int *retry;         // [n] binned indices of the retried cells, in the order they were found
+};
+
+// Face confirmation state of the overflow rows: two mask words and a partner
+// slot per overflow slot (the main rows use the per-cell masks and partners).
+struct OvfFaces {
+    unsigned long long *emit, *conf;  // [2*orows]
+    signed char *partner;             // [orows*MAXF_BIG]
 };
 
 // kernels' host launchers (stream-ordered, no syncs)
@@ -79,14 +105,22 @@ void launch_scan(const int *in, int *out, int64_t n, int *tmp, cudaStream_t s);
 
 // vol receives each cell's volume and cen its first moment about the
 // generator ([3][n]); launch_face_write turns the moment into the centroid.
+// The main clipper (every cell, fixed capacities; a cell over a capacity is
+// appended to sl.retry) and the large clipper (the cells of sl.retry, their
+// faces to the overflow rows; a launch of sl.orows warps handles the first
+// min(nretry, orows) of them and flags the rest).
 void launch_clip(const double4_32a *sorted, const float4 *sortedf, const int *start, int64_t n, const BoxDev *boxes,
                  const int *cbox,
                  int precision, int collect, int warps, int cand_cap, double *vol, double *cen, Slots sl,
                  DevStatus *st, cudaStream_t s);
+void launch_clip_big(const double4_32a *sorted, const float4 *sortedf, const int *start, int64_t n,
+                     const BoxDev *boxes, const int *cbox, int precision, int collect, int cand_cap, double *vol,
+                     double *cen, Slots sl, DevStatus *st, cudaStream_t s);
 
-void launch_face_confirm(int64_t n, Slots sl, unsigned long long *emit_mask, unsigned long long *conf_mask,
-                         signed char *partner, int *emit_cnt, int *conf_cnt, cudaStream_t s);
-void launch_face_write(int64_t n, const double *pos, const BoxDev *boxes, const int *cbox, Slots sl,
+void launch_face_confirm(int64_t n, Slots sl, OvfFaces ov, unsigned long long *emit_mask,
+                         unsigned long long *conf_mask, signed char *partner, int *emit_cnt, int *conf_cnt,
+                         cudaStream_t s);
+void launch_face_write(int64_t n, const double *pos, const BoxDev *boxes, const int *cbox, Slots sl, OvfFaces ov,
                        const unsigned long long *emit_mask, const unsigned long long *conf_mask,
                        const signed char *partner, const int *face_off, const int *inc_off,
                        int *face_i, int *face_j, int *face_shift, double *face_area, double *face_normal,
