@@ -39,7 +39,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n-side", type=int, default=256, help="shear layer generators per axis")
-    p.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    p.add_argument("--precision", choices=["fp64", "mixed"], default=None,
+                   help="default: fp64 for the shear layer, mixed for the ensemble")
     p.add_argument("--clip-filter", type=int, choices=[0, 1], default=1,
                    help="1: FP32-filtered clipping with exact FP64 fallback (same mesh bit for bit)")
     p.add_argument("--e2e-steps", type=int, default=3)
@@ -268,7 +269,8 @@ def run_reference(args, world, rank):
         rates.append(rate)
     value = statistics.mean(rates)
     sample = (f"shear-layer recipe at {side}^3 generators, whole oracle step, {procs} concurrent replicas "
-              f"(one thread each), {args.steps} x ~{per_step:.0f} s")
+              f"(one thread each), {args.steps} x ~{per_step:.0f} s; the per-cell rate stands for the "
+              f"{args.n_side}^3 box (same recipe, the oracle's work per cell does not depend on the box size)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * (side ** 3) / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -563,6 +565,7 @@ def run_ensemble(args, world, rank, local):
     per-box timesteps and conserved totals gathered once at the end.  value =
     all ranks' cells per step / the slowest rank's time (strong scaling: the
     batch is fixed).  Mixed precision unless --precision fp64."""
+    args.precision = args.precision or "mixed"
     import numpy as np
     import torch
     from paper_1707_05333_gb300 import build as B
@@ -700,6 +703,7 @@ def run_ours(args, world, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     B.build()
+    args.precision = args.precision or "fp64"
     w = WL.shear_layer(args.n_side)
     prec = 0 if args.precision == "fp64" else 1
     # clipper settings tuned on the same recipe at half the side (untimed)
@@ -823,7 +827,9 @@ def run_ours(args, world, rank, local):
         cpu = {"value": rate, "unit": UNIT, "cores": procs, "kind": "oracle",
                "sample": f"shear-layer recipe at {args.cpu_sample_side}^3 generators, whole oracle steps: "
                          f"{procs} concurrent replicas (one thread each, {steps} steps in about "
-                         f"{args.cpu_seconds / 2:.0f} s)",
+                         f"{args.cpu_seconds / 2:.0f} s); the per-cell rate stands for the "
+                         f"{args.n_side}^3 box (same recipe and spacing statistics, the oracle's work per "
+                         f"cell does not depend on the box size)",
                "single_thread": {"value": r1, "steps": steps1, "seconds": round(el1, 1)}}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
