@@ -90,3 +90,58 @@ def test_batched_mesh_is_the_union_of_the_boxes(oracle):
     bj = np.searchsorted(off, G["face_j"], side="right") - 1
     assert np.array_equal(bi, bj)
     H.check_incidence(G)
+
+
+def test_ensemble_split_across_ranks_equals_one_batch():
+    """The multi-GPU split of an ensemble (whole boxes per rank, chosen by
+    cost; paper_1707_05333_gb300/ensemble.py), run here as one batch per
+    "rank" on the same GPU one after the other: every box's charges,
+    positions and timestep equal those of one batch over all boxes, bit for
+    bit, and the gathered per-box table matches."""
+    import torch
+    from paper_1707_05333_gb300 import binding
+    from paper_1707_05333_gb300 import ensemble as E
+    sizes = [300, 1200, 450, 2048, 64, 777, 1500]
+    boxes = [WL.ensemble_box(b, n) for b, n in enumerate(sizes)]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = binding.Context(stream=stream, gamma=5.0 / 3.0, cfl=0.3, limiter=1, precision=1)
+        Us = []
+        for wb in boxes:
+            pb = torch.tensor(wb.pos.T.copy(), dtype=torch.float64, device="cuda")
+            mb = ctx.mm_tessellate(pb, wb.box)
+            Us.append(ctx.mm_prims_to_charges(mb, torch.tensor(wb.rho, device="cuda"),
+                                              torch.tensor(wb.vel.T.copy(), device="cuda"),
+                                              torch.tensor(wb.pres, device="cuda")))
+
+        def batch(ids):
+            c = binding.Context(stream=stream, gamma=5.0 / 3.0, cfl=0.3, limiter=1, precision=1)
+            pos = torch.tensor(np.concatenate([boxes[b].pos for b in ids]).T.copy(), dtype=torch.float64,
+                               device="cuda")
+            U = torch.cat([Us[b] for b in ids], dim=1).contiguous()
+            off = E.offsets([sizes[b] for b in ids])
+            dt = torch.empty(len(ids), dtype=torch.float64, device="cuda")
+            for _ in range(2):
+                c.mm_step_batched(pos, U, off, np.ones((len(ids), 3)), dt_out=dt)
+            c.mm_sync_status()
+            out = {}
+            for k, b in enumerate(ids):
+                lo, hi = off[k], off[k + 1]
+                out[b] = (pos[:, lo:hi].clone(), U[:, lo:hi].clone(), float(dt[k].item()))
+            c.close()
+            return out
+
+        whole = batch(list(range(len(sizes))))
+        parts = E.partition_boxes(sizes, 3)
+        E.check_partition(parts, len(sizes))
+        split = {}
+        for p in parts:
+            split.update(batch([int(b) for b in p]))
+        ctx.close()
+    for b in range(len(sizes)):
+        assert torch.equal(whole[b][0], split[b][0]) and torch.equal(whole[b][1], split[b][1]), b
+        assert whole[b][2] == split[b][2], b
+    # the gathered table (one process here) is the per-box rows in box order
+    rows = np.array([[split[b][2]] + split[b][1].sum(dim=1).cpu().tolist() for b in range(len(sizes))])
+    table = E.gather_box_results(len(sizes), np.arange(len(sizes)), rows)
+    np.testing.assert_array_equal(table, rows)
