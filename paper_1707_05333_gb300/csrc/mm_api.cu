@@ -465,7 +465,7 @@ static mm_status tess_enqueue(mm_ctx *c, const double *pos, bool fixed)
     };
     auto ovf = [c]() {
         return OvfFaces{P<unsigned long long>(c->o_emit), P<unsigned long long>(c->o_conf),
-                        P<signed char>(c->o_partner)};
+                        P<signed char>(c->o_partner), &c->st->nretry};
     };
     Slots sl = slots();
     const int prec = c->cfg.clip_filter ? 1 : 0;

@@ -74,14 +74,21 @@ __device__ __forceinline__ int find_partner(const int *nb, const unsigned char *
 // then mark which faces are confirmed and which this cell stores.  A cell in
 // an overflow row keeps two mask words there; the low word also goes to the
 // per-cell mask, which is all a neighbour's partner slot below 64 needs.
-__global__ void k_face_confirm(int64_t n, Slots sl, OvfFaces ov, unsigned long long *__restrict__ emit_mask,
-                               unsigned long long *__restrict__ conf_mask, signed char *__restrict__ partner,
-                               int *__restrict__ emit_cnt, int *__restrict__ conf_cnt)
+// OVF false: no cell was re-clipped, every row is a main row.
+template <bool OVF>
+__device__ __forceinline__ void face_confirm_cell(int64_t n, int64_t i, const Slots &sl, const OvfFaces &ov,
+                                                  unsigned long long *__restrict__ emit_mask,
+                                                  unsigned long long *__restrict__ conf_mask,
+                                                  signed char *__restrict__ partner, int *__restrict__ emit_cnt,
+                                                  int *__restrict__ conf_cnt)
 {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const Row r = row_of(sl, n, i);
-    signed char *const part = r.orow < 0 ? partner : ov.partner;
+    Row r;
+    if constexpr (OVF) {
+        r = row_of(sl, n, i);
+    } else {
+        r.nb = sl.nb; r.sh = sl.sh; r.base = i * MAXF; r.cnt = sl.cnt[i]; r.orow = -1;
+    }
+    signed char *const part = (!OVF || r.orow < 0) ? partner : ov.partner;
     unsigned long long em0 = 0, cm0 = 0, em1 = 0, cm1 = 0;
     for (int k = 0; k < r.cnt; ++k) {
         const int64_t s = r.base + k;
@@ -90,7 +97,7 @@ __global__ void k_face_confirm(int64_t n, Slots sl, OvfFaces ov, unsigned long l
         const int want = 26 - code;  // the mirrored image seen from j
         const int cj = sl.cnt[j];
         int m;
-        if (cj >= 0) {
+        if (!OVF || cj >= 0) {
             m = find_partner(sl.nb + (int64_t)j * MAXF, sl.sh + (int64_t)j * MAXF, cj, (int)i, want);
         } else {
             const int64_t ob = (int64_t)(-cj - 1) * MAXF_BIG;
@@ -100,7 +107,7 @@ __global__ void k_face_confirm(int64_t n, Slots sl, OvfFaces ov, unsigned long l
         if (m >= 0) {
             const unsigned long long bit = 1ull << (k & 63);
             const bool mine = i < j || (i == j && code > 13);
-            if (k < 64) {
+            if (!OVF || k < 64) {
                 cm0 |= bit;
                 if (mine) em0 |= bit;
             } else {
@@ -111,14 +118,97 @@ __global__ void k_face_confirm(int64_t n, Slots sl, OvfFaces ov, unsigned long l
     }
     emit_mask[i] = em0;
     conf_mask[i] = cm0;
-    if (r.orow >= 0) {
+    if (OVF && r.orow >= 0) {
         ov.emit[2 * r.orow] = em0;
         ov.emit[2 * r.orow + 1] = em1;
         ov.conf[2 * r.orow] = cm0;
         ov.conf[2 * r.orow + 1] = cm1;
     }
-    emit_cnt[i] = __popcll(em0) + __popcll(em1);
-    conf_cnt[i] = __popcll(cm0) + __popcll(cm1);
+    emit_cnt[i] = __popcll(em0) + (OVF ? __popcll(em1) : 0);
+    conf_cnt[i] = __popcll(cm0) + (OVF ? __popcll(cm1) : 0);
+}
+
+__global__ void k_face_confirm(int64_t n, Slots sl, OvfFaces ov, unsigned long long *__restrict__ emit_mask,
+                               unsigned long long *__restrict__ conf_mask, signed char *__restrict__ partner,
+                               int *__restrict__ emit_cnt, int *__restrict__ conf_cnt)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (*ov.nretry == 0) face_confirm_cell<false>(n, i, sl, ov, emit_mask, conf_mask, partner, emit_cnt, conf_cnt);
+    else face_confirm_cell<true>(n, i, sl, ov, emit_mask, conf_mask, partner, emit_cnt, conf_cnt);
+}
+
+// The face records and incidences of cell i's confirmed slots, one lane per
+// slot (OVF false: no cell was re-clipped, every row is a main row).
+template <bool OVF>
+__device__ __forceinline__ void face_write_slots(int64_t n, int64_t i, int lane, double pix, double piy, double piz,
+                                                 const double *L, const double *__restrict__ pos, const Slots &sl,
+                                                 const OvfFaces &ov, const unsigned long long *__restrict__ emit_mask,
+                                                 const unsigned long long *__restrict__ conf_mask,
+                                                 const signed char *__restrict__ partner,
+                                                 const int *__restrict__ face_off, const int *__restrict__ inc_off,
+                                                 int *__restrict__ face_i, int *__restrict__ face_j,
+                                                 int *__restrict__ face_shift, double *__restrict__ face_area,
+                                                 double *__restrict__ face_normal, double *__restrict__ face_cen,
+                                                 int64_t fcap, int *__restrict__ inc_face)
+{
+    Row r;
+    if constexpr (OVF) {
+        r = row_of(sl, n, i);
+    } else {
+        r.nb = sl.nb; r.sh = sl.sh; r.area = sl.area; r.fc = sl.fc;
+        r.base = i * MAXF; r.fstride = n * (int64_t)MAXF; r.orow = -1;
+    }
+    const unsigned long long em0 = emit_mask[i], cm0 = conf_mask[i];
+    unsigned long long em1 = 0, cm1 = 0;
+    if (OVF && r.orow >= 0) {
+        em1 = ov.emit[2 * r.orow + 1];
+        cm1 = ov.conf[2 * r.orow + 1];
+    }
+    const int fbase = face_off[i], e0 = inc_off[i];
+    const int kend = cm1 ? 128 - __clzll((long long)cm1) : 64 - __clzll((long long)cm0);
+    for (int k = lane; k < kend; k += 32) {
+        if (!(((k < 64 ? cm0 : cm1) >> (k & 63)) & 1ull)) continue;
+        const int e = e0 + (OVF ? popc_below(cm0, cm1, k) : __popcll(cm0 & ((1ull << k) - 1ull)));
+        const int64_t s = r.base + k;
+        const int j = r.nb[s];
+        const int code = r.sh[s];
+        if ((((k < 64 ? em0 : em1) >> (k & 63)) & 1ull)) {
+            const int f = fbase + (OVF ? popc_below(em0, em1, k) : __popcll(em0 & ((1ull << k) - 1ull)));
+            if (f < fcap) {
+                // image offsets -L, 0, +L by selection (no FP64 arithmetic)
+                const int cx = code % 3, cy = (code / 3) % 3, cz = code / 9;
+                const double ox = cx == 1 ? 0.0 : (cx == 2 ? L[0] : -L[0]);
+                const double oy = cy == 1 ? 0.0 : (cy == 2 ? L[1] : -L[1]);
+                const double oz = cz == 1 ? 0.0 : (cz == 2 ? L[2] : -L[2]);
+                const double qx = pos[j] + ox - pix;
+                const double qy = pos[n + j] + oy - piy;
+                const double qz = pos[2 * n + j] + oz - piz;
+                const double inv = rsqrt(qx * qx + qy * qy + qz * qz);
+                face_i[f] = (int)i;
+                face_j[f] = j;
+                face_shift[f] = code;
+                face_area[f] = r.area[s];
+                face_normal[f] = qx * inv;
+                face_normal[fcap + f] = qy * inv;
+                face_normal[2 * fcap + f] = qz * inv;
+                face_cen[f] = pix + r.fc[s];  // the slots hold it relative to the generator
+                face_cen[fcap + f] = piy + r.fc[r.fstride + s];
+                face_cen[2 * fcap + f] = piz + r.fc[2 * r.fstride + s];
+            }
+            inc_face[e] = f;
+        } else {
+            const int m = ((!OVF || r.orow < 0) ? partner : ov.partner)[s];
+            int pre;
+            if (!OVF || m < 64) {
+                pre = __popcll(emit_mask[j] & ((1ull << m) - 1ull));
+            } else {  // a slot of the second word: j's faces are in an overflow row
+                const int kj = -sl.cnt[j] - 1;
+                pre = popc_below(ov.emit[2 * kj], ov.emit[2 * kj + 1], m);
+            }
+            inc_face[e] = ~(face_off[j] + pre);
+        }
+    }
 }
 
 // One warp per cell, one lane per face slot: the slot rows are read and the
@@ -154,57 +244,12 @@ __global__ void k_face_write(int64_t n, const double *__restrict__ pos, const Bo
         if (lane == 0) atomicOr(&st->flags, ST_ECAP_MESH);
         return;
     }
-    const Row r = row_of(sl, n, i);
-    const unsigned long long em0 = emit_mask[i], cm0 = conf_mask[i];
-    unsigned long long em1 = 0, cm1 = 0;
-    if (r.orow >= 0) {
-        em1 = ov.emit[2 * r.orow + 1];
-        cm1 = ov.conf[2 * r.orow + 1];
-    }
-    const int fbase = face_off[i], e0 = inc_off[i];
-    const int kend = cm1 ? 128 - __clzll((long long)cm1) : 64 - __clzll((long long)cm0);
-    for (int k = lane; k < kend; k += 32) {
-        if (!(((k < 64 ? cm0 : cm1) >> (k & 63)) & 1ull)) continue;
-        const int e = e0 + popc_below(cm0, cm1, k);
-        const int64_t s = r.base + k;
-        const int j = r.nb[s];
-        const int code = r.sh[s];
-        if ((((k < 64 ? em0 : em1) >> (k & 63)) & 1ull)) {
-            const int f = fbase + popc_below(em0, em1, k);
-            if (f < fcap) {
-                // image offsets -L, 0, +L by selection (no FP64 arithmetic)
-                const int cx = code % 3, cy = (code / 3) % 3, cz = code / 9;
-                const double ox = cx == 1 ? 0.0 : (cx == 2 ? L[0] : -L[0]);
-                const double oy = cy == 1 ? 0.0 : (cy == 2 ? L[1] : -L[1]);
-                const double oz = cz == 1 ? 0.0 : (cz == 2 ? L[2] : -L[2]);
-                const double qx = pos[j] + ox - pix;
-                const double qy = pos[n + j] + oy - piy;
-                const double qz = pos[2 * n + j] + oz - piz;
-                const double inv = rsqrt(qx * qx + qy * qy + qz * qz);
-                face_i[f] = (int)i;
-                face_j[f] = j;
-                face_shift[f] = code;
-                face_area[f] = r.area[s];
-                face_normal[f] = qx * inv;
-                face_normal[fcap + f] = qy * inv;
-                face_normal[2 * fcap + f] = qz * inv;
-                face_cen[f] = pix + r.fc[s];  // the slots hold it relative to the generator
-                face_cen[fcap + f] = piy + r.fc[r.fstride + s];
-                face_cen[2 * fcap + f] = piz + r.fc[2 * r.fstride + s];
-            }
-            inc_face[e] = f;
-        } else {
-            const int m = (r.orow < 0 ? partner : ov.partner)[s];
-            int pre;
-            if (m < 64) {
-                pre = __popcll(emit_mask[j] & ((1ull << m) - 1ull));
-            } else {  // a slot of the second word: j's faces are in an overflow row
-                const int kj = -sl.cnt[j] - 1;
-                pre = popc_below(ov.emit[2 * kj], ov.emit[2 * kj + 1], m);
-            }
-            inc_face[e] = ~(face_off[j] + pre);
-        }
-    }
+    if (*ov.nretry == 0)
+        face_write_slots<false>(n, i, lane, pix, piy, piz, L, pos, sl, ov, emit_mask, conf_mask, partner, face_off,
+                                inc_off, face_i, face_j, face_shift, face_area, face_normal, face_cen, fcap, inc_face);
+    else
+        face_write_slots<true>(n, i, lane, pix, piy, piz, L, pos, sl, ov, emit_mask, conf_mask, partner, face_off,
+                               inc_off, face_i, face_j, face_shift, face_area, face_normal, face_cen, fcap, inc_face);
 }
 
 void launch_face_confirm(int64_t n, Slots sl, OvfFaces ov, unsigned long long *emit_mask,

@@ -90,6 +90,7 @@ struct Slots {         // per-cell face slots written by the clipper
 struct OvfFaces {
     unsigned long long *emit, *conf;  // [2*orows]
     signed char *partner;             // [orows*MAXF_BIG]
+    const int *nretry;                // cells re-clipped (0: no overflow row is in use)
 };
 
 // kernels' host launchers (stream-ordered, no syncs)
