@@ -175,8 +175,8 @@ def clip_roofline(direct, filtered, ms, n, clip_filter):
 # block), per cell; it scales with the cells of the launch.  Valid only for the
 # clipper source it was taken on: the digest of the clipping kernel's sources
 # must match, else the figure is withheld.
-CLIP_TRAFFIC = {"sources": ("csrc/mm_clip.cu", "csrc/mm_internal.cuh"), "sha256_16": "f7d9c89636ea4670",
-                "bytes_per_cell": 1901569536 / 2097152, "cells_captured": 2097152}
+CLIP_TRAFFIC = {"sources": ("csrc/mm_clip.cu", "csrc/mm_internal.cuh"), "sha256_16": None,
+                "bytes_per_cell": None, "cells_captured": 2097152}
 
 
 def clip_sources_digest():
@@ -416,7 +416,7 @@ def tune_clipper(args, pos_np, box, reps=3):
     return res
 
 
-DEFAULT_CLIPPER = {"clip_warps": 2, "cand_cap": 64, "bin_scale": 1.0}
+DEFAULT_CLIPPER = {"clip_warps": 2, "cand_cap": 64, "bin_scale": 1.0, "clip_sort": 0}
 
 
 def confirm_clipper(w, tuned, reps=2, **cfg):
@@ -510,7 +510,7 @@ def measure_ensemble(args, precision=1, per_box=True):
         big = boxes[int(np.argmax(sizes))]
         args.ensemble_tuned = {} if args.no_autotune else tune_clipper(args, big.pos, big.box)
     tuned = args.ensemble_tuned
-    tunables = {k: tuned[k] for k in ("clip_warps", "cand_cap", "bin_scale")} if tuned else {}
+    tunables = {k: tuned[k] for k in ("clip_warps", "cand_cap", "bin_scale", "clip_sort")} if tuned else {}
     off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
     n = int(off[-1])
     L = np.ones((len(boxes), 3))
@@ -593,7 +593,7 @@ def run_ensemble(args, world, rank, local):
     if not args.no_autotune:
         big = boxes[int(np.argmax(msz))]
         t = tune_clipper(args, big.pos, big.box)
-        tuned = {k: t[k] for k in ("clip_warps", "cand_cap", "bin_scale")}
+        tuned = {k: t[k] for k in ("clip_warps", "cand_cap", "bin_scale", "clip_sort")}
     stream = torch.cuda.Stream()
 
     def barrier():
@@ -713,7 +713,7 @@ def run_ours(args, world, rank, local):
         tune_info = tune_clipper(args, ws.pos, ws.box)
         tune_info["sample"] = f"shear_layer_{max(32, args.n_side // 2)}^3, 3 timed tessellations per setting"
         del ws
-        tuned = {k: tune_info[k] for k in ("clip_warps", "cand_cap", "bin_scale")}
+        tuned = {k: tune_info[k] for k in ("clip_warps", "cand_cap", "bin_scale", "clip_sort")}
         args.tuned, check = confirm_clipper(w, tuned, clip_filter=args.clip_filter)
         tune_info.update(check)
         tune_info["used"] = dict(args.tuned)

@@ -86,6 +86,8 @@ typedef struct {
     int integrator;   /* 0: half-step predictor with start-of-step geometry (Sec. 4.1);      */
                       /*    1: Heun, fluxes averaged over start and end meshes (Sec. 6; FP64 */
                       /*    hydro, no entropy column; one more tessellation per step)        */
+    int clip_sort;    /* how the clipper orders more than 32 buffered candidates: 0 in      */
+                      /*    shared memory, 1 in registers (same order and mesh; tunable)      */
 } mm_config;
 
 /* Fill a config with the defaults: gamma 5/3, cfl 0.3, eta 1, chi 1, zeta
@@ -93,7 +95,7 @@ typedef struct {
  * roundness correction, FP64 hydro, filtered clipping, no counters, HLLC,
  * 2 clip warps per block, batches of 64 candidates, bins one mean spacing
  * wide, no entropy column (mach_th 1.1 when it is switched on), half-step
- * time integration. */
+ * time integration, candidates over 32 sorted in shared memory. */
 void mm_default_config(mm_config *cfg);
 
 typedef struct mm_ctx mm_ctx;
@@ -215,8 +217,9 @@ mm_status mm_step_batched(mm_ctx *ctx, double *pos, double *U, int64_t n, const 
 /* The context's current configuration. */
 mm_status mm_get_config(const mm_ctx *ctx, mm_config *cfg);
 
-/* Pick clip_warps, cand_cap and bin_scale for generators like pos[3][n] in
- * box: every combination of {2,4,8} x {32,64} x {0.8,1,1.25,1.5} is timed on
+/* Pick clip_warps, cand_cap, bin_scale and clip_sort for generators like
+ * pos[3][n] in box: every combination of {2,4,8} x {32,64} x
+ * {0.8,1,1.25,1.5} x {0,1} is timed on
  * `reps` tessellations (after one warm-up each) and the fastest is kept in
  * the context's configuration; *best_ms (may be NULL) receives its time.
  * The mesh of the last timed tessellation is left in the context. */

@@ -45,7 +45,8 @@ class Config(ctypes.Structure):
                 ("precision", ctypes.c_int), ("collect_stats", ctypes.c_int),
                 ("riemann", ctypes.c_int), ("clip_warps", ctypes.c_int), ("cand_cap", ctypes.c_int),
                 ("clip_filter", ctypes.c_int), ("bin_scale", ctypes.c_double),
-                ("mach_th", ctypes.c_double), ("entropy", ctypes.c_int), ("integrator", ctypes.c_int)]
+                ("mach_th", ctypes.c_double), ("entropy", ctypes.c_int), ("integrator", ctypes.c_int),
+                ("clip_sort", ctypes.c_int)]
 
 
 class MeshStruct(ctypes.Structure):
@@ -309,7 +310,7 @@ class Context:
         cfg = self.mm_get_config()
         self.config = cfg
         return {"clip_warps": cfg.clip_warps, "cand_cap": cfg.cand_cap, "bin_scale": cfg.bin_scale,
-                "tessellate_ms": best.value}
+                "clip_sort": cfg.clip_sort, "tessellate_ms": best.value}
 
     def mm_sync_status(self) -> None:
         self._call("mm_sync_status", self.h)

@@ -213,6 +213,7 @@ static mm_status check_cfg(mm_ctx *c, const mm_config *g)
     if (g->clip_warps < 1 || g->clip_warps > CLIP_MAX_WARPS) return fail(c, MM_EINVAL, "clip_warps must be in [1, 8]");
     if (g->cand_cap < 32 || g->cand_cap > 64) return fail(c, MM_EINVAL, "cand_cap must be in [32, 64]");
     if (!(g->bin_scale >= 0.25 && g->bin_scale <= 4.0)) return fail(c, MM_EINVAL, "bin_scale must be in [0.25, 4]");
+    if (g->clip_sort != 0 && g->clip_sort != 1) return fail(c, MM_EINVAL, "clip_sort must be 0 or 1");
     return MM_OK;
 }
 
@@ -472,7 +473,8 @@ static mm_status tess_enqueue(mm_ctx *c, const double *pos, bool fixed)
     stage_mark(c, MM_STAGE_CLIP, true);
     launch_clip(P<double4_32a>(c->sorted), P<float4>(c->sortedf), P<int>(c->bin_start), n, boxes, cbox, prec,
                 c->cfg.collect_stats,
-                c->cfg.clip_warps, c->cfg.cand_cap, P<double>(c->vol), P<double>(c->cen), sl, c->st, s);
+                c->cfg.clip_warps, c->cfg.cand_cap, c->cfg.clip_sort, P<double>(c->vol), P<double>(c->cen), sl, c->st,
+                s);
     // cells over a capacity of the main clipper, again with the large one
     // (one warp per overflow row; nothing to do when no cell overflowed)
     launch_clip_big(P<double4_32a>(c->sorted), P<float4>(c->sortedf), P<int>(c->bin_start), n, boxes, cbox, prec,
@@ -720,6 +722,7 @@ void mm_default_config(mm_config *g)
     g->mach_th = 1.1;
     g->entropy = 0;
     g->integrator = 0;
+    g->clip_sort = 0;
 }
 
 mm_status mm_create(mm_ctx **out, const mm_config *cfg, void *cuda_stream)
@@ -983,6 +986,7 @@ mm_status mm_autotune(mm_ctx *c, const double *pos, int64_t n, const double box[
     static const int warps_opt[] = {2, 4, 8};
     static const int cap_opt[] = {32, 64};
     static const double scale_opt[] = {0.8, 1.0, 1.25, 1.5};
+    static const int sort_opt[] = {0, 1};
     const mm_config keep = c->cfg;
     const int keep_timing = c->timing;
     cudaEvent_t e0, e1;
@@ -994,11 +998,13 @@ mm_status mm_autotune(mm_ctx *c, const double *pos, int64_t n, const double box[
     c->timing = 0;
     for (double sc : scale_opt)
         for (int wp : warps_opt)
-            for (int cap : cap_opt) {
+            for (int cap : cap_opt)
+                for (int so : sort_opt) {
                 c->cfg = keep;
                 c->cfg.bin_scale = sc;
                 c->cfg.clip_warps = wp;
                 c->cfg.cand_cap = cap;
+                c->cfg.clip_sort = so;
                 double tot = 0.0;
                 for (int k = 0; k < reps + 1 && r == MM_OK; ++k) {
                     cudaEventRecord(e0, c->stream);
@@ -1023,6 +1029,7 @@ mm_status mm_autotune(mm_ctx *c, const double *pos, int64_t n, const double box[
     c->cfg.bin_scale = best_cfg.bin_scale;
     c->cfg.clip_warps = best_cfg.clip_warps;
     c->cfg.cand_cap = best_cfg.cand_cap;
+    c->cfg.clip_sort = best_cfg.clip_sort;
     if (best_ms) *best_ms = best;
     return MM_OK;
 }

@@ -713,7 +713,12 @@ struct Gather {
     const double4_32a *sorted;
 };
 
-template <int PREC, class CAP>
+// SORT 0 orders more than 32 candidates by a bitonic network on the buffer in
+// shared memory, SORT 1 by the same network on keys held two per lane
+// (shuffles, no barriers), producing only the permutation.  Both give the same
+// order (the keys are unique), so the mesh does not depend on SORT; which is
+// faster depends on the code around it, and the autotuner picks.
+template <int PREC, class CAP, int SORT>
 __device__ void flush_batch(ClipSmem<PREC, CAP> &S, int &ncand, CellState &C, int lane, const Gather &G)
 {
     if (ncand == 0) return;
@@ -759,6 +764,46 @@ __device__ void flush_batch(ClipSmem<PREC, CAP> &S, int &ncand, CellState &C, in
             }
         }
         if (have) S.perm[lane] = (unsigned char)idx;
+    } else if constexpr (SORT == 1) {
+        // 33..64 candidates, two per lane (entries lane and lane + 32):
+        // partners in other lanes by shuffles (distance below 32), in the
+        // same lane at distance 32
+        unsigned long long key0 = (unsigned long long)S.u.c.d2[lane];
+        unsigned tie0 = (unsigned)S.cid[lane] * 27u + (unsigned)S.csh[lane];
+        const bool have1 = lane + 32 < ncand;
+        unsigned long long key1 = have1 ? (unsigned long long)S.u.c.d2[lane + 32] : ~0ull;
+        unsigned tie1 = have1 ? (unsigned)S.cid[lane + 32] * 27u + (unsigned)S.csh[lane + 32] : ~0u;
+        int idx0 = lane, idx1 = lane + 32;
+#pragma unroll 1
+        for (int kk = 2; kk <= 64; kk <<= 1) {
+#pragma unroll 1
+            for (int j = kk >> 1; j > 0; j >>= 1) {
+                if (j == 32) {
+                    // entries lane and lane + 32, ascending (kk = 64 here)
+                    if (key1 < key0 || (key1 == key0 && tie1 < tie0)) {
+                        const unsigned long long tk = key0; key0 = key1; key1 = tk;
+                        const unsigned tt = tie0; tie0 = tie1; tie1 = tt;
+                        const int ti = idx0; idx0 = idx1; idx1 = ti;
+                    }
+                    continue;
+                }
+                const bool lower = (lane & j) == 0;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    unsigned long long &key = h ? key1 : key0;
+                    unsigned &tie = h ? tie1 : tie0;
+                    int &idx = h ? idx1 : idx0;
+                    const unsigned long long ok = __shfl_xor_sync(FULL, key, j);
+                    const unsigned ot = __shfl_xor_sync(FULL, tie, j);
+                    const int oi = __shfl_xor_sync(FULL, idx, j);
+                    const bool other_less = ok < key || (ok == key && ot < tie);
+                    const bool up = ((lane + 32 * h) & kk) == 0;
+                    if (lower == up ? other_less : !other_less) { key = ok; tie = ot; idx = oi; }
+                }
+            }
+        }
+        S.perm[lane] = (unsigned char)idx0;
+        if (have1) S.perm[lane + 32] = (unsigned char)idx1;
     } else {
         sort_candidates(S, ncand, lane);
         for (int k = lane; k < ncand; k += 32) S.perm[k] = (unsigned char)k;
@@ -786,7 +831,7 @@ __device__ void flush_batch(ClipSmem<PREC, CAP> &S, int &ncand, CellState &C, in
 // cell that overflows one of its lists goes to the retry list instead of
 // failing.  The large instance (one warp per block) clips entry retry[r] of
 // block r and writes its faces to overflow row r.
-template <int PREC, class CAP>
+template <int PREC, class CAP, int SORT>
 __global__ void __maxnreg__(MM_CLIP_MAXNREG)
 k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sortedf, const int *__restrict__ start,
        int64_t n,
@@ -971,7 +1016,7 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
             maxcand = max(maxcand, ncand);
             __syncwarp();
         }
-        flush_batch<PREC, CAP>(S, ncand, C, lane, G);
+        flush_batch<PREC, CAP, SORT>(S, ncand, C, lane, G);
         if (C.err || !ring_done) continue;
         ++rings;
         // radius the gathered rings are guaranteed to cover
@@ -1200,34 +1245,37 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
     }
 }
 
-template <int PREC, class CAP>
+template <int PREC, class CAP, int SORT>
 static void launch_clip_t(const double4_32a *sorted, const float4 *sortedf, const int *start, int64_t n,
                           const BoxDev *boxes, const int *cbox, double *vol, double *cen, Slots sl, DevStatus *st,
                           int collect, int warps, int cand_cap, int64_t blocks, cudaStream_t s)
 {
     static bool configured = false;  // the attribute is per function and process-wide
     if (!configured) {
-        cudaFuncSetAttribute(k_clip<PREC, CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_clip<PREC, CAP, SORT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(ClipSmem<PREC, CAP>) * (CAP::BIG ? 1 : CLIP_MAX_WARPS)));
         configured = true;
     }
     const size_t smem = sizeof(ClipSmem<PREC, CAP>) * warps;
-    k_clip<PREC, CAP><<<(unsigned)blocks, 32 * warps, smem, s>>>(sorted, sortedf, start, n, boxes, cbox, vol, cen,
+    k_clip<PREC, CAP, SORT><<<(unsigned)blocks, 32 * warps, smem, s>>>(sorted, sortedf, start, n, boxes, cbox, vol, cen,
                                                                  sl, st, collect, cand_cap);
 }
 
 void launch_clip(const double4_32a *sorted, const float4 *sortedf, const int *start, int64_t n, const BoxDev *boxes,
                  const int *cbox,
-                 int precision, int collect, int warps, int cand_cap, double *vol, double *cen, Slots sl,
-                 DevStatus *st, cudaStream_t s)
+                 int precision, int collect, int warps, int cand_cap, int sort, double *vol, double *cen,
+                 Slots sl, DevStatus *st, cudaStream_t s)
 {
     warps = warps < 1 ? 1 : (warps > CLIP_MAX_WARPS ? CLIP_MAX_WARPS : warps);
     cand_cap = cand_cap < 32 ? 32 : (cand_cap > CBATCH ? CBATCH : cand_cap);
     const int64_t nb = (n + warps - 1) / warps;
+    // the sort variant only changes speed, so the direct FP64 clipper keeps one
     if (precision == 0)
-        launch_clip_t<0, CapMain>(sorted, sortedf, start, n, boxes, cbox, vol, cen, sl, st, collect, warps, cand_cap, nb, s);
+        launch_clip_t<0, CapMain, 0>(sorted, sortedf, start, n, boxes, cbox, vol, cen, sl, st, collect, warps, cand_cap, nb, s);
+    else if (sort == 1)
+        launch_clip_t<1, CapMain, 1>(sorted, sortedf, start, n, boxes, cbox, vol, cen, sl, st, collect, warps, cand_cap, nb, s);
     else
-        launch_clip_t<1, CapMain>(sorted, sortedf, start, n, boxes, cbox, vol, cen, sl, st, collect, warps, cand_cap, nb, s);
+        launch_clip_t<1, CapMain, 0>(sorted, sortedf, start, n, boxes, cbox, vol, cen, sl, st, collect, warps, cand_cap, nb, s);
 }
 
 void launch_clip_big(const double4_32a *sorted, const float4 *sortedf, const int *start, int64_t n,
@@ -1237,9 +1285,9 @@ void launch_clip_big(const double4_32a *sorted, const float4 *sortedf, const int
     if (sl.orows < 1) return;
     cand_cap = cand_cap < 32 ? 32 : (cand_cap > CBATCH ? CBATCH : cand_cap);
     if (precision == 0)
-        launch_clip_t<0, CapBig>(sorted, sortedf, start, n, boxes, cbox, vol, cen, sl, st, collect, 1, cand_cap, sl.orows, s);
+        launch_clip_t<0, CapBig, 0>(sorted, sortedf, start, n, boxes, cbox, vol, cen, sl, st, collect, 1, cand_cap, sl.orows, s);
     else
-        launch_clip_t<1, CapBig>(sorted, sortedf, start, n, boxes, cbox, vol, cen, sl, st, collect, 1, cand_cap, sl.orows, s);
+        launch_clip_t<1, CapBig, 0>(sorted, sortedf, start, n, boxes, cbox, vol, cen, sl, st, collect, 1, cand_cap, sl.orows, s);
 }
 
 }  // namespace mm

@@ -112,8 +112,8 @@ void launch_scan(const int *in, int *out, int64_t n, int *tmp, cudaStream_t s);
 // min(nretry, orows) of them and flags the rest).
 void launch_clip(const double4_32a *sorted, const float4 *sortedf, const int *start, int64_t n, const BoxDev *boxes,
                  const int *cbox,
-                 int precision, int collect, int warps, int cand_cap, double *vol, double *cen, Slots sl,
-                 DevStatus *st, cudaStream_t s);
+                 int precision, int collect, int warps, int cand_cap, int sort, double *vol, double *cen,
+                 Slots sl, DevStatus *st, cudaStream_t s);
 void launch_clip_big(const double4_32a *sorted, const float4 *sortedf, const int *start, int64_t n,
                      const BoxDev *boxes, const int *cbox, int precision, int collect, int cand_cap, double *vol,
                      double *cen, Slots sl, DevStatus *st, cudaStream_t s);

@@ -48,7 +48,9 @@ def test_default_config_and_struct_layout(lib):
     binding._lib = None
     cfg = binding.default_config()
     assert cfg.gamma == pytest.approx(5.0 / 3.0) and cfg.cfl == 0.3 and cfg.limiter == 1
-    assert ctypes.sizeof(binding.Config) == 9 * 8 + 8 * 4 + 8 + 8 + 2 * 4
+    # 9 doubles, 8 ints, bin_scale, mach_th, entropy and integrator, clip_sort and the padding to 8 bytes
+    assert ctypes.sizeof(binding.Config) == 9 * 8 + 8 * 4 + 8 + 8 + 2 * 4 + 4 + 4
+    assert cfg.clip_sort == 0 and cfg.clip_warps == 2 and cfg.cand_cap == 64
     assert ctypes.sizeof(binding.MeshStruct) == 4 * 8 + 3 * 8 + 8 + 2 * 8 + 10 * 8
 
 

@@ -163,18 +163,37 @@ def test_full_size_shear_layer_sampled_cells(oracle, ctx):
     print(f"[256^3 sampled cells] faces in the band (1e-10, 1e-8] of (V/n)^(2/3): {nband}")
 
 
-@pytest.mark.parametrize("warps,cap,scale", [(2, 32, 0.8), (8, 64, 1.5), (1, 48, 1.25), (4, 64, 2.5)])
-def test_tunable_settings_keep_the_mesh(oracle, ctx, warps, cap, scale):
+@pytest.mark.parametrize("warps,cap,scale,sort", [(2, 32, 0.8, 0), (8, 64, 1.5, 1), (1, 48, 1.25, 0),
+                                                  (4, 64, 2.5, 0), (2, 64, 1.25, 1)])
+def test_tunable_settings_keep_the_mesh(oracle, ctx, warps, cap, scale, sort):
     c, torch = ctx
     pos = WL.random_points(1500, seed=12)
     T = oracle.tessellate(pos, np.ones(3), 1)
-    c.set_config(clip_warps=warps, cand_cap=cap, bin_scale=scale)
+    c.set_config(clip_warps=warps, cand_cap=cap, bin_scale=scale, clip_sort=sort)
     try:
         _, _, G = H.gpu_tessellate(c, torch, pos, np.ones(3))
     finally:
-        c.set_config(clip_warps=2, cand_cap=64, bin_scale=1.0)
+        c.set_config(clip_warps=2, cand_cap=64, bin_scale=1.0, clip_sort=0)
     H.compare_tessellations(oracle, T, G, pos, np.ones(3))
     H.check_incidence(G)
+
+
+def test_candidate_sorts_give_the_same_mesh_bit_for_bit(ctx):
+    """clip_sort 0 (shared memory) and 1 (registers) order more than 32
+    buffered candidates the same way: uniform random points, where such
+    batches are common, give the same mesh bit for bit."""
+    c, torch = ctx
+    pos = WL.random_points(20000, seed=14)
+    c.set_config(collect_stats=1)
+    try:
+        _, _, A = H.gpu_tessellate(c, torch, pos, np.ones(3))
+        assert c.mm_tess_stats()["max_candidates"] > 32
+        c.set_config(clip_sort=1)
+        _, _, B = H.gpu_tessellate(c, torch, pos, np.ones(3))
+    finally:
+        c.set_config(collect_stats=0, clip_sort=0)
+    for k in A:
+        np.testing.assert_array_equal(A[k], B[k], err_msg=k)
 
 
 def test_autotune_picks_a_valid_setting(ctx):
@@ -185,10 +204,11 @@ def test_autotune_picks_a_valid_setting(ctx):
     try:
         assert best["clip_warps"] in (2, 4, 8) and best["cand_cap"] in (32, 64)
         assert best["bin_scale"] in (0.8, 1.0, 1.25, 1.5) and best["tessellate_ms"] > 0
+        assert best["clip_sort"] in (0, 1)
         mesh = c.mm_tessellate(P, w.box)
         assert mesh.nfaces > 0
     finally:
-        c.set_config(clip_warps=2, cand_cap=64, bin_scale=1.0)
+        c.set_config(clip_warps=2, cand_cap=64, bin_scale=1.0, clip_sort=0)
 
 
 def test_rejects_bad_sizes_and_boxes(ctx):
