@@ -208,21 +208,31 @@ def test_full_size_shear_layer_step_properties(gpu):
     assert 0 < float(dt.item()) < 1e-2
 
 
-def test_full_size_shear_layer_sampled_cells_match_oracle(oracle, gpu):
-    """The bench workload (256^3 generators, FP64 path, S10 limiter): one
-    whole step on the device against the oracle on sampled cells, each
-    computed from the oracle's own tessellation of the cell's rings 0..3 (see
+FULL_SIZE_CASES = {
+    "S10_HLLC": dict(limiter=1),
+    "DM_roundness": dict(limiter=2, regularize=1),
+    "HLL_entropy_switch": dict(limiter=1, riemann=1, entropy=1, mach_th=1.1),
+}
+
+
+@pytest.mark.parametrize("case", list(FULL_SIZE_CASES))
+def test_full_size_shear_layer_sampled_cells_match_oracle(oracle, gpu, case):
+    """The bench workload (256^3 generators, FP64 path): one whole step on the
+    device against the oracle on sampled cells, each computed from the
+    oracle's own tessellation of the cell's rings 0..3 (see
     helpers.oracle_local_step).  Inputs are identical on both sides: the
     shear-layer primitives turned into charges with the nominal volume 1/n
     (so W = U / V carries each cell's volume jitter), a fixed dt below the
     CFL value.  Charges to 1e-10 of each component's scale (momentum: the
     largest component's), positions to 1e-12."""
     c, torch = gpu
+    kw = FULL_SIZE_CASES[case]
+    ent = bool(kw.get("entropy", 0))
     w = WL.shear_layer(256)
     n = w.n
-    U0 = oracle.charges_from_prims(np.full(n, 1.0 / n), w.rho, w.vel, w.pres, w.gamma)
+    U0 = oracle.charges_from_prims(np.full(n, 1.0 / n), w.rho, w.vel, w.pres, w.gamma, entropy=ent)
     dt = 2e-4
-    ocfg, gcfg = cfg_pair(oracle, w.gamma, cfl=w.cfl, limiter=1)
+    ocfg, gcfg = cfg_pair(oracle, w.gamma, cfl=w.cfl, **kw)
     c.set_config(**{f: getattr(gcfg, f) for f, _ in gcfg._fields_})
     pos = H.to_dev(torch, w.pos.T)
     Ud = H.to_dev(torch, U0.T)
@@ -236,16 +246,55 @@ def test_full_size_shear_layer_sampled_cells_match_oracle(oracle, gpu):
     G = Ud[:, torch.as_tensor(cells, device="cuda")].cpu().numpy().T
     GP = pos[:, torch.as_tensor(cells, device="cuda")].cpu().numpy().T
     del Ud, pos
-    U0 = oracle.charges_from_prims(np.full(n, 1.0 / n), w.rho, w.vel, w.pres, w.gamma)
+    U0 = oracle.charges_from_prims(np.full(n, 1.0 / n), w.rho, w.vel, w.pres, w.gamma, entropy=ent)
     O, OP, _, m = H.oracle_local_step(oracle, w.pos, U0, w.box, ocfg, cells, dt)
-    print(f"[256^3 one-step parity] {len(cells)} sampled cells, {m} cells tessellated by the oracle")
+    print(f"[256^3 one-step parity {case}] {len(cells)} sampled cells, {m} cells tessellated by the oracle")
     scale = np.abs(O).max(axis=0)
     scale[1:4] = scale[1:4].max()
-    for k in range(5):
+    for k in range(O.shape[1]):
         np.testing.assert_allclose(G[:, k], O[:, k], rtol=0, atol=RTOL_STEP * scale[k], err_msg=f"component {k}")
     dp = GP - OP
     dp -= np.round(dp / w.box) * w.box
     assert np.abs(dp).max() <= 1e-12
+
+
+def test_full_size_shear_layer_mixed_step_sampled_l1(oracle, gpu):
+    """The mixed-precision path on the bench workload (256^3): one step
+    against the FP64 oracle on 24 sampled cells (rings 0..3 of each
+    tessellated by the oracle), identical inputs as above; relative L1 of
+    density, momentum and energy over the sample <= 1e-5, and the device's
+    totals conserved to 1e-12."""
+    c, torch = gpu
+    w = WL.shear_layer(256)
+    n = w.n
+    U0 = oracle.charges_from_prims(np.full(n, 1.0 / n), w.rho, w.vel, w.pres, w.gamma)
+    dt = 2e-4
+    ocfg, gcfg = cfg_pair(oracle, w.gamma, cfl=w.cfl, limiter=1)
+    gcfg.precision = 1
+    c.set_config(**{f: getattr(gcfg, f) for f, _ in gcfg._fields_})
+    try:
+        pos = H.to_dev(torch, w.pos.T)
+        Ud = H.to_dev(torch, U0.T)
+        del U0
+        t0 = c.mm_totals(Ud).cpu().numpy()
+        c.mm_step(pos, Ud, w.box, dt_fixed=torch.tensor([dt], dtype=torch.float64, device="cuda"))
+        t1 = c.mm_totals(Ud).cpu().numpy()
+        rng = np.random.default_rng(2)
+        cells = rng.choice(n, 24, replace=False)
+        G = Ud[:, torch.as_tensor(cells, device="cuda")].cpu().numpy().T
+        del Ud, pos
+    finally:
+        c.set_config(precision=0)
+    U0 = oracle.charges_from_prims(np.full(n, 1.0 / n), w.rho, w.vel, w.pres, w.gamma)
+    scale = np.abs(U0).sum(0)
+    scale[1:4] = max(scale[1:4].max(), np.sqrt(scale[0] * scale[4]))
+    assert np.all(np.abs(t1 - t0) <= 1e-12 * scale), (t1 - t0) / scale
+    O, _, _, m = H.oracle_local_step(oracle, w.pos, U0, w.box, ocfg, cells, dt)
+    l1 = {}
+    for name, cols in (("density", [0]), ("momentum", [1, 2, 3]), ("energy", [4])):
+        l1[name] = np.abs(G[:, cols] - O[:, cols]).sum() / np.abs(O[:, cols]).sum()
+    print("256^3 mixed step, sampled cells: relative L1 vs the FP64 oracle", {k: f"{v:.2e}" for k, v in l1.items()})
+    assert max(l1.values()) <= 1e-5, l1
 
 
 MIXED_CASES = {
