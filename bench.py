@@ -170,13 +170,13 @@ def clip_roofline(direct, filtered, ms, n, clip_filter):
 
 
 # DRAM traffic of one k_clip launch, from an ncu capture of one launch on the
-# 128^3 shear layer (dram__bytes_read.sum + dram__bytes_write.sum = 462,103,040
-# + 1,439,943,168 bytes over 2,097,152 cells; filtered clipping, two warps per
+# 128^3 shear layer (dram__bytes_read.sum + dram__bytes_write.sum = 459,768,320
+# + 1,439,416,576 bytes over 2,097,152 cells; filtered clipping, two warps per
 # block), per cell; it scales with the cells of the launch.  Valid only for the
 # clipper source it was taken on: the digest of the clipping kernel's sources
 # must match, else the figure is withheld.
-CLIP_TRAFFIC = {"sources": ("csrc/mm_clip.cu", "csrc/mm_internal.cuh"), "sha256_16": "47f2de91b800d8d8",
-                "bytes_per_cell": 1902046208 / 2097152, "cells_captured": 2097152}
+CLIP_TRAFFIC = {"sources": ("csrc/mm_clip.cu", "csrc/mm_internal.cuh"), "sha256_16": "b7d0b195687e6760",
+                "bytes_per_cell": 1899184896 / 2097152, "cells_captured": 2097152}
 
 
 def clip_sources_digest():

@@ -63,6 +63,7 @@ struct mm_ctx {
     Buf vol, cen, s_cnt, s_nb, s_sh, s_area, s_fc;
     // cells re-clipped by the large clipper: the retry list and their overflow rows
     Buf retry, o_cnt, o_nb, o_sh, o_area, o_fc, o_emit, o_conf, o_partner;
+    Buf cell_order;  // processing order of the incident-face kernels
     int64_t orows = 0;
     // face compaction
     Buf emit_mask, conf_mask, partner, emit_cnt, conf_cnt, face_off, inc_off;
@@ -300,6 +301,7 @@ static MeshDev mesh_from(const mm_mesh *mm)
     m.cen = mm->cell_centroid;
     m.inc_off = mm->inc_off;
     m.inc_face = mm->inc_face;
+    m.order = nullptr;  // a caller's mesh: cells in index order
     return m;
 }
 
@@ -432,7 +434,7 @@ static mm_status ensure_tess_buffers(mm_ctx *c, int64_t n)
         (r = ensure(c, c->emit_mask, n * 8)) || (r = ensure(c, c->conf_mask, n * 8)) || (r = ensure(c, c->partner, ns)) ||
         (r = ensure(c, c->emit_cnt, n * sizeof(int))) || (r = ensure(c, c->conf_cnt, n * sizeof(int))) ||
         (r = ensure(c, c->face_off, (n + 1) * sizeof(int))) || (r = ensure(c, c->inc_off, (n + 1) * sizeof(int))) ||
-        (r = ensure(c, c->retry, n * sizeof(int))))
+        (r = ensure(c, c->retry, n * sizeof(int))) || (r = ensure(c, c->cell_order, n * sizeof(int))))
         return r;
     if (c->orows < RETRY_ROWS_FIXED && (r = ensure_overflow(c, RETRY_ROWS_FIXED))) return r;
     return MM_OK;
@@ -520,6 +522,8 @@ static mm_status tess_enqueue(mm_ctx *c, const double *pos, bool fixed)
         if ((r = ensure_faces(c, nf, ni))) return r;
         stage_mark(c, MM_STAGE_FACES, true);
     }
+    // the order in which the incident-face kernels take the cells (by face count)
+    launch_cell_order(n, P<int>(c->inc_off), P<int>(c->cell_order), s);
     launch_face_write(n, pos, boxes, cbox, sl, ovf(), P<unsigned long long>(c->emit_mask), P<unsigned long long>(c->conf_mask),
                       P<signed char>(c->partner), P<int>(c->face_off), P<int>(c->inc_off), P<int>(c->face_i),
                       P<int>(c->face_j), P<int>(c->face_shift), P<double>(c->face_area), P<double>(c->face_normal),
@@ -527,7 +531,7 @@ static mm_status tess_enqueue(mm_ctx *c, const double *pos, bool fixed)
                       P<double>(c->cen), c->st, s);
     CKLAUNCH();
     stage_mark(c, MM_STAGE_FACES, false);
-    c->launches += 1;
+    c->launches += 2;
 
     MeshDev &m = c->mesh;
     m.n = n;
@@ -546,6 +550,7 @@ static mm_status tess_enqueue(mm_ctx *c, const double *pos, bool fixed)
     m.cen = P<double>(c->cen);
     m.inc_off = P<int>(c->inc_off);
     m.inc_face = P<int>(c->inc_face);
+    m.order = P<int>(c->cell_order);
     c->mesh_ninc = fixed ? 0 : ni;
     c->have_mesh = true;
     return MM_OK;
@@ -761,7 +766,7 @@ void mm_destroy(mm_ctx *c)
                    &c->face_off, &c->inc_off, &c->face_i, &c->face_j, &c->face_shift, &c->face_area,
                    &c->face_normal, &c->face_cen, &c->inc_face, &c->Wh, &c->grad, &c->flux, &c->w_int, &c->dt_int,
                    &c->retry, &c->o_cnt, &c->o_nb, &c->o_sh, &c->o_area, &c->o_fc, &c->o_emit, &c->o_conf,
-                   &c->o_partner,
+                   &c->o_partner, &c->cell_order,
                    &c->tot_partial, &c->drift_box, &c->drift_cbox, &c->x_fij, &c->x_fa, &c->x_fq, &c->x_ff,
                    &c->x_cw, &c->x_ch, &c->x_grad, &c->x_wv, &c->x_flux, &c->heun_U0, &c->fgeo, &c->minv};
     for (Buf *b : bufs)

@@ -102,9 +102,10 @@ __global__ void __launch_bounds__(128, MM_GRAD_MINBLOCKS) k_gradient(MeshDev m, 
                                                   double *__restrict__ grad, double *__restrict__ Wh,
                                                   const double *__restrict__ dtp)
 {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t n = m.n, fs = m.fs;
-    if (i >= n) return;
+    if (t >= n) return;
+    const int64_t i = cell_of(m, t);
     double Wi[NG];
     loadw<NG>(S, n, i, 1.0, Wi);
     const int e0 = m.inc_off[i], e1 = m.inc_off[i + 1];
@@ -476,9 +477,10 @@ template <int NG>
 __global__ void __launch_bounds__(256) k_update(MeshDev m, HydroCfg c, const double *__restrict__ flux,
                                                 const double *__restrict__ dtp, double *__restrict__ U)
 {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t n = m.n, nf = m.fs;  // flux rows are face-capacity apart
-    if (i >= n) return;
+    if (t >= n) return;
+    const int64_t i = cell_of(m, t);
     double acc[NG];
 #pragma unroll
     for (int k = 0; k < NG; ++k) acc[k] = 0.0;
@@ -805,6 +807,33 @@ void launch_totals(const double *U, int64_t n, double *partial, int nblocks, dou
 {
     k_totals_partial<<<nblocks, 256, 0, s>>>(U, n, partial);
     k_totals_final<<<1, 32, 0, s>>>(partial, nblocks, totals);
+}
+
+// The cell order of MeshDev::order: each block sorts its CELL_ORDER_BLOCK
+// cells by incident-face count (ties by index: a stable, deterministic order)
+// by counting, for each cell, the block's cells that come before it.
+__global__ void __launch_bounds__(CELL_ORDER_BLOCK) k_cell_order(int64_t n, const int *__restrict__ inc_off,
+                                                                 int *__restrict__ order)
+{
+    __shared__ int cnt[CELL_ORDER_BLOCK];
+    const int64_t base = (int64_t)blockIdx.x * CELL_ORDER_BLOCK;
+    const int t = threadIdx.x;
+    const int64_t i = base + t;
+    const int c = i < n ? inc_off[i + 1] - inc_off[i] : 0x7fffffff;  // beyond n: last
+    cnt[t] = c;
+    __syncthreads();
+    int rank = 0;
+    for (int u = 0; u < CELL_ORDER_BLOCK; ++u) {
+        const int cu = cnt[u];
+        rank += (cu < c) || (cu == c && u < t);
+    }
+    if (i < n) order[base + rank] = (int)i;
+}
+
+void launch_cell_order(int64_t n, const int *inc_off, int *order, cudaStream_t s)
+{
+    const int64_t nb = (n + CELL_ORDER_BLOCK - 1) / CELL_ORDER_BLOCK;
+    k_cell_order<<<(unsigned)nb, CELL_ORDER_BLOCK, 0, s>>>(n, inc_off, order);
 }
 
 }  // namespace mm

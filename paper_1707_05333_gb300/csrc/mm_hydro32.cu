@@ -83,6 +83,8 @@ template <bool PREDICT>
 __global__ void __launch_bounds__(128) k_gradient32(MeshDev m, HydroCfg c, Mixed x, const float4 *__restrict__ rin,
                                                     float4 *__restrict__ rout, const double *__restrict__ dtp)
 {
+    // index order: this kernel is bound by its gathers, and the FP32 loop's
+    // uneven lengths cost less than scattering the cells of a warp
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t n = m.n;
     if (i >= n) return;
@@ -289,9 +291,10 @@ __global__ void __launch_bounds__(128) k_face_flux32(MeshDev m, HydroCfg c, Mixe
 __global__ void __launch_bounds__(256) k_update32(MeshDev m, HydroCfg c, Mixed x, const double *__restrict__ dtp,
                                                   double *__restrict__ U)
 {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t n = m.n;
-    if (i >= n) return;
+    if (t >= n) return;
+    const int64_t i = cell_of(m, t);
     double acc[5] = {0, 0, 0, 0, 0};
     for (int e = m.inc_off[i]; e < m.inc_off[i + 1]; ++e) {
         int f = m.inc_face[e];

@@ -139,7 +139,17 @@ struct MeshDev {
     const double *area, *normal, *fcen;
     const double *vol, *cen;
     const int *inc_off, *inc_face;
+    // Order in which the kernels that loop over a cell's incident faces take
+    // the cells: within every aligned run of CELL_ORDER_BLOCK entries, that
+    // run's cells by their number of incident faces (then by index), so the
+    // lanes of a warp run loops of nearly equal length.  NULL: index order.
+    const int *order;
 };
+constexpr int CELL_ORDER_BLOCK = 128;
+
+// The cell a thread of an incident-face kernel takes (t < n).
+__device__ __forceinline__ int64_t cell_of(const MeshDev &m, int64_t t) { return m.order ? m.order[t] : t; }
+void launch_cell_order(int64_t n, const int *inc_off, int *order, cudaStream_t s);
 
 struct HydroCfg {
     double gamma, cfl, eta, chi, zeta, theta, rho_floor, eps_floor;
