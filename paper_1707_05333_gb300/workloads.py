@@ -250,3 +250,27 @@ WORKLOADS = {
     "shear_layer": shear_layer,
     "gresho_vortex": gresho_vortex,
 }
+
+
+def clustered_points(n, core_fraction=0.5, core_scale=0.02, seed=0):
+    """Strongly clustered generators for robustness tests (seeded): a
+    fraction of the points in a Plummer-like core (radius drawn so that the
+    enclosed fraction is r^3 / (r^2 + a^2)^(3/2), a = core_scale) about the
+    box centre, the rest uniform; positions wrapped into the unit box."""
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + 300 + seed))
+    nc = int(round(core_fraction * n))
+    u = rng.uniform(1e-6, 0.999, size=nc)
+    r = core_scale / np.sqrt(u ** (-2.0 / 3.0) - 1.0)
+    d = rng.normal(size=(nc, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    core = 0.5 + np.minimum(r, 0.45)[:, None] * d
+    rest = rng.uniform(0.0, 1.0, size=(n - nc, 3))
+    return np.concatenate([core, rest]) % 1.0
+
+
+def clustered_box(n=6000, seed=1):
+    """A clustered point set (clustered_points) in the periodic unit box with
+    a uniform gas at rest (rho = 1, P = 1, gamma = 5/3): the mesh, not the
+    flow, is the test."""
+    pos = clustered_points(n, seed=seed)
+    return _finish(f"clustered_{n}", pos, np.ones(3), np.ones(n), np.zeros((n, 3)), np.ones(n), 5.0 / 3.0, 0.3, 1)

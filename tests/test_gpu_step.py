@@ -79,6 +79,7 @@ CONFIGS = {
     "face_centroid_limiter_random": dict(maker=lambda: WL.smooth_wave(10), kw=dict(limiter=3, regularize=1),
                                          random=True),
     "gresho_vortex_16x16x3_regularized": dict(maker=lambda: WL.gresho_vortex(16), kw=dict(limiter=1, regularize=1)),
+    "clustered_6000_random_state_DM": dict(maker=lambda: WL.clustered_box(6000), kw=dict(limiter=2), random=True),
     # entropy column and switch (Sec. 4.3): cells at the shock keep the energy
     # equation, the rest take E from the entropy
     "entropy_switch_shock_tube_48x6x6": dict(maker=lambda: WL.shock_tube(48, 6, 6),

@@ -37,6 +37,8 @@ CASES = {
     "n2": lambda: (np.array([[0.1, 0.5, 0.5], [0.6, 0.55, 0.45]]), np.ones(3)),
     "n5": lambda: (WL.random_points(5, seed=6), np.ones(3)),
     "n37": lambda: (WL.random_points(37, seed=7), np.ones(3)),
+    # a dense core in a sparse background: cell volumes over five decades, crowded bins
+    "clustered_6000": lambda: (WL.clustered_points(6000, seed=1), np.ones(3)),
 }
 
 
