@@ -141,7 +141,8 @@ __global__ void k_face_confirm(int64_t n, Slots sl, OvfFaces ov, unsigned long l
 // The face records and incidences of cell i's confirmed slots, one lane per
 // slot (OVF false: no cell was re-clipped, every row is a main row).
 template <bool OVF>
-__device__ __forceinline__ void face_write_slots(int64_t n, int64_t i, int lane, double pix, double piy, double piz,
+__device__ __forceinline__ void face_write_slots(int64_t n, int64_t i, int lane, int stride, double pix, double piy,
+                                                 double piz,
                                                  const double *L, const double *__restrict__ pos, const Slots &sl,
                                                  const OvfFaces &ov, const unsigned long long *__restrict__ emit_mask,
                                                  const unsigned long long *__restrict__ conf_mask,
@@ -167,7 +168,7 @@ __device__ __forceinline__ void face_write_slots(int64_t n, int64_t i, int lane,
     }
     const int fbase = face_off[i], e0 = inc_off[i];
     const int kend = cm1 ? 128 - __clzll((long long)cm1) : 64 - __clzll((long long)cm0);
-    for (int k = lane; k < kend; k += 32) {
+    for (int k = lane; k < kend; k += stride) {
         if (!(((k < 64 ? cm0 : cm1) >> (k & 63)) & 1ull)) continue;
         const int e = e0 + (OVF ? popc_below(cm0, cm1, k) : __popcll(cm0 & ((1ull << k) - 1ull)));
         const int64_t s = r.base + k;
@@ -211,10 +212,13 @@ __device__ __forceinline__ void face_write_slots(int64_t n, int64_t i, int lane,
     }
 }
 
-// One warp per cell, one lane per face slot: the slot rows are read and the
-// face records and incidences written with consecutive lanes on consecutive
-// addresses.  Each slot knows its place in the face and incidence lists from
-// the masks, so the results do not depend on the schedule.
+// Four lanes per cell, each taking every fourth face slot: eight cells per
+// warp keep the lanes busy (a cell has about 16 faces; a warp per cell left
+// half the lanes idle and its FP64 work per face made that the bound;
+// measured at 256^3: a warp 18.4 ms, 16 lanes 14.3, 8 lanes 11.4, 4 lanes
+// 10.1, 2 lanes 9.9, one thread 21.0; on random points 4 lanes was best).
+// Each slot knows its place in the face and incidence lists from the masks,
+// so the results do not depend on the schedule.
 __global__ void k_face_write(int64_t n, const double *__restrict__ pos, const BoxDev *__restrict__ boxes,
                              const int *__restrict__ cbox, Slots sl, OvfFaces ov,
                              const unsigned long long *__restrict__ emit_mask,
@@ -226,9 +230,9 @@ __global__ void k_face_write(int64_t n, const double *__restrict__ pos, const Bo
                              int *__restrict__ inc_face, int64_t icap, const double *__restrict__ vol,
                              double *__restrict__ cen, DevStatus *st)
 {
-    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (i >= n) return;  // whole warps
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 2;
+    const int lane = threadIdx.x & 3;
+    if (i >= n) return;  // whole groups of four lanes
     const double pix = pos[i], piy = pos[n + i], piz = pos[2 * n + i];
     if (lane == 0) {
         // the cell centroid from the clipper's volume and first moment about
@@ -245,11 +249,13 @@ __global__ void k_face_write(int64_t n, const double *__restrict__ pos, const Bo
         return;
     }
     if (*ov.nretry == 0)
-        face_write_slots<false>(n, i, lane, pix, piy, piz, L, pos, sl, ov, emit_mask, conf_mask, partner, face_off,
-                                inc_off, face_i, face_j, face_shift, face_area, face_normal, face_cen, fcap, inc_face);
+        face_write_slots<false>(n, i, lane, 4, pix, piy, piz, L, pos, sl, ov, emit_mask, conf_mask, partner,
+                                face_off, inc_off, face_i, face_j, face_shift, face_area, face_normal, face_cen, fcap,
+                                inc_face);
     else
-        face_write_slots<true>(n, i, lane, pix, piy, piz, L, pos, sl, ov, emit_mask, conf_mask, partner, face_off,
-                               inc_off, face_i, face_j, face_shift, face_area, face_normal, face_cen, fcap, inc_face);
+        face_write_slots<true>(n, i, lane, 4, pix, piy, piz, L, pos, sl, ov, emit_mask, conf_mask, partner,
+                               face_off, inc_off, face_i, face_j, face_shift, face_area, face_normal, face_cen, fcap,
+                               inc_face);
 }
 
 void launch_face_confirm(int64_t n, Slots sl, OvfFaces ov, unsigned long long *emit_mask,
@@ -267,7 +273,7 @@ void launch_face_write(int64_t n, const double *pos, const BoxDev *boxes, const 
                        int64_t fcap, int *inc_face, int64_t icap, const double *vol, double *cen, DevStatus *st,
                        cudaStream_t s)
 {
-    const int nb = (int)((n + 3) / 4);  // four cells (warps) per block
+    const int nb = (int)((n + 31) / 32);  // 32 cells per block of 128 threads
     k_face_write<<<nb, 128, 0, s>>>(n, pos, boxes, cbox, sl, ov, emit_mask, conf_mask, partner, face_off, inc_off,
                                     face_i, face_j, face_shift, face_area, face_normal, face_cen, fcap, inc_face,
                                     icap, vol, cen, st);
