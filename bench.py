@@ -769,22 +769,20 @@ def run_ours(args, world, rank, local):
         n = w.n
         value, ms = aggregate(ms, n, args.steps, world)
 
-        # ---- end to end through the ABI with host buffers
+        # ---- end to end through the ABI with host buffers: mm_step_host copies
+        # the step's inputs up and its results back (page-locked memory, the
+        # copies overlapped with the step inside the library)
         pos_h = torch.empty_like(pos, device="cpu").pin_memory()
         U_h = torch.empty_like(U, device="cpu").pin_memory()
         pos_h.copy_(pos0.cpu())
         U_h.copy_(U0.cpu())
-        pd, Ud = torch.empty_like(pos), torch.empty_like(U)
+        ctx.mm_step_host(pos_h, U_h, w.box)  # untimed: the context's device copies are allocated here
         barrier()
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
         for _ in range(args.e2e_steps):
-            pd.copy_(pos_h, non_blocking=True)
-            Ud.copy_(U_h, non_blocking=True)
-            ctx.mm_step(pd, Ud, w.box)
-            pos_h.copy_(pd, non_blocking=True)
-            U_h.copy_(Ud, non_blocking=True)
+            ctx.mm_step_host(pos_h, U_h, w.box)
         f1.record(stream)
         stream.synchronize()
         e2e_ms = f0.elapsed_time(f1)

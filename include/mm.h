@@ -198,6 +198,19 @@ mm_status mm_drift(mm_ctx *ctx, double *pos, int64_t n, const double *w, const d
 mm_status mm_step(mm_ctx *ctx, double *pos, double *U, int64_t n, const double box[3],
                   const double *dt_fixed, double *dt_out, double *w_out);
 
+/* One whole step (as mm_step, CFL timestep) on HOST arrays: pos[3][n] and
+ * U[5][n] (U[6][n] with cfg.entropy) are read from host memory and
+ * overwritten with the step's result; dt_out (host, may be NULL) receives
+ * dt.  The context keeps device copies (grown as needed, freed by
+ * mm_destroy).  The copies overlap the step: the positions go up first (the
+ * binning reads them), the charges on a second stream while the mesh is
+ * built (the mesh velocity reads them first), and the new charges come back
+ * while the generators drift.  With page-locked host memory (cudaHostAlloc,
+ * torch pin_memory) the copies are asynchronous; pageable memory works but
+ * serialises them.  Returns once the results are in the host arrays.  The
+ * caller keeps ownership of the host arrays. */
+mm_status mm_step_host(mm_ctx *ctx, double *pos, double *U, int64_t n, const double box[3], double *dt_out);
+
 /* One whole step (as mm_step, CFL timestep per box) for nboxes independent
  * periodic boxes stored back to back: box b holds cells
  * [box_off[b], box_off[b+1]) of pos[3][n] and U[5][n] and has size

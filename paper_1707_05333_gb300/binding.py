@@ -61,7 +61,7 @@ EXPORTS = ["mm_default_config", "mm_create", "mm_destroy", "mm_last_error", "mm_
            "mm_tessellate", "mm_gradients", "mm_mesh_velocity", "mm_timestep", "mm_flux_step",
            "mm_drift", "mm_step", "mm_prims_to_charges", "mm_totals", "mm_copy", "mm_tess_stats",
            "mm_set_timing", "mm_stage_times", "mm_kernel_launches", "mm_totals_noalloc", "mm_step_batched",
-           "mm_sync_status", "mm_current_mesh", "mm_get_config", "mm_autotune"]
+           "mm_sync_status", "mm_current_mesh", "mm_get_config", "mm_autotune", "mm_step_host"]
 
 STATS = ["max_candidates", "max_planes", "max_vertices", "multi_ring_cells", "cuts", "fp64_plane_tests",
          "fp64_vertex_solves", "fp64_fan_terms", "candidates_tested", "retried_cells"]
@@ -106,6 +106,7 @@ def load(path: str | None = None):
     L.mm_set_timing.argtypes = [_c_p, ctypes.c_int]
     L.mm_stage_times.argtypes = [_c_p, P(ctypes.c_double), P(_c_i64)]
     L.mm_step_batched.argtypes = [_c_p, _c_p, _c_p, _c_i64, P(_c_i64), P(ctypes.c_double), ctypes.c_int, _c_p]
+    L.mm_step_host.argtypes = [_c_p, _c_p, _c_p, _c_i64, P(ctypes.c_double), _c_p]
     L.mm_sync_status.argtypes = [_c_p]
     L.mm_get_config.argtypes = [_c_p, P(Config)]
     L.mm_autotune.argtypes = [_c_p, _c_p, _c_i64, P(ctypes.c_double), ctypes.c_int, P(ctypes.c_double)]
@@ -146,6 +147,21 @@ def _ptr(t: torch.Tensor | None, shape=None, dtype=torch.float64):
         return None
     if not t.is_cuda:
         raise ValueError("libmm takes device tensors")
+    if t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(t: torch.Tensor | None, shape=None, dtype=torch.float64):
+    """Pointer to a contiguous host tensor (the host-buffer step)."""
+    if t is None:
+        return None
+    if t.device.type != "cpu":
+        raise ValueError("expected a host tensor")
     if t.dtype != dtype:
         raise TypeError(f"expected {dtype}, got {t.dtype}")
     if not t.is_contiguous():
@@ -282,6 +298,14 @@ class Context:
         b = (ctypes.c_double * 3)(*[float(x) for x in box])
         self._call("mm_step", self.h, _ptr(pos, (3, n)), _ptr(U, (self.ng, n)), n, b,
                    _ptr(dt_fixed, (1,)), _ptr(dt_out, (1,)), _ptr(w_out, (3, n)))
+
+    def mm_step_host(self, pos, U, box, dt_out=None):
+        """One step on host tensors (pos [3][n], U [5 or 6][n], float64, in place;
+        page-locked memory lets the library overlap the copies with the step).
+        dt_out: optional host float64 tensor of one element."""
+        n = pos.shape[1]
+        b = (ctypes.c_double * 3)(*[float(x) for x in box])
+        self._call("mm_step_host", self.h, _hptr(pos, (3, n)), _hptr(U, (self.ng, n)), n, b, _hptr(dt_out, (1,)))
 
     def mm_step_batched(self, pos, U, box_off, boxes, dt_out=None):
         """One step of independent periodic boxes stored back to back (replays a

@@ -64,6 +64,11 @@ struct mm_ctx {
     // cells re-clipped by the large clipper: the retry list and their overflow rows
     Buf retry, o_cnt, o_nb, o_sh, o_area, o_fc, o_emit, o_conf, o_partner;
     Buf cell_order;  // processing order of the incident-face kernels
+    // mm_step_host: device copies of the host arrays, and the stream and
+    // events that overlap their copies with the step
+    Buf h_pos, h_U, h_dt;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_u_in = nullptr, ev_u_done = nullptr, ev_u_out = nullptr;
     int64_t orows = 0;
     // face compaction
     Buf emit_mask, conf_mask, partner, emit_cnt, conf_cnt, face_off, inc_off;
@@ -649,8 +654,17 @@ static mm_status heun_stage(mm_ctx *c, const MeshDev &m, const double *pos, cons
 // integrator 1 (Heun): stage 1 on the start mesh, drift, a second
 // tessellation, stage 2 on the end mesh with the same generator velocities,
 // and the average of the start and stage-2 charges.
+// Where a host step sends the final charges: U_host (ubytes), copied on the
+// copy stream while the generators drift (the event ev_u_out marks its end),
+// or on the stream after the step when the integrator finishes with U later.
+struct HostOut {
+    double *U_host;
+    size_t ubytes;
+    bool on_copy_stream;
+};
+
 static mm_status step_rest(mm_ctx *c, double *pos, double *U, const double *dt_fixed, double *w, double *dt,
-                           bool fixed)
+                           bool fixed, HostOut *ho = nullptr)
 {
     const MeshDev m = c->mesh;
     HydroCfg h = hydro_cfg(c->cfg);
@@ -676,6 +690,14 @@ static mm_status step_rest(mm_ctx *c, double *pos, double *U, const double *dt_f
     } else if ((r = hydro_enqueue(c, m, pos, w, dt, U))) {
         return r;
     }
+    if (ho && c->cfg.integrator != 1) {
+        // U is final: bring it back while the generators drift
+        CK(cudaEventRecord(c->ev_u_done, s));
+        CK(cudaStreamWaitEvent(c->copy_stream, c->ev_u_done, 0));
+        CK(cudaMemcpyAsync(ho->U_host, U, ho->ubytes, cudaMemcpyDeviceToHost, c->copy_stream));
+        CK(cudaEventRecord(c->ev_u_out, c->copy_stream));
+        ho->on_copy_stream = true;
+    }
     stage_mark(c, MM_STAGE_DRIFT, true);
     launch_drift(pos, m.n, w, dt, m.cbox, m.boxL, s);
     stage_mark(c, MM_STAGE_DRIFT, false);
@@ -689,6 +711,7 @@ static mm_status step_rest(mm_ctx *c, double *pos, double *U, const double *dt_f
         launch_heun_average(m1, h, P<double>(c->heun_U0), U, s);
         CKLAUNCH();
         c->launches += 1;
+        if (ho) CK(cudaMemcpyAsync(ho->U_host, U, ho->ubytes, cudaMemcpyDeviceToHost, s));
     }
     return MM_OK;
 }
@@ -766,12 +789,16 @@ void mm_destroy(mm_ctx *c)
                    &c->face_off, &c->inc_off, &c->face_i, &c->face_j, &c->face_shift, &c->face_area,
                    &c->face_normal, &c->face_cen, &c->inc_face, &c->Wh, &c->grad, &c->flux, &c->w_int, &c->dt_int,
                    &c->retry, &c->o_cnt, &c->o_nb, &c->o_sh, &c->o_area, &c->o_fc, &c->o_emit, &c->o_conf,
-                   &c->o_partner, &c->cell_order,
+                   &c->o_partner, &c->cell_order, &c->h_pos, &c->h_U, &c->h_dt,
                    &c->tot_partial, &c->drift_box, &c->drift_cbox, &c->x_fij, &c->x_fa, &c->x_fq, &c->x_ff,
                    &c->x_cw, &c->x_ch, &c->x_grad, &c->x_wv, &c->x_flux, &c->heun_U0, &c->fgeo, &c->minv};
+    if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    for (cudaEvent_t e : {c->ev_start, c->ev_u_in, c->ev_u_done, c->ev_u_out})
+        if (e) cudaEventDestroy(e);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     if (c->st) cudaFree(c->st);
     if (c->st_host) cudaFreeHost(c->st_host);
     if (c->cnt_host) cudaFreeHost(c->cnt_host);
@@ -901,6 +928,52 @@ mm_status mm_step(mm_ctx *c, double *pos, double *U, int64_t n, const double box
     double *w = w_out ? w_out : P<double>(c->w_int);
     double *dt = dt_out ? dt_out : P<double>(c->dt_int);
     return step_rest(c, pos, U, dt_fixed, w, dt, false);
+}
+
+mm_status mm_step_host(mm_ctx *c, double *pos, double *U, int64_t n, const double box[3], double *dt_out)
+{
+    if (!c) return MM_EINVAL;
+    if (!pos || !U) return fail(c, MM_EINVAL, "null pointer argument");
+    if (n < 1 || n > MM_MAX_CELLS) return fail(c, MM_EINVAL, "n = %lld outside [1, %lld]", (long long)n, MM_MAX_CELLS);
+    const size_t pbytes = 3 * (size_t)n * sizeof(double);
+    const size_t ubytes = (c->cfg.entropy ? 6 : 5) * (size_t)n * sizeof(double);
+    mm_status r;
+    if ((r = ensure(c, c->h_pos, pbytes)) || (r = ensure(c, c->h_U, ubytes)) || (r = ensure(c, c->h_dt, sizeof(double))))
+        return r;
+    if (!c->copy_stream) {
+        CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&c->ev_start, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&c->ev_u_in, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&c->ev_u_done, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&c->ev_u_out, cudaEventDisableTiming));
+    }
+    cudaStream_t s = c->stream, s2 = c->copy_stream;
+    double *pd = P<double>(c->h_pos), *Ud = P<double>(c->h_U), *dtd = P<double>(c->h_dt);
+    // the copy stream follows the work already queued (it may still read Ud)
+    CK(cudaEventRecord(c->ev_start, s));
+    CK(cudaStreamWaitEvent(s2, c->ev_start, 0));
+    CK(cudaMemcpyAsync(pd, pos, pbytes, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(Ud, U, ubytes, cudaMemcpyHostToDevice, s2));
+    CK(cudaEventRecord(c->ev_u_in, s2));
+    HostOut ho{U, ubytes, false};
+    r = mm_tessellate(c, pd, n, box, nullptr);
+    if (r == MM_OK) r = ensure(c, c->w_int, 3 * n * sizeof(double));
+    if (r == MM_OK) r = ensure_hydro(c, n, c->mesh.fs);
+    if (r == MM_OK) {
+        // the charges are first read by the mesh velocity
+        CK(cudaStreamWaitEvent(s, c->ev_u_in, 0));
+        r = step_rest(c, pd, Ud, nullptr, P<double>(c->w_int), dtd, false, &ho);
+    }
+    if (r != MM_OK) {
+        cudaStreamSynchronize(s2);  // the host arrays stay in use until their copies end
+        cudaStreamSynchronize(s);
+        return r;
+    }
+    CK(cudaMemcpyAsync(pos, pd, pbytes, cudaMemcpyDeviceToHost, s));
+    if (dt_out) CK(cudaMemcpyAsync(dt_out, dtd, sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (ho.on_copy_stream) CK(cudaStreamWaitEvent(s, c->ev_u_out, 0));
+    CK(cudaStreamSynchronize(s));
+    return MM_OK;
 }
 
 mm_status mm_step_batched(mm_ctx *c, double *pos, double *U, int64_t n, const int64_t *box_off, const double *boxes,
