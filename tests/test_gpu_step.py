@@ -298,6 +298,54 @@ def test_full_size_shear_layer_mixed_step_sampled_l1(oracle, gpu):
     assert max(l1.values()) <= 1e-5, l1
 
 
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_ensemble_largest_box_sampled_cells_match_oracle(oracle, gpu, precision):
+    """The batched ensemble's largest box (uniform random generators,
+    lognormal density from a k^-3 Gaussian field, Gaussian velocities, P = 1,
+    gamma 5/3), one step on the device against the oracle's local step on 16
+    sampled cells, identical inputs (primitives times the nominal volume 1/n,
+    a fixed dt below the CFL step).  FP64: charges to 1e-10 of each
+    component's scale, positions to 1e-12; mixed precision: relative L1 of
+    density, momentum and energy over the sample <= 1e-5."""
+    c, torch = gpu
+    sizes = WL.ensemble_sizes(512)
+    b = int(np.argmax(sizes))
+    w = WL.ensemble_box(b, int(sizes[b]))
+    n = w.n
+    U0 = oracle.charges_from_prims(np.full(n, 1.0 / n), w.rho, w.vel, w.pres, w.gamma)
+    dt = 3e-4  # below the CFL step of the box's smallest cells
+    ocfg, gcfg = cfg_pair(oracle, w.gamma, cfl=w.cfl, limiter=1)
+    gcfg.precision = precision
+    c.set_config(**{f: getattr(gcfg, f) for f, _ in gcfg._fields_})
+    try:
+        pos = H.to_dev(torch, w.pos.T)
+        Ud = H.to_dev(torch, U0.T)
+        c.mm_step(pos, Ud, w.box, dt_fixed=torch.tensor([dt], dtype=torch.float64, device="cuda"))
+        rng = np.random.default_rng(5)
+        cells = rng.choice(n, 16, replace=False)
+        G = Ud[:, torch.as_tensor(cells, device="cuda")].cpu().numpy().T
+        GP = pos[:, torch.as_tensor(cells, device="cuda")].cpu().numpy().T
+    finally:
+        c.set_config(precision=0)
+    O, OP, _, m = H.oracle_local_step(oracle, w.pos, U0, w.box, ocfg, cells, dt)
+    print(f"[ensemble box {b}, {n} cells, precision {precision}] {len(cells)} sampled cells, "
+          f"{m} tessellated by the oracle")
+    if precision == 0:
+        scale = np.abs(O).max(axis=0)
+        scale[1:4] = scale[1:4].max()
+        for k in range(O.shape[1]):
+            np.testing.assert_allclose(G[:, k], O[:, k], rtol=0, atol=RTOL_STEP * scale[k], err_msg=f"component {k}")
+        dp = GP - OP
+        dp -= np.round(dp / w.box) * w.box
+        assert np.abs(dp).max() <= 1e-12
+    else:
+        l1 = {}
+        for name, cols in (("density", [0]), ("momentum", [1, 2, 3]), ("energy", [4])):
+            l1[name] = np.abs(G[:, cols] - O[:, cols]).sum() / np.abs(O[:, cols]).sum()
+        print("relative L1 vs the FP64 oracle", {k: f"{v:.2e}" for k, v in l1.items()})
+        assert max(l1.values()) <= 1e-5, l1
+
+
 MIXED_CASES = {
     "smooth_wave_16^3": lambda: WL.smooth_wave(16),
     "shear_layer_32^3": lambda: WL.shear_layer(32),
