@@ -32,6 +32,10 @@
 // it solves that vertex in FP64 and classifies exactly as PREC 0 does.  At the
 // end every vertex is solved in FP64 from its three planes.  Both variants
 // therefore take the same decisions and produce the same FP64 geometry.
+// Ties: a vertex lies beyond a plane only past a margin of 2^-40..2^-39 of the
+// plane's offset, so vertices on it (co-spherical generators of exact
+// lattices, where one point has several representations with different
+// rounding) are kept consistently.
 #include "mm_internal.cuh"
 
 namespace mm {
@@ -514,6 +518,13 @@ __device__ void clip_by(ClipSmem<PREC, CAP> &S, int k, CellState &C, int lane)
     constexpr int BMW = CAP::BMW;
     const double qx = S.u.c.x[k], qy = S.u.c.y[k], qz = S.u.c.z[k];
     const double off = half_of(S.u.c.d2[k]);
+    // A vertex is beyond the plane when q.v exceeds the offset by a margin of
+    // 2^-40..2^-39 of it (2^13 units in the last place, an integer add on the
+    // bit pattern): a vertex exactly on the plane (co-spherical generators,
+    // exact lattices) stays, whatever rounding its several representations
+    // carry, so copies of one point are never split across the plane.  The
+    // planes themselves, and every vertex solved from them, are exact.
+    const double offk = __longlong_as_double(__double_as_longlong(off) + (1LL << 13));
     const int nchunk = (C.nt + 31) >> 5;
     ChunkMask<CAP::TM> outm;
     C.tested++;
@@ -530,7 +541,7 @@ __device__ void clip_by(ClipSmem<PREC, CAP> &S, int k, CellState &C, int lane)
         const int t = c * 32 + lane;
         const bool live = t < C.nt;
         if constexpr (PREC == 0) {
-            if (live) o = beyond64(qx, qy, qz, off, S.tx[t], S.ty[t], S.tz[t]);
+            if (live) o = beyond64(qx, qy, qz, offk, S.tx[t], S.ty[t], S.tz[t]);
         } else {
             bool unsure = false;
             if (live) {
@@ -539,14 +550,16 @@ __device__ void clip_by(ClipSmem<PREC, CAP> &S, int k, CellState &C, int lane)
                 const float s = fmaf(fqx, vx, fmaf(fqy, vy, fmaf(fqz, vz, -foff)));
                 const float mag = fabsf(fqx * vx) + fabsf(fqy * vy) + fabsf(fqz * vz) + foff;
                 const float B = fqn * V.w + 16.0f * 5.9604645e-8f * mag;
-                if (fabsf(s) > B) o = s > 0.0f;
+                // the margin is below 2^-19 B, so B (1 + 1e-5) still settles the sign
+                if (s > B * 1.00001f) o = true;
+                else if (s < -B) o = false;
                 else unsure = true;
             }
             const unsigned um = __ballot_sync(FULL, unsure);
             if (um) {
                 C.pred64 += __popc(um);
                 C.solve64 += __popc(um);
-                if (unsure) o = beyond_exact(S, S.tv[t], qx, qy, qz, off);
+                if (unsure) o = beyond_exact(S, S.tv[t], qx, qy, qz, offk);
             }
         }
         outm.put(c, __ballot_sync(FULL, o));

@@ -54,6 +54,49 @@ def test_tessellation_matches_oracle(oracle, ctx, case):
     assert abs(G["cell_volume"].sum() - np.prod(box)) <= 1e-11 * np.prod(box)
 
 
+def lattice_at(kind, m, offset):
+    """Exact lattice of m^3 cells in the unit box, basis shifted by `offset`
+    cells (0.1 and 1/3-like offsets make coordinates inexact in binary)."""
+    s = 1.0 / m
+    basis = {"sc": [(0, 0, 0)], "bcc": [(0, 0, 0), (0.5, 0.5, 0.5)],
+             "fcc": [(0, 0, 0), (0.5, 0.5, 0), (0.5, 0, 0.5), (0, 0.5, 0.5)]}[kind]
+    pts = [((i + b[0] + offset) * s, (j + b[1] + offset) * s, (k + b[2] + offset) * s)
+           for k in range(m) for j in range(m) for i in range(m) for b in basis]
+    return np.array(pts) % 1.0
+
+
+# (kind, cells per axis, basis offset, bin width): sizes and offsets whose
+# coordinates are not exact in binary, where every Voronoi vertex is shared by
+# more cells than three planes define (cube corners, rhombic-dodecahedron
+# vertices) and rounding gives one point several slightly different values
+LATTICES = [("sc", 6, 0.0, 1.0), ("sc", 12, 0.25, 1.25), ("sc", 24, 0.1, 1.0), ("bcc", 12, 0.5, 1.25),
+            ("fcc", 4, 0.1, 1.0), ("fcc", 6, 0.0, 1.25), ("fcc", 12, 0.25, 1.0)]
+
+
+@pytest.mark.parametrize("kind,m,offset,bin_scale", LATTICES)
+def test_exact_lattices_at_inexact_sizes_and_offsets(oracle, ctx, kind, m, offset, bin_scale):
+    """Perfect lattices: every cell is the lattice's Voronoi cell (cube, truncated
+    octahedron, rhombic dodecahedron): its volume 1/n, its face count 6, 14 or
+    12, and the mesh equals the oracle's (faces at or below the area threshold
+    excepted, as everywhere)."""
+    c, torch = ctx
+    pos = lattice_at(kind, m, offset)
+    n = len(pos)
+    box = np.ones(3)
+    c.set_config(bin_scale=bin_scale)
+    try:
+        mesh, P, G = H.gpu_tessellate(c, torch, pos, box)
+    finally:
+        c.set_config(bin_scale=1.0)
+    np.testing.assert_allclose(G["cell_volume"], 1.0 / n, rtol=1e-12, atol=0)
+    faces = {"sc": 6, "bcc": 14, "fcc": 12}[kind]
+    assert np.all(np.diff(G["inc_off"]) == faces)
+    H.check_incidence(G)
+    if n <= 4000:
+        T = oracle.tessellate(pos, box, 0 if n <= 1100 else 1)
+        H.compare_tessellations(oracle, T, G, pos, box, label=f"{kind}{m}+{offset}")
+
+
 def test_tessellation_is_deterministic(ctx):
     c, torch = ctx
     pos = WL.random_points(3000, seed=8)
