@@ -45,7 +45,6 @@ def parse():
                    help="default: fp64 for the shear layer, mixed for the ensemble")
     p.add_argument("--clip-filter", type=int, choices=[0, 1], default=1,
                    help="1: FP32-filtered clipping with exact FP64 fallback (same mesh bit for bit)")
-    p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--cpu-sample-side", type=int, default=24)
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -674,7 +673,7 @@ def run_ensemble(args, world, rank, local):
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
-        for _ in range(args.e2e_steps):
+        for _ in range(args.steps):
             pos.copy_(pos_h, non_blocking=True)
             U.copy_(U_h, non_blocking=True)
             ctx.mm_step_batched(pos, U, off, L, dt_out=dt)
@@ -683,7 +682,7 @@ def run_ensemble(args, world, rank, local):
         f1.record(stream)
         stream.synchronize()
         e2e_ms = f0.elapsed_time(f1)
-        _, e2e_ms = aggregate(e2e_ms, n_mine, args.e2e_steps, world)
+        _, e2e_ms = aggregate(e2e_ms, n_mine, args.steps, world)
         ctx.close()
     if rank == 0:
         nbytes = int(pos0.numel() * 8 + U0.numel() * 8)
@@ -701,7 +700,7 @@ def run_ensemble(args, world, rank, local):
                 "roofline_note": "per-kernel times are not separable inside the captured graph; the ncu launch "
                                  "list of this mode gives each kernel's share",
                 "cpu_baseline": None,
-                "e2e": {"value": n_all * args.e2e_steps / (e2e_ms / 1e3), "unit": UNIT,
+                "e2e": {"value": n_all * args.steps / (e2e_ms / 1e3), "unit": UNIT,
                         "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                         "note": "rank 0's share of the bytes"},
                 "gpu_launches": launches, "clocks": clocks,
@@ -793,21 +792,24 @@ def run_ours(args, world, rank, local):
         # ---- end to end through the ABI with host buffers: mm_step_host copies
         # the step's inputs up and its results back (page-locked memory, the
         # copies overlapped with the step inside the library)
+        # the same steps as the timed window: from its start state, args.steps steps
         pos_h = torch.empty_like(pos, device="cpu").pin_memory()
         U_h = torch.empty_like(U, device="cpu").pin_memory()
         pos_h.copy_(pos0.cpu())
         U_h.copy_(U0.cpu())
         ctx.mm_step_host(pos_h, U_h, w.box)  # untimed: the context's device copies are allocated here
+        pos_h.copy_(pos_w0.cpu())
+        U_h.copy_(U_w0.cpu())
         barrier()
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
-        for _ in range(args.e2e_steps):
+        for _ in range(args.steps):
             ctx.mm_step_host(pos_h, U_h, w.box)
         f1.record(stream)
         stream.synchronize()
         e2e_ms = f0.elapsed_time(f1)
-        e2e_value, e2e_ms = aggregate(e2e_ms, n, args.e2e_steps, world)
+        e2e_value, e2e_ms = aggregate(e2e_ms, n, args.steps, world)
         e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": int(pos.numel() * 8 + U.numel() * 8),
                "d2h_bytes_per_step": int(pos.numel() * 8 + U.numel() * 8)}
