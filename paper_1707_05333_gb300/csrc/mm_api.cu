@@ -230,8 +230,10 @@ static mm_status read_status(mm_ctx *c)
     if (s.flags & ST_EINVAL)
         return fail(c, MM_EINVAL, "generator %d lies outside [0, box) or is not finite", s.bad_cell);
     if (s.flags & ST_EDEGEN)
-        return fail(c, MM_EDEGENERATE, "cell %d: inconsistent cut (degenerate or coincident generators)",
-                    s.bad_cell);
+        return fail(c, MM_EDEGENERATE, "cell %d: two generators at one position", s.bad_cell);
+    if (s.flags & ST_EDEGEN_CUT)
+        return fail(c, MM_EDEGENERATE,
+                    "cell %d: inconsistent cut under both tie rules (near-degenerate generators)", s.bad_cell);
     if (s.flags & ST_ECAP_MESH)
         return fail(c, MM_ECAPACITY, "the batch has more faces than its fixed capacity (%lld faces, %lld incidences)",
                     (long long)c->fcap, (long long)c->icap);

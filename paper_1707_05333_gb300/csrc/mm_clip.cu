@@ -408,6 +408,7 @@ struct CellState {
     float slack;    // 2e-6 max(L): the position-rounding term of that margin
     int err;
     int cuts;
+    bool strict;     // tie rule: strict (q.v > o) instead of the margin (retry of an inconsistent cut)
     // work counters (warp-uniform), reported when the caller collects stats
     unsigned pred64, solve64, fan64, tested;
 };
@@ -523,8 +524,12 @@ __device__ void clip_by(ClipSmem<PREC, CAP> &S, int k, CellState &C, int lane)
     // bit pattern): a vertex exactly on the plane (co-spherical generators,
     // exact lattices) stays, whatever rounding its several representations
     // carry, so copies of one point are never split across the plane.  The
-    // planes themselves, and every vertex solved from them, are exact.
-    const double offk = __longlong_as_double(__double_as_longlong(off) + (1LL << 13));
+    // planes themselves, and every vertex solved from them, are exact.  The
+    // margin can itself split distinct points that lie within it of a plane
+    // (lattices perturbed by about 1e-12..1e-9 of a spacing); a cell whose cut
+    // is then inconsistent is clipped again with the strict rule (C.strict),
+    // which decides those by the geometry.
+    const double offk = C.strict ? off : __longlong_as_double(__double_as_longlong(off) + (1LL << 13));
     const int nchunk = (C.nt + 31) >> 5;
     ChunkMask<CAP::TM> outm;
     C.tested++;
@@ -644,7 +649,7 @@ __device__ void clip_by(ClipSmem<PREC, CAP> &S, int k, CellState &C, int lane)
     xs = warp_or(xs);
     ys = warp_or(ys);
     if (nnew > CAP::NS) { C.err |= ST_ECAP_STAGE; return; }
-    if (nnew < 3 || xs != ys || xs.popc() != nnew) { C.err |= ST_EDEGEN; return; }
+    if (nnew < 3 || xs != ys || xs.popc() != nnew) { C.err |= ST_EDEGEN_CUT; return; }
     const int nrem = outm.count();
     const int nkept = C.nt - nrem;
     if (nkept + nnew > CAP::TM) { C.err |= ST_ECAP_TRI; return; }
@@ -854,11 +859,14 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int64_t w;
+    bool strict = false;
     if constexpr (CAP::BIG) {
         const int nr = *(volatile int *)&st->nretry;
         if (blockIdx.x == 0 && threadIdx.x == 0 && nr > sl.orows) atomicOr(&st->flags, ST_ECAP_RETRY);
         if ((int64_t)blockIdx.x >= (nr < sl.orows ? (int64_t)nr : sl.orows)) return;
-        w = sl.retry[blockIdx.x];
+        const int e = sl.retry[blockIdx.x];
+        strict = e < 0;
+        w = strict ? ~e : e;
     } else {
         w = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
         if (w >= n) return;
@@ -936,6 +944,7 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
     C.slack = 2e-6f * fmaxf(g.Lf[0], fmaxf(g.Lf[1], g.Lf[2]));
     C.err = 0;
     C.cuts = 0;
+    C.strict = strict;
     C.pred64 = C.solve64 = C.fan64 = C.tested = 0;
 
     // Home bin of p in FP32 (the FP32 copy of p from the bin sort), and the
@@ -1160,7 +1169,7 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
                 y = z;
             }
             fan += cnt;
-            if (!ok) { C.err |= ST_EDEGEN; continue; }
+            if (!ok) { C.err |= ST_EDEGEN_CUT; continue; }
             const double aw = fabs(W);
             const double qn2 = 2.0 * S.po[p];  // |q|^2
             // 1 / q_k and 1 / (3 W) from one reciprocal of 3 W q_k; a face
@@ -1225,8 +1234,9 @@ k_clip(const double4_32a *__restrict__ sorted, const float4 *__restrict__ sorted
         if (C.err) {
             nface = 0;
             if (!CAP::BIG && (C.err & ~ST_RETRYABLE) == 0) {
-                // over a capacity of this instance only: the large one clips it again
-                sl.retry[atomicAdd(&st->nretry, 1)] = (int)w;
+                // over a capacity of this instance, or an inconsistent cut: the
+                // large one clips it again (with the strict tie rule for the latter)
+                sl.retry[atomicAdd(&st->nretry, 1)] = (C.err & ST_EDEGEN_CUT) ? ~(int)w : (int)w;
             } else {
                 atomicOr(&st->flags, C.err);
                 atomicExch(&st->bad_cell, self);

@@ -38,12 +38,16 @@ enum : int {
     ST_ECAP_STAGE = 16,
     ST_ECAP_FACE = 32,
     ST_ECAP_RING = 64,
-    ST_EDEGEN = 128,
+    ST_EDEGEN = 128,     // two generators at one position
     ST_ECAP_MESH = 256,  // more unique faces or incidences than a fixed capacity (graph mode)
     ST_ECAP_RETRY = 512, // more retried cells than overflow rows (graph mode)
+    ST_EDEGEN_CUT = 1024, // a cut whose removed vertices are not a cap (near-degenerate generators)
 };
-// Capacity flags that send a cell to the large clipper instead of failing.
-constexpr int ST_RETRYABLE = ST_ECAP_CAND | ST_ECAP_PLANE | ST_ECAP_TRI | ST_ECAP_STAGE | ST_ECAP_FACE | ST_ECAP_RING;
+// Flags that send a cell to the large clipper instead of failing: its
+// capacities, and an inconsistent cut, which the large clipper retries with
+// the strict tie rule (the retry entry is then ~w instead of w).
+constexpr int ST_RETRYABLE =
+    ST_ECAP_CAND | ST_ECAP_PLANE | ST_ECAP_TRI | ST_ECAP_STAGE | ST_ECAP_FACE | ST_ECAP_RING | ST_EDEGEN_CUT;
 
 struct DevStatus {
     int flags;
@@ -82,7 +86,7 @@ struct Slots {         // per-cell face slots written by the clipper
     unsigned char *osh; // [orows*MAXF_BIG]
     double *oarea;      // [orows*MAXF_BIG]
     double *ofc;        // [3][orows*MAXF_BIG]
-    int *retry;         // [n] binned indices of the retried cells, in the order they were found
+    int *retry;         // [n] binned indices w of the retried cells (~w: retry with the strict tie rule)
 };
 
 // Face confirmation state of the overflow rows: two mask words and a partner
