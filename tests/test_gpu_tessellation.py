@@ -107,6 +107,56 @@ def test_exact_lattices_at_inexact_sizes_and_offsets(oracle, ctx, kind, m, offse
         H.compare_tessellations(oracle, T, G, pos, box, label=f"{kind}{m}+{offset}")
 
 
+def _extreme(name):
+    rng = np.random.default_rng(21)
+    if name == "generators_on_a_plane":
+        u = rng.uniform(0, 1, size=(600, 2))
+        return np.column_stack([u, np.full(600, 0.5)]), np.ones(3)
+    if name == "generators_on_a_line":
+        return np.column_stack([rng.uniform(0, 1, 200), np.full(200, 0.3), np.full(200, 0.7)]), np.ones(3)
+    if name == "hcp_lattice":
+        m, a = 6, 1.0 / 6
+        pts = [((i + 0.5 * (j % 2) + 0.5 * (k % 2)) * a, (j + (k % 2) / 3.0) * a * np.sqrt(3) / 2,
+                k * a * np.sqrt(2.0 / 3.0)) for k in range(m) for j in range(m) for i in range(m)]
+        box = np.array([1.0, m * a * np.sqrt(3) / 2, m * a * np.sqrt(2.0 / 3.0)])
+        return np.array(pts) % box, box
+    if name == "flat_box_100_to_1":
+        box = np.array([1.0, 1.0, 0.01])
+        return rng.uniform(0, 1, size=(1500, 3)) * box, box
+    if name == "tight_cluster_in_a_large_box":
+        return 0.5 + 1e-3 * rng.uniform(-1, 1, size=(800, 3)), np.ones(3)
+    if name == "lattice_and_a_near_centred_point":
+        return np.concatenate([lattice_at("sc", 6, 0.0), [[0.5 + 1e-12, 0.5, 0.5]]]) % 1.0, np.ones(3)
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name", ["generators_on_a_plane", "generators_on_a_line", "hcp_lattice", "flat_box_100_to_1",
+                                  "tight_cluster_in_a_large_box", "lattice_and_a_near_centred_point"])
+def test_degenerate_and_extreme_generator_sets(oracle, ctx, name):
+    """Generators on one plane or one line (cells are prisms and slabs through
+    the whole box), the hcp lattice (co-spherical neighbours), a box 100 times
+    thinner than wide, a cluster 1e-3 across in a unit box (cells over nine
+    decades of volume), a cubic lattice with one more point 1e-12 off a cube
+    corner: the tessellation closes (volumes sum to the box) and equals the
+    oracle's.  The last case is checked for closure only: there the oracle's
+    own volumes sum to the box only to 1.5e-8 (its clipping tolerance meets
+    the point 1e-12 off the corner), while the device closes it to rounding."""
+    c, torch = ctx
+    pos, box = _extreme(name)
+    mesh, P, G = H.gpu_tessellate(c, torch, pos, box)
+    H.check_incidence(G)
+    assert abs(G["cell_volume"].sum() - np.prod(box)) <= 1e-12 * np.prod(box)
+    assert np.all(G["cell_volume"] > 0)
+    if name == "lattice_and_a_near_centred_point":
+        return
+    T = oracle.tessellate(pos, box, 0 if len(pos) <= 1100 else 1)
+    # the cluster's outer cells reach 500 times their generators' spacing: their
+    # vertices come from nearly parallel planes (condition numbers near 1e5), and
+    # two FP64 computations of a face agree to 1e-8 of it there, not 1e-9
+    rtol = 1e-8 if name == "tight_cluster_in_a_large_box" else H.GEOM_RTOL
+    H.compare_tessellations(oracle, T, G, pos, box, geom_rtol=rtol, label=name)
+
+
 def test_tessellation_is_deterministic(ctx):
     c, torch = ctx
     pos = WL.random_points(3000, seed=8)
