@@ -322,154 +322,6 @@ __device__ __noinline__ bool beyond_exact(const S_t &S, unsigned v, double qx, d
     vertex64(S, v & 255u, (v >> 8) & 255u, (v >> 16) & 255u, x, y, z);
     return beyond64(qx, qy, qz, off, x, y, z);
 }
-// ---- exact plane test (the large instance's retry with the strict rule)
-//
-// Vertex (a, b, c) lies beyond plane k (x.q_k <= o_k) when s = q_k.v - o_k > 0,
-// v the exact intersection of the three planes.  With N the 4x4 matrix of
-// rows (q_i, o_i), i = a, b, c, k, and M = (q_a; q_b; q_c), Schur's formula
-// gives det N = det M (o_k - q_k.v) = -det M s, so sign(s) = -sign(det N)
-// sign(det M): a polynomial in the planes' doubles, whose sign floating-point
-// expansions give exactly (Shewchuk, "Adaptive precision floating-point
-// arithmetic and fast robust geometric predicates", 1997: sums and products
-// of doubles carried as nonoverlapping sums of doubles).  An FP64 evaluation
-// with a bound on its rounding decides first; the expansions run only when
-// it cannot.  s = 0 (a vertex exactly on the plane) is not beyond, for every
-// copy of that point alike.
-namespace xp {
-__device__ __forceinline__ void two_sum(double a, double b, double &x, double &y)
-{
-    x = __dadd_rn(a, b);
-    const double bv = __dsub_rn(x, a), av = __dsub_rn(x, bv);
-    y = __dadd_rn(__dsub_rn(a, av), __dsub_rn(b, bv));
-}
-__device__ __forceinline__ void two_prod(double a, double b, double &x, double &y)
-{
-    x = __dmul_rn(a, b);
-    y = __fma_rn(a, b, -x);
-}
-// h = e + f (components in increasing magnitude, zeros dropped); returns its length
-__device__ int sum(int ne, const double *e, int nf, const double *f, double *h)
-{
-    // merge by magnitude, then carry a running sum through the merged sequence
-    double g[192];
-    int i = 0, j = 0, n = 0;
-    while (i < ne || j < nf) {
-        if (j >= nf || (i < ne && fabs(e[i]) < fabs(f[j]))) g[n++] = e[i++];
-        else g[n++] = f[j++];
-    }
-    int m = 0;
-    double q = g[0];
-    for (int k = 1; k < n; ++k) {
-        double x, y;
-        two_sum(q, g[k], x, y);
-        if (y != 0.0) h[m++] = y;
-        q = x;
-    }
-    if (q != 0.0 || m == 0) h[m++] = q;
-    return m;
-}
-// h = b e; returns its length
-__device__ int scale(int ne, const double *e, double b, double *h)
-{
-    int m = 0;
-    double q, y;
-    two_prod(e[0], b, q, y);
-    if (y != 0.0) h[m++] = y;
-    for (int k = 1; k < ne; ++k) {
-        double p1, p0, t, u;
-        two_prod(e[k], b, p1, p0);
-        two_sum(q, p0, t, u);
-        if (u != 0.0) h[m++] = u;
-        two_sum(p1, t, q, u);
-        if (u != 0.0) h[m++] = u;
-    }
-    if (q != 0.0 || m == 0) h[m++] = q;
-    return m;
-}
-__device__ __forceinline__ int sign(int n, const double *e) { return e[n - 1] > 0.0 ? 1 : (e[n - 1] < 0.0 ? -1 : 0); }
-// u . (v x w) exactly, as an expansion of at most 24 components
-__device__ int det3(const double *u, const double *v, const double *w, double *h)
-{
-    double acc[24], tmp[24], cr[4], sc[8];
-    int na = 0;
-    for (int d = 0; d < 3; ++d) {
-        const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
-        double a1, a0, b1, b0;
-        two_prod(v[d1], w[d2], a1, a0);
-        two_prod(v[d2], w[d1], b1, b0);
-        const double pa[2] = {a0, a1}, pb[2] = {-b0, -b1};
-        const int nc = sum(2, pa, 2, pb, cr);
-        const int ns = scale(nc, cr, u[d], sc);
-        if (na == 0) {
-            for (int k = 0; k < ns; ++k) acc[k] = sc[k];
-            na = ns;
-        } else {
-            const int nt = sum(na, acc, ns, sc, tmp);
-            for (int k = 0; k < nt; ++k) acc[k] = tmp[k];
-            na = nt;
-        }
-    }
-    for (int k = 0; k < na; ++k) h[k] = acc[k];
-    return na;
-}
-// FP64 u . (v x w) and the sum of the absolute values of its terms
-__device__ __forceinline__ double det3_fp(const double *u, const double *v, const double *w, double &perm)
-{
-    double d = 0.0;
-    perm = 0.0;
-    for (int k = 0; k < 3; ++k) {
-        const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
-        d += u[k] * (v[k1] * w[k2] - v[k2] * w[k1]);
-        perm += fabs(u[k]) * (fabs(v[k1] * w[k2]) + fabs(v[k2] * w[k1]));
-    }
-    return d;
-}
-}  // namespace xp
-
-template <class S_t>
-__device__ __noinline__ bool beyond_exact_pred(const S_t &S, unsigned v, double kx, double ky, double kz, double ko)
-{
-    const int ia = v & 255u, ib = (v >> 8) & 255u, ic = (v >> 16) & 255u;
-    const double qa[3] = {S.px[ia], S.py[ia], S.pz[ia]}, qb[3] = {S.px[ib], S.py[ib], S.pz[ib]};
-    const double qc[3] = {S.px[ic], S.py[ic], S.pz[ic]}, qk[3] = {kx, ky, kz};
-    const double oa = S.po[ia], ob = S.po[ib], oc = S.po[ic];
-    // det N = -o_a det(q_b,q_c,q_k) + o_b det(q_a,q_c,q_k) - o_c det(q_a,q_b,q_k) + o_k det(q_a,q_b,q_c)
-    const double *r[4][3] = {{qb, qc, qk}, {qa, qc, qk}, {qa, qb, qk}, {qa, qb, qc}};
-    const double co[4] = {-oa, ob, -oc, ko};
-    double dN = 0.0, pN = 0.0, dM = 0.0, pM = 0.0;
-    for (int i = 0; i < 4; ++i) {
-        double pp;
-        const double d3 = xp::det3_fp(r[i][0], r[i][1], r[i][2], pp);
-        dN += co[i] * d3;
-        pN += fabs(co[i]) * pp;
-        if (i == 3) { dM = d3; pM = pp; }
-    }
-    // first-order rounding of these evaluations stays below 16 u of the sums of
-    // absolute terms (u = 2^-53); the factor covers the rounding of the sums
-    const double eps = 16.0 * 1.1102230246251565e-16 * 1.001;
-    int sN = fabs(dN) > eps * pN ? (dN > 0.0 ? 1 : -1) : 2;
-    int sM = fabs(dM) > eps * pM ? (dM > 0.0 ? 1 : -1) : 2;
-    if (sN == 2 || sM == 2) {
-        double t[24], u[48], acc[192], tmp[192];
-        int na = 0;
-        for (int i = 0; i < 4; ++i) {
-            const int n3 = xp::det3(r[i][0], r[i][1], r[i][2], t);
-            if (i == 3) sM = xp::sign(n3, t);
-            const int ns = xp::scale(n3, t, co[i], u);
-            if (na == 0) {
-                for (int k = 0; k < ns; ++k) acc[k] = u[k];
-                na = ns;
-            } else {
-                const int nt = xp::sum(na, acc, ns, u, tmp);
-                for (int k = 0; k < nt; ++k) acc[k] = tmp[k];
-                na = nt;
-            }
-        }
-        sN = xp::sign(na, acc);
-    }
-    return -sN * sM > 0;
-}
-
 template <class S_t>
 __device__ __noinline__ void vertex64_call(const S_t &S, int a, int b, int c, double &x, double &y, double &z)
 {
@@ -675,9 +527,8 @@ __device__ void clip_by(ClipSmem<PREC, CAP> &S, int k, CellState &C, int lane)
     // planes themselves, and every vertex solved from them, are exact.  The
     // margin can itself split distinct points that lie within it of a plane
     // (lattices perturbed by about 1e-12..1e-9 of a spacing); a cell whose cut
-    // is then inconsistent is clipped again by the large instance with the
-    // strict rule (C.strict): whatever the FP32 bound leaves open is decided
-    // exactly (beyond_exact_pred).
+    // is then inconsistent is clipped again with the strict rule (C.strict),
+    // which decides those by the geometry.
     const double offk = C.strict ? off : __longlong_as_double(__double_as_longlong(off) + (1LL << 13));
     const int nchunk = (C.nt + 31) >> 5;
     ChunkMask<CAP::TM> outm;
@@ -695,24 +546,10 @@ __device__ void clip_by(ClipSmem<PREC, CAP> &S, int k, CellState &C, int lane)
         const int t = c * 32 + lane;
         const bool live = t < C.nt;
         if constexpr (PREC == 0) {
-            if constexpr (CAP::BIG) {
-                if (live) {
-                    if (C.strict) o = beyond_exact_pred(S, S.tv[t], qx, qy, qz, off);
-                    else o = beyond64(qx, qy, qz, offk, S.tx[t], S.ty[t], S.tz[t]);
-                }
-            } else {
-                if (live) o = beyond64(qx, qy, qz, offk, S.tx[t], S.ty[t], S.tz[t]);
-            }
+            if (live) o = beyond64(qx, qy, qz, offk, S.tx[t], S.ty[t], S.tz[t]);
         } else {
             bool unsure = false;
-            // the large instance's strict retry decides every test exactly: the
-            // FP32 bound assumes the FP64 solves behind ill-conditioned FP32
-            // vertices are exact, which near-coincident generators defeat
-            bool exact_all = false;
-            if constexpr (CAP::BIG) exact_all = C.strict;
-            if (exact_all) {
-                if (live) o = beyond_exact_pred(S, S.tv[t], qx, qy, qz, off);
-            } else if (live) {
+            if (live) {
                 const float4 V = S.tf[t];
                 const float vx = V.x, vy = V.y, vz = V.z;
                 const float s = fmaf(fqx, vx, fmaf(fqy, vy, fmaf(fqz, vz, -foff)));
