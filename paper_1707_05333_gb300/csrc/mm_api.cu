@@ -231,9 +231,6 @@ static mm_status read_status(mm_ctx *c)
         return fail(c, MM_EINVAL, "generator %d lies outside [0, box) or is not finite", s.bad_cell);
     if (s.flags & ST_EDEGEN)
         return fail(c, MM_EDEGENERATE, "cell %d: two generators at one position", s.bad_cell);
-    if (s.flags & ST_EDEGEN_CUT)
-        return fail(c, MM_EDEGENERATE,
-                    "cell %d: inconsistent cut under both tie rules (near-degenerate generators)", s.bad_cell);
     if (s.flags & ST_ECAP_MESH)
         return fail(c, MM_ECAPACITY, "the batch has more faces than its fixed capacity (%lld faces, %lld incidences)",
                     (long long)c->fcap, (long long)c->icap);
@@ -242,7 +239,9 @@ static mm_status read_status(mm_ctx *c)
                     "%d cells overflowed the main clipper's per-cell lists, more than the %lld overflow rows "
                     "reserved for a captured batch",
                     s.nretry, (long long)c->orows);
-    // name every per-cell capacity that overflowed, with its limit
+    // name every per-cell capacity that overflowed, with its limit (before the
+    // mesh inconsistency: a cell left without faces by an overflow leaves its
+    // neighbours' faces unconfirmed too)
     struct Cap {
         int bit;
         const char *what;
@@ -262,8 +261,11 @@ static mm_status read_status(mm_ctx *c)
         if ((s.flags & k.bit) && used < sizeof(list))
             used += (size_t)snprintf(list + used, sizeof(list) - used, "%s%s (limit %d)", used ? ", " : "", k.what,
                                      k.limit);
-    return fail(c, MM_ECAPACITY, "cell %d exceeded a per-cell capacity: %s", s.bad_cell,
-                used ? list : "unknown");
+    if (used || !(s.flags & ST_EDEGEN_CUT))
+        return fail(c, MM_ECAPACITY, "cell %d exceeded a per-cell capacity: %s", s.bad_cell, used ? list : "unknown");
+    return fail(c, MM_EDEGENERATE,
+                "cell %d: inconsistent mesh (near-degenerate generators): a cut inconsistent under both tie rules, "
+                "or a face its neighbour does not have", s.bad_cell);
 }
 
 static void fill_mesh(const mm_ctx *c, mm_mesh *out)
@@ -492,7 +494,7 @@ static mm_status tess_enqueue(mm_ctx *c, const double *pos, bool fixed)
     stage_mark(c, MM_STAGE_CLIP, false);
     c->launches += 2;
     stage_mark(c, MM_STAGE_FACES, true);
-    launch_face_confirm(n, sl, ovf(), P<unsigned long long>(c->emit_mask), P<unsigned long long>(c->conf_mask),
+    launch_face_confirm(n, sl, ovf(), boxes, cbox, c->st, P<unsigned long long>(c->emit_mask), P<unsigned long long>(c->conf_mask),
                         P<signed char>(c->partner), P<int>(c->emit_cnt), P<int>(c->conf_cnt), s);
     launch_scan(P<int>(c->emit_cnt), P<int>(c->face_off), n, P<int>(c->scan_tmp), s);
     launch_scan(P<int>(c->conf_cnt), P<int>(c->inc_off), n, P<int>(c->scan_tmp), s);
@@ -506,16 +508,20 @@ static mm_status tess_enqueue(mm_ctx *c, const double *pos, bool fixed)
             CK(cudaMemcpyAsync(&c->cnt_host[0], P<int>(c->face_off) + n, sizeof(int), cudaMemcpyDeviceToHost, s));
             CK(cudaMemcpyAsync(&c->cnt_host[1], P<int>(c->inc_off) + n, sizeof(int), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
-            if (attempt > 0 || c->st_host->flags != ST_ECAP_RETRY) break;
             // more cells overflowed than there were overflow rows: grow them to
-            // the count and re-clip the list (its first rows again, harmlessly)
+            // the count and re-clip the list (its first rows again, harmlessly).
+            // The cells not re-clipped yet had no faces, so their neighbours'
+            // faces went unconfirmed: ST_EDEGEN_CUT alongside is expected, and
+            // the second pass, from cleared flags, decides it again.
+            const int fl = c->st_host->flags;
+            if (attempt > 0 || !(fl & ST_ECAP_RETRY) || (fl & ~(ST_ECAP_RETRY | ST_EDEGEN_CUT))) break;
             if ((r = ensure_overflow(c, c->st_host->nretry))) return r;
             sl = slots();
             CK(cudaMemsetAsync(&c->st->flags, 0, sizeof(int), s));
             launch_clip_big(P<double4_32a>(c->sorted), P<float4>(c->sortedf), P<int>(c->bin_start), n, boxes, cbox,
                             prec, c->cfg.collect_stats, c->cfg.cand_cap, P<double>(c->vol), P<double>(c->cen), sl,
                             c->st, s);
-            launch_face_confirm(n, sl, ovf(), P<unsigned long long>(c->emit_mask),
+            launch_face_confirm(n, sl, ovf(), boxes, cbox, c->st, P<unsigned long long>(c->emit_mask),
                                 P<unsigned long long>(c->conf_mask), P<signed char>(c->partner), P<int>(c->emit_cnt),
                                 P<int>(c->conf_cnt), s);
             launch_scan(P<int>(c->emit_cnt), P<int>(c->face_off), n, P<int>(c->scan_tmp), s);

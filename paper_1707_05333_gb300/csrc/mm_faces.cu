@@ -82,8 +82,15 @@ __device__ __forceinline__ int find_partner(const int *nb, const unsigned char *
 // an overflow row keeps two mask words there; the low word also goes to the
 // per-cell mask, which is all a neighbour's partner slot below 64 needs.
 // OVF false: no cell was re-clipped, every row is a main row.
+//
+// A face the neighbour does not confirm is dropped, which is right for the
+// faces near the area threshold that one side keeps and the other drops.  A
+// face far above it (1e4 times the threshold) that the neighbour lacks means
+// the two cells disagree on the mesh (near-degenerate generators): that is
+// reported (ST_EDEGEN_CUT, cell i) instead of returned.
 template <bool OVF>
 __device__ __forceinline__ void face_confirm_cell(int64_t n, int64_t i, int lane, const Slots &sl, const OvfFaces &ov,
+                                                  double amin, DevStatus *st,
                                                   unsigned long long *__restrict__ emit_mask,
                                                   unsigned long long *__restrict__ conf_mask,
                                                   signed char *__restrict__ partner, int *__restrict__ emit_cnt,
@@ -93,7 +100,7 @@ __device__ __forceinline__ void face_confirm_cell(int64_t n, int64_t i, int lane
     if constexpr (OVF) {
         r = row_of(sl, n, i);
     } else {
-        r.nb = sl.nb; r.sh = sl.sh; r.base = i * MAXF; r.cnt = sl.cnt[i]; r.orow = -1;
+        r.nb = sl.nb; r.sh = sl.sh; r.area = sl.area; r.base = i * MAXF; r.cnt = sl.cnt[i]; r.orow = -1;
     }
     signed char *const part = (!OVF || r.orow < 0) ? partner : ov.partner;
     unsigned long long em0 = 0, cm0 = 0, em1 = 0, cm1 = 0;
@@ -111,6 +118,10 @@ __device__ __forceinline__ void face_confirm_cell(int64_t n, int64_t i, int lane
             m = find_partner(sl.onb + ob, sl.osh + ob, sl.ocnt[-cj - 1], (int)i, want);
         }
         part[s] = (signed char)m;
+        if (m < 0 && amin > 0.0 && r.area[s] > 1e4 * amin) {
+            atomicOr(&st->flags, ST_EDEGEN_CUT);
+            atomicExch(&st->bad_cell, (int)i);
+        }
         if (m >= 0) {
             const unsigned long long bit = 1ull << (k & 63);
             const bool mine = i < j || (i == j && code > 13);
@@ -146,7 +157,8 @@ __device__ __forceinline__ void face_confirm_cell(int64_t n, int64_t i, int lane
     conf_cnt[i] = __popcll(cm0) + (OVF ? __popcll(cm1) : 0);
 }
 
-__global__ void k_face_confirm(int64_t n, Slots sl, OvfFaces ov, unsigned long long *__restrict__ emit_mask,
+__global__ void k_face_confirm(int64_t n, Slots sl, OvfFaces ov, const BoxDev *__restrict__ boxes,
+                               const int *__restrict__ cbox, DevStatus *st, unsigned long long *__restrict__ emit_mask,
                                unsigned long long *__restrict__ conf_mask, signed char *__restrict__ partner,
                                int *__restrict__ emit_cnt, int *__restrict__ conf_cnt)
 {
@@ -155,10 +167,11 @@ __global__ void k_face_confirm(int64_t n, Slots sl, OvfFaces ov, unsigned long l
     const int lane = threadIdx.x % CONFIRM_LANES;
     const int64_t i = g < n ? g : n - 1;
     const bool live = g < n;
-    if (*ov.nretry == 0) face_confirm_cell<false>(n, i, live ? lane : MAXF_BIG, sl, ov, emit_mask, conf_mask,
-                                                  partner, emit_cnt, conf_cnt);
-    else face_confirm_cell<true>(n, i, live ? lane : MAXF_BIG, sl, ov, emit_mask, conf_mask, partner, emit_cnt,
-                                 conf_cnt);
+    const double amin = boxes[cbox[i]].amin;
+    if (*ov.nretry == 0) face_confirm_cell<false>(n, i, live ? lane : MAXF_BIG, sl, ov, amin, st, emit_mask,
+                                                  conf_mask, partner, emit_cnt, conf_cnt);
+    else face_confirm_cell<true>(n, i, live ? lane : MAXF_BIG, sl, ov, amin, st, emit_mask, conf_mask, partner,
+                                 emit_cnt, conf_cnt);
 }
 
 // The face records and incidences of cell i's confirmed slots, one lane per
@@ -281,12 +294,13 @@ __global__ void k_face_write(int64_t n, const double *__restrict__ pos, const Bo
                                inc_face);
 }
 
-void launch_face_confirm(int64_t n, Slots sl, OvfFaces ov, unsigned long long *emit_mask,
-                         unsigned long long *conf_mask, signed char *partner, int *emit_cnt, int *conf_cnt,
-                         cudaStream_t s)
+void launch_face_confirm(int64_t n, Slots sl, OvfFaces ov, const BoxDev *boxes, const int *cbox, DevStatus *st,
+                         unsigned long long *emit_mask, unsigned long long *conf_mask, signed char *partner,
+                         int *emit_cnt, int *conf_cnt, cudaStream_t s)
 {
     const int64_t nb = (n * CONFIRM_LANES + 127) / 128;
-    k_face_confirm<<<(unsigned)nb, 128, 0, s>>>(n, sl, ov, emit_mask, conf_mask, partner, emit_cnt, conf_cnt);
+    k_face_confirm<<<(unsigned)nb, 128, 0, s>>>(n, sl, ov, boxes, cbox, st, emit_mask, conf_mask, partner, emit_cnt,
+                                                conf_cnt);
 }
 
 void launch_face_write(int64_t n, const double *pos, const BoxDev *boxes, const int *cbox, Slots sl, OvfFaces ov,

@@ -122,9 +122,11 @@ void launch_clip_big(const double4_32a *sorted, const float4 *sortedf, const int
                      const BoxDev *boxes, const int *cbox, int precision, int collect, int cand_cap, double *vol,
                      double *cen, Slots sl, DevStatus *st, cudaStream_t s);
 
-void launch_face_confirm(int64_t n, Slots sl, OvfFaces ov, unsigned long long *emit_mask,
-                         unsigned long long *conf_mask, signed char *partner, int *emit_cnt, int *conf_cnt,
-                         cudaStream_t s);
+// (also reports ST_EDEGEN_CUT for a face far above the area threshold that
+// the neighbour does not have)
+void launch_face_confirm(int64_t n, Slots sl, OvfFaces ov, const BoxDev *boxes, const int *cbox, DevStatus *st,
+                         unsigned long long *emit_mask, unsigned long long *conf_mask, signed char *partner,
+                         int *emit_cnt, int *conf_cnt, cudaStream_t s);
 void launch_face_write(int64_t n, const double *pos, const BoxDev *boxes, const int *cbox, Slots sl, OvfFaces ov,
                        const unsigned long long *emit_mask, const unsigned long long *conf_mask,
                        const signed char *partner, const int *face_off, const int *inc_off,
