@@ -949,11 +949,19 @@ mm_status mm_step_host(mm_ctx *c, double *pos, double *U, int64_t n, const doubl
     if ((r = ensure(c, c->h_pos, pbytes)) || (r = ensure(c, c->h_U, ubytes)) || (r = ensure(c, c->h_dt, sizeof(double))))
         return r;
     if (!c->copy_stream) {
-        CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
-        CK(cudaEventCreateWithFlags(&c->ev_start, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&c->ev_u_in, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&c->ev_u_done, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&c->ev_u_out, cudaEventDisableTiming));
+        // all or nothing, so that a later call never meets half of them
+        cudaStream_t cs = nullptr;
+        cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            for (cudaEvent_t x : ev)
+                if (x) cudaEventDestroy(x);
+            if (cs) cudaStreamDestroy(cs);
+            return fail(c, MM_ECUDA, "copy stream: %s", cudaGetErrorString(e));
+        }
+        c->copy_stream = cs;
+        c->ev_start = ev[0]; c->ev_u_in = ev[1]; c->ev_u_done = ev[2]; c->ev_u_out = ev[3];
     }
     cudaStream_t s = c->stream, s2 = c->copy_stream;
     double *pd = P<double>(c->h_pos), *Ud = P<double>(c->h_U), *dtd = P<double>(c->h_dt);
