@@ -66,3 +66,39 @@ def test_committed_clip_traffic_matches_the_current_clipper_or_is_absent():
         # a stale figure is withheld at run time; this flags it in review
         assert bench.CLIP_TRAFFIC["sha256_16"] == bench.clip_sources_digest()
         assert 64 <= bench.CLIP_TRAFFIC["bytes_per_cell"] <= 4000
+
+
+def test_window_counts_average_every_step_of_the_window():
+    """The method's work of the clipper is counted on every step of the timed
+    window (the window replayed from its start state): counters averaged over
+    the steps, maxima kept as maxima, the direct clipper used for the counts
+    and the caller's clipper restored for the steps."""
+    import bench
+
+    class FakeCtx:
+        def __init__(self):
+            self.cfg = {}
+            self.k = 0
+            self.steps = 0
+            self.tess_filters = []
+
+        def set_config(self, **kw):
+            self.cfg.update(kw)
+
+        def mm_tessellate(self, pos, box):
+            self.tess_filters.append(self.cfg.get("clip_filter"))
+
+        def mm_tess_stats(self):
+            self.k += 1
+            return {"cuts": 10 * self.k, "fp64_plane_tests": 100.0 * self.k, "max_vertices": 30 + self.k}
+
+        def mm_step(self, pos, U, box):
+            assert self.cfg.get("collect_stats") == 0 and self.cfg.get("clip_filter") == 1
+            self.steps += 1
+
+    ctx = FakeCtx()
+    out = bench.window_direct_counts(ctx, None, None, None, 4, 1)
+    assert ctx.steps == 4 and ctx.tess_filters == [0, 0, 0, 0]
+    assert out["cuts"] == pytest.approx((10 + 20 + 30 + 40) / 4)
+    assert out["fp64_plane_tests"] == pytest.approx(250.0)
+    assert out["max_vertices"] == 34
