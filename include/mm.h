@@ -51,7 +51,7 @@ typedef enum {
     MM_ENOMEM = 2,      /* device allocation failed                                  */
     MM_ECAPACITY = 3,   /* a cell exceeded a fixed per-cell list even when re-clipped  */
                         /* with the large lists (see mm_tessellate)                   */
-    MM_EDEGENERATE = 4, /* clipping met an inconsistent (numerically degenerate) cut */
+    MM_EDEGENERATE = 4, /* coincident generators, or an inconsistent mesh (near-degenerate generators) */
     MM_ECUDA = 5,       /* a CUDA runtime call failed                               */
     MM_ETIMEOUT = 6     /* reserved: a bounded device wait gave up                   */
 } mm_status;
@@ -154,7 +154,15 @@ mm_status mm_set_config(mm_ctx *ctx, const mm_config *cfg);
  * large lists fails the call with MM_ECAPACITY.  Overflow rows are grown to
  * the number of such cells here; a captured batch (mm_step_batched) has 256
  * and reports more through mm_sync_status.  Two generators at the same
- * position (or at the same periodic image) are MM_EDEGENERATE. */
+ * position (or at the same periodic image) are MM_EDEGENERATE.
+ * Ties: a vertex lies beyond a plane only past a margin of 2^-40..2^-39 of
+ * the plane's offset, so generators on exact lattices (cubic, bcc, fcc:
+ * several cells sharing each vertex) tessellate; a cell whose cut is
+ * inconsistent under that margin is clipped again with the strict rule.
+ * A cell inconsistent under both, or two cells that disagree on a face far
+ * above the area threshold (1e4 times it), make the call MM_EDEGENERATE
+ * rather than return such a mesh (seen for cubic lattices perturbed by
+ * 1e-13..1e-11 of a spacing and for generators 1e-10 apart). */
 mm_status mm_tessellate(mm_ctx *ctx, const double *pos, int64_t n, const double box[3], mm_mesh *out);
 
 /* Limited cell-centred gradient of per-volume states W[5][n] (Sec. 4.1):
