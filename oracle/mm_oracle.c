@@ -678,7 +678,7 @@ static int state_width(const orc_cfg *cfg) { return cfg->entropy ? 6 : 5; }
  * linear fields.  Then the S10 factor min(1, psi_ij) over the neighbours
  * (psi from the neighbourhood max/min and Delta_ij = grad . (c_j - c_i)), and
  * optionally the Duffell-MacFadyen factor min(1, max(0, theta (W_j - W_i) /
- * Delta_ij)).  limiter 3 is S10 with Delta_ij measured to the face centroid,
+ * Delta_ij)) over the neighbours whose Delta_ij is nonzero beyond rounding.  limiter 3 is S10 with Delta_ij measured to the face centroid,
  * grad . (x_f - c_i), as in the original S10 scheme.  Every state column,
  * the entropy column included, is treated alike (Sec. 4.3). */
 void orc_gradient(int64_t n, int64_t nf, const int32_t *fi, const int32_t *fj, const int32_t *fshift,
@@ -751,7 +751,14 @@ void orc_gradient(int64_t n, int64_t nf, const int32_t *fi, const int32_t *fj, c
                     if (del > 0.0) p = (wmax[ng * c + k] - W[ng * c + k]) / del;
                     else if (del < 0.0) p = (wmin[ng * c + k] - W[ng * c + k]) / del;
                     if (p < psi[ng * c + k]) psi[ng * c + k] = p;
-                    if (cfg->limiter == 2 && del != 0.0) {
+                    /* the Duffell-MacFadyen ratio counts only where Delta is
+                     * nonzero (Sec. 4.1); a Delta within 2^-40 |g|_1 |d|_1, far
+                     * below what the gradient's and the centroids' own rounding
+                     * leaves, is zero in exact arithmetic (a gradient orthogonal
+                     * to d, as toward the equal-valued transverse neighbours of a
+                     * lattice) and does not count */
+                    double gd = (fabs(g[0]) + fabs(g[1]) + fabs(g[2])) * (fabs(dv[0]) + fabs(dv[1]) + fabs(dv[2]));
+                    if (cfg->limiter == 2 && fabs(del) > 0x1p-40 * gd) {
                         double pd = cfg->theta * (W[ng * o + k] - W[ng * c + k]) / del;
                         if (pd < 0.0) pd = 0.0;
                         if (pd < psidm[ng * c + k]) psidm[ng * c + k] = pd;

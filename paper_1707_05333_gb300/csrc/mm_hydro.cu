@@ -176,12 +176,9 @@ __global__ void __launch_bounds__(128, MM_GRAD_MINBLOCKS) k_gradient(MeshDev m, 
         // S10: alpha = min(1, min_j psi_ij); with c_max = W_max - W_i >= 0 and
         // c_min = W_min - W_i <= 0 the minimum over j is attained at the
         // largest positive and the most negative Delta_ij = g . d_ij.
-        // DM: min_j max(0, theta (W_j - W_i) / Delta_ij), tracked as a
-        // fraction (num, den > 0) to avoid a division per face.
         long long kdx[NG], kdn[NG];  // max / min of Delta, starting from 0
-        double rn[NG], rd[NG];
 #pragma unroll
-        for (int k = 0; k < NG; ++k) { kdx[k] = 0; kdn[k] = 0; rn[k] = 1.0; rd[k] = 1.0; }
+        for (int k = 0; k < NG; ++k) { kdx[k] = 0; kdn[k] = 0; }
         bool exhaustive = c.limiter != 1;
         if (c.limiter == 1) {
             // S10 with centroid separations: Delta in FP32 from FP32 copies of
@@ -270,17 +267,10 @@ __global__ void __launch_bounds__(128, MM_GRAD_MINBLOCKS) k_gradient(MeshDev m, 
                 const long long kd = okey(del);
                 kdx[k] = kmax(kdx[k], kd);
                 kdn[k] = kmin(kdn[k], kd);
-                if (c.limiter == 2 && del != 0.0) {
-                    const int o = fwd ? m.face_j[f] : m.face_i[f];
-                    double num = c.theta * (S[k * n + o] - Wi[k]);
-                    double den = del;
-                    if (den < 0.0) { num = -num; den = -den; }
-                    if (num < 0.0) num = 0.0;
-                    if (num * rd[k] < rn[k] * den) { rn[k] = num; rd[k] = den; }
-                }
             }
         }
         }
+        double al[NG];
 #pragma unroll
         for (int k = 0; k < NG; ++k) {
             // the ratios matter only below 1 (min(1, x)), so most cells skip the
@@ -290,10 +280,49 @@ __global__ void __launch_bounds__(128, MM_GRAD_MINBLOCKS) k_gradient(MeshDev m, 
             const double dmax = okey_value(kdx[k]), dmin = okey_value(kdn[k]);
             if (kdx[k] > 0 && up < dmax) a = fmin(a, up / dmax);
             if (kdn[k] < 0 && dn > dmin) a = fmin(a, dn / dmin);
-            if (c.limiter == 2) a *= fmin(1.0, rn[k] / rd[k]);
-            g[3 * k] *= a;
-            g[3 * k + 1] *= a;
-            g[3 * k + 2] *= a;
+            al[k] = a;
+        }
+        if (c.limiter == 2) {
+            // DM: min_j max(0, theta (W_j - W_i) / Delta_ij) with the unlimited
+            // gradient, tracked as a fraction (num, den > 0) to avoid a division
+            // per face.  A neighbour counts only where Delta is nonzero beyond
+            // the rounding of g and d, 2^-40 |g|_1 |d|_1: toward the equal-valued
+            // transverse neighbours of a lattice Delta is zero in exact
+            // arithmetic.  A pass of its own, after the S10 extremes are dead.
+            double rn[NG], rd[NG], gl[NG];
+#pragma unroll
+            for (int k = 0; k < NG; ++k) {
+                rn[k] = 1.0; rd[k] = 1.0;
+                gl[k] = 0x1p-40 * (fabs(g[3 * k]) + fabs(g[3 * k + 1]) + fabs(g[3 * k + 2]));
+            }
+            for (int e = e0; e < e1; ++e) {
+                int f = m.inc_face[e];
+                const bool fwd = f >= 0;
+                if (!fwd) f = ~f;
+                const long long sm = fwd ? 0LL : (long long)0x8000000000000000ULL;
+                const double dx = flip(geo[3 * fs + f], sm), dy = flip(geo[4 * fs + f], sm),
+                             dz = flip(geo[5 * fs + f], sm);
+                const double dl = fabs(dx) + fabs(dy) + fabs(dz);
+                const int o = fwd ? m.face_j[f] : m.face_i[f];
+#pragma unroll
+                for (int k = 0; k < NG; ++k) {
+                    const double del = deldot(g[3 * k], g[3 * k + 1], g[3 * k + 2], dx, dy, dz);
+                    if (!(fabs(del) > gl[k] * dl)) continue;
+                    double num = c.theta * (S[k * n + o] - Wi[k]);
+                    double den = del;
+                    if (den < 0.0) { num = -num; den = -den; }
+                    if (num < 0.0) num = 0.0;
+                    if (num * rd[k] < rn[k] * den) { rn[k] = num; rd[k] = den; }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NG; ++k) al[k] *= fmin(1.0, rn[k] / rd[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < NG; ++k) {
+            g[3 * k] *= al[k];
+            g[3 * k + 1] *= al[k];
+            g[3 * k + 2] *= al[k];
         }
     }
     if (!PREDICT) {

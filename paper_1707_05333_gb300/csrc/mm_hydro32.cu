@@ -80,7 +80,8 @@ __device__ __forceinline__ Nbr32 nbr32(const MeshDev &m, const Mixed &x, int e)
 // Limited gradient in FP32 (same estimator and limiters as the FP64 path);
 // with PREDICT the half step is taken and W^(n+1/2) written instead.
 template <bool PREDICT>
-__global__ void __launch_bounds__(128) k_gradient32(MeshDev m, HydroCfg c, Mixed x, const float4 *__restrict__ rin,
+// six resident blocks (80 registers): left free, ptxas trades a spill for a seventh
+__global__ void __launch_bounds__(128, 6) k_gradient32(MeshDev m, HydroCfg c, Mixed x, const float4 *__restrict__ rin,
                                                     float4 *__restrict__ rout, const double *__restrict__ dtp)
 {
     // index order: this kernel is bound by its gathers, and the FP32 loop's
@@ -133,10 +134,9 @@ __global__ void __launch_bounds__(128) k_gradient32(MeshDev m, HydroCfg c, Mixed
         g[3 * k + 2] = (c02 * b0 + c12 * b1 + c22 * b2) * idet;
     }
     if (c.limiter >= 1) {
-        float dmax[5], dmin[5], rn[5], rd[5];
+        float dmax[5], dmin[5];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) { dmax[k] = 0.0f; dmin[k] = 0.0f; rn[k] = 1.0f; rd[k] = 1.0f; }
-        const float theta = (float)c.theta;
+        for (int k = 0; k < 5; ++k) { dmax[k] = 0.0f; dmin[k] = 0.0f; }
         for (int e = e0; e < e1; ++e) {
             const Nbr32 q = nbr32(m, x, e);
             const float4 fq = x.fq[q.f];
@@ -154,13 +154,43 @@ __global__ void __launch_bounds__(128) k_gradient32(MeshDev m, HydroCfg c, Mixed
                 dy = q.sg * fq.y + o1.z - diy;
                 dz = q.sg * fq.z + o1.w - diz;
             }
-            const float Wo[5] = {o0.x, o0.y, o0.z, o0.w, o1.x};
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
                 const float del = g[3 * k] * dx + g[3 * k + 1] * dy + g[3 * k + 2] * dz;
                 dmax[k] = fmaxf(dmax[k], del);
                 dmin[k] = fminf(dmin[k], del);
-                if (c.limiter == 2 && del != 0.0f) {
+            }
+        }
+        float al[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            al[k] = 1.0f;
+            if (dmax[k] > 0.0f) al[k] = fminf(al[k], (wmax[k] - Wi[k]) / dmax[k]);
+            if (dmin[k] < 0.0f) al[k] = fminf(al[k], (wmin[k] - Wi[k]) / dmin[k]);
+        }
+        if (c.limiter == 2) {
+            // DM with the unlimited gradient, over the neighbours whose Delta
+            // is nonzero beyond the rounding of g and d (2^-40 |g|_1 |d|_1;
+            // toward the equal-valued transverse neighbours of a lattice Delta
+            // is zero in exact arithmetic), as a fraction (num, den > 0)
+            const float theta = (float)c.theta;
+            float rn[5], rd[5], gl[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                rn[k] = 1.0f; rd[k] = 1.0f;
+                gl[k] = 0x1p-40f * (fabsf(g[3 * k]) + fabsf(g[3 * k + 1]) + fabsf(g[3 * k + 2]));
+            }
+            for (int e = e0; e < e1; ++e) {
+                const Nbr32 q = nbr32(m, x, e);
+                const float4 fq = x.fq[q.f];
+                const float4 o0 = rin[2 * q.o], o1 = rin[2 * q.o + 1];
+                const float dx = q.sg * fq.x + o1.y - dix, dy = q.sg * fq.y + o1.z - diy, dz = q.sg * fq.z + o1.w - diz;
+                const float dl = fabsf(dx) + fabsf(dy) + fabsf(dz);
+                const float Wo[5] = {o0.x, o0.y, o0.z, o0.w, o1.x};
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    const float del = g[3 * k] * dx + g[3 * k + 1] * dy + g[3 * k + 2] * dz;
+                    if (!(fabsf(del) > gl[k] * dl)) continue;
                     float num = theta * (Wo[k] - Wi[k]);
                     float den = del;
                     if (den < 0.0f) { num = -num; den = -den; }
@@ -168,16 +198,14 @@ __global__ void __launch_bounds__(128) k_gradient32(MeshDev m, HydroCfg c, Mixed
                     if (num * rd[k] < rn[k] * den) { rn[k] = num; rd[k] = den; }
                 }
             }
+#pragma unroll
+            for (int k = 0; k < 5; ++k) al[k] *= fminf(1.0f, rn[k] / rd[k]);
         }
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-            float al = 1.0f;
-            if (dmax[k] > 0.0f) al = fminf(al, (wmax[k] - Wi[k]) / dmax[k]);
-            if (dmin[k] < 0.0f) al = fminf(al, (wmin[k] - Wi[k]) / dmin[k]);
-            if (c.limiter == 2) al *= fminf(1.0f, rn[k] / rd[k]);
-            g[3 * k] *= al;
-            g[3 * k + 1] *= al;
-            g[3 * k + 2] *= al;
+            g[3 * k] *= al[k];
+            g[3 * k + 1] *= al[k];
+            g[3 * k + 2] *= al[k];
         }
     }
     if (!PREDICT) {

@@ -252,6 +252,32 @@ WORKLOADS = {
 }
 
 
+def planar_profile(x):
+    """Primitives (rho, u, P) of a planar state along x in [0, 1): a smooth
+    wave with a raised block in density and pressure on [0.3, 0.6) (a
+    contact and two jumps), flowing at u = 0.1 + 0.2 cos 2 pi x."""
+    blk = ((x >= 0.3) & (x < 0.6)).astype(np.float64)
+    rho = 1.0 + 0.3 * np.sin(2 * np.pi * x) + 0.5 * blk
+    u = 0.1 + 0.2 * np.cos(2 * np.pi * x)
+    P = 1.0 + 0.2 * np.sin(4 * np.pi * x) + 0.6 * blk
+    return rho, u, P
+
+
+def planar_lattice(nx, ny, nz):
+    """An exact cubic lattice of spacing h = 1/nx (no jitter) in the box
+    (1, ny h, nz h), cells in x-major order, carrying planar_profile along x
+    (gamma = 5/3): the mesh is the Cartesian grid and the flow one-dimensional."""
+    h = 1.0 / nx
+    ix, iy, iz = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    ix, iy, iz = ix.ravel(), iy.ravel(), iz.ravel()
+    pos = np.stack([(ix + 0.5) * h, (iy + 0.5) * h, (iz + 0.5) * h], axis=1)
+    rho, u, P = planar_profile(pos[:, 0])
+    vel = np.zeros((len(pos), 3))
+    vel[:, 0] = u
+    return _finish(f"planar_lattice_{nx}x{ny}x{nz}", pos, np.array([1.0, ny * h, nz * h]), rho, vel, P,
+                   5.0 / 3.0, 0.3, 1)
+
+
 def clustered_points(n, core_fraction=0.5, core_scale=0.02, seed=0):
     """Strongly clustered generators for robustness tests (seeded): a
     fraction of the points in a Plummer-like core (radius drawn so that the

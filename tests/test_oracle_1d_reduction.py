@@ -31,26 +31,14 @@ largest charge (measured 5e-16)."""
 import numpy as np
 import pytest
 
+from paper_1707_05333_gb300 import workloads as WL
+
 GAMMA = 5.0 / 3.0
 
 
-def lattice(nx, ny, nz):
-    h = 1.0 / nx
-    ix, iy, iz = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
-    ix, iy, iz = ix.ravel(), iy.ravel(), iz.ravel()
-    pos = np.stack([(ix + 0.5) * h, (iy + 0.5) * h, (iz + 0.5) * h], axis=1)
-    return pos, np.array([1.0, ny * h, nz * h]), h, ix
-
-
-def profile(x):
-    """Conserved state per volume (rho, rho u, 0, 0, rho e) of a smooth wave
-    with a raised block in density and pressure (a contact and two jumps,
-    where the limiter acts)."""
-    blk = ((x >= 0.3) & (x < 0.6)).astype(float)
-    rho = 1.0 + 0.3 * np.sin(2 * np.pi * x) + 0.5 * blk
-    u = 0.1 + 0.2 * np.cos(2 * np.pi * x)
-    P = 1.0 + 0.2 * np.sin(4 * np.pi * x) + 0.6 * blk
-    W = np.zeros((len(x), 5))
+def conserved(rho, u, P):
+    """Conserved state per volume (rho, rho u, 0, 0, rho e)."""
+    W = np.zeros((len(rho), 5))
     W[:, 0] = rho
     W[:, 1] = rho * u
     W[:, 4] = P / (GAMMA - 1.0) + 0.5 * rho * u * u
@@ -70,19 +58,33 @@ def flux_derivative(W, g):
     return euler_flux_x(W + 1j * eps * g).imag / eps
 
 
-def s10(W, g, h):
+def s10(W, g, h, to_face=False):
     """S10 limiter (Sec. 4.1) on the line: neighbourhood extremes including
-    the cell, Delta = g (c_j - c_i) to both neighbours, alpha = min(1, psi)."""
+    the cell, Delta = g (c_j - c_i) to both neighbours (g (x_f - c_i), half
+    as far, for the face-centroid form), alpha = min(1, psi)."""
     Wm, Wp = np.roll(W, 1, axis=0), np.roll(W, -1, axis=0)
     hi = np.maximum(np.maximum(Wm, W), Wp)
     lo = np.minimum(np.minimum(Wm, W), Wp)
     a = np.ones_like(W)
-    for d in (h, -h):
+    for d in ((0.5 * h, -0.5 * h) if to_face else (h, -h)):
         D = g * d
         with np.errstate(divide="ignore", invalid="ignore"):
             psi = np.where(D > 0, (hi - W) / D, np.where(D < 0, (lo - W) / D, 1.0))
         a = np.minimum(a, psi)
-    return a * g
+    return a
+
+
+def dm(W, g, h, theta):
+    """Duffell-MacFadyen factor (Sec. 4.1) on the line: min(1, min_j max(0,
+    theta (W_j - W_i) / Delta_ij)) over the two neighbours with Delta != 0;
+    the transverse neighbours have Delta = 0 and do not count."""
+    a = np.ones_like(W)
+    for Wj, d in ((np.roll(W, -1, axis=0), h), (np.roll(W, 1, axis=0), -h)):
+        D = g * d
+        with np.errstate(divide="ignore", invalid="ignore"):
+            psi = np.where(D != 0, np.maximum(0.0, theta * (Wj - W) / D), 1.0)
+        a = np.minimum(a, psi)
+    return a
 
 
 def prim_in_face_frame(W, wf):
@@ -92,10 +94,15 @@ def prim_in_face_frame(W, wf):
     return np.array([rho, u[0] - wf, u[1], u[2], P])
 
 
-def step_1d(W, h, dt, eta, limiter, riemann, plant=None):
+def step_1d(W, h, dt, eta, limiter, riemann, plant=None, theta=0.49):
     def grad(X):
         g = (np.roll(X, -1, axis=0) - np.roll(X, 1, axis=0)) / (2.0 * h)
-        return s10(X, g, h) if limiter and plant != "no_limiter" else g
+        if not limiter or plant == "no_limiter":
+            return g
+        a = s10(X, g, h, to_face=limiter == 3)
+        if limiter == 2:
+            a = a * dm(X, g, h, theta)
+        return a * g
 
     g0 = grad(W)
     Wh = W - (1.0 if plant == "full_step" else 0.5) * dt * flux_derivative(W, g0)
@@ -118,23 +125,27 @@ CASES = {
     "static_s10_hllc": dict(eta=0.0, limiter=1, riemann=0),
     "moving_s10_hllc": dict(eta=1.0, limiter=1, riemann=0),
     "moving_s10_hll": dict(eta=1.0, limiter=1, riemann=1),
+    "moving_s10_dm_hllc": dict(eta=1.0, limiter=2, riemann=0),
+    "moving_face_centroid_s10_hllc": dict(eta=1.0, limiter=3, riemann=0),
 }
 
 
 def _run(oracle, nx, ny, nz, c):
-    pos, box, h, ix = lattice(nx, ny, nz)
-    W1d = profile((np.arange(nx) + 0.5) * h)
+    w = WL.planar_lattice(nx, ny, nz)  # h = 1/nx, not a power of two for nx = 30
+    h = 1.0 / nx
+    ix = np.rint(w.pos[:, 0] / h - 0.5).astype(int)
+    W1d = conserved(*WL.planar_profile((np.arange(nx) + 0.5) * h))
     U = W1d[ix] * h ** 3
     rho, u = W1d[:, 0], W1d[:, 1] / W1d[:, 0]
     P = (GAMMA - 1.0) * (W1d[:, 4] - 0.5 * rho * u * u)
     dt = 0.3 * h / np.max(np.abs(u) + np.sqrt(GAMMA * P / rho))
     cfg = oracle.make_cfg(gamma=GAMMA, eta=c["eta"], limiter=c["limiter"], riemann=c["riemann"])
-    out = oracle.step(pos, U, box, cfg, dt=dt)
+    out = oracle.step(w.pos, U, w.box, cfg, dt=dt)
     riemann = oracle.hll_1d if c["riemann"] else oracle.hllc_1d
     return out["U"], W1d, ix, h, dt, riemann
 
 
-@pytest.mark.parametrize("shape", [(32, 1, 1), (32, 2, 2)], ids=["32x1x1", "32x2x2"])
+@pytest.mark.parametrize("shape", [(32, 1, 1), (32, 2, 2), (30, 3, 3)], ids=["32x1x1", "32x2x2", "30x3x3"])
 @pytest.mark.parametrize("case", list(CASES))
 def test_lattice_step_is_the_one_dimensional_scheme(oracle, case, shape):
     c = CASES[case]
