@@ -20,9 +20,13 @@ passages directly:
         transformation of the Euler flux (Sec. 4 items 3-5),
   U_i <- U_i - dt h^2 (F_{i+1/2} - F_{i-1/2}) (Sec. 4, outward flux);
 
-and Heun's flux averaging (Sec. 6) with every generator moving at one
+Heun's flux averaging (Sec. 6) with every generator moving at one
 velocity, so that the lattice translates and stays a lattice: two
-forward-Euler stages reconstructing in space only, averaged with the start.
+forward-Euler stages reconstructing in space only, averaged with the start;
+and the entropy column with the shock switch (Sec. 4.3): rho A predicted
+through the complex-step derivative of its passive flux (rho A) u, its face
+flux upwind of the contact, the faces' shock Mach numbers, and the switch
+at the swept volume V'.
 
 The Riemann solvers are the oracle's one-dimensional ones, pinned on their
 own (Toro's exact star states, the jump conditions); everything the
@@ -32,8 +36,9 @@ unique-face bookkeeping and the sign of the update -- is checked here.  A
 mistake planted in the one-dimensional scheme (a full instead of a half
 step, one gradient pass instead of two, the reconstruction from the wrong
 side, a face at rest, a back-boost without its energy term, no limiter)
-moves the result by 1e-3 or more; the two agree to 1e-13 of the largest
-charge (measured 7.5e-15)."""
+moves the result by 1e-3 or more, and in the entropy scheme (the start
+volume for V', the downwind side's A, the switch inverted) by 4e-5 or more;
+the two agree to 1e-13 of the largest charge (measured 7.5e-15)."""
 import numpy as np
 import pytest
 
@@ -52,10 +57,14 @@ def conserved(rho, u, P):
 
 
 def euler_flux_x(W):
-    rho, mx, my, mz, E = W.T
+    """Euler flux along x; a sixth column rho A is carried passively, (rho A) u."""
+    rho, mx, my, mz, E = W[:, :5].T
     u = mx / rho
     P = (GAMMA - 1.0) * (E - 0.5 * (mx * mx + my * my + mz * mz) / rho)
-    return np.stack([mx, mx * u + P, my * u, mz * u, (E + P) * u], axis=1)
+    cols = [mx, mx * u + P, my * u, mz * u, (E + P) * u]
+    if W.shape[1] == 6:
+        cols.append(W[:, 5] * u)
+    return np.stack(cols, axis=1)
 
 
 def flux_derivative(W, g):
@@ -155,6 +164,55 @@ def heun_1d(W, h, dt, w, limiter, riemann):
     return 0.5 * (W + stage(stage(W)))
 
 
+def step_1d_entropy(W, h, dt, limiter, riemann, mach_th, oracle, plant=None):
+    """The half-step scheme with the entropy column rho A (Sec. 4.3): rho A
+    reconstructed and predicted like the other columns, its flux the mass
+    flux times A of the contact's upwind side (HLLC) or the HLL average of
+    rho A (HLL), unchanged by the boost; each face's shock Mach number from
+    the Riemann problem; a cell whose faces all stay below mach_th takes its
+    energy from its entropy, E = |m|^2/2M + A rho^gamma V'/(gamma - 1), at the
+    volume V' = V + dt sum (+-) A (w_f . n) the faces sweep it to, and the
+    other cells reset their entropy from their energy.  The transverse faces
+    carry equal states: Mach number 0, or 1 up to rounding, below every
+    threshold used here, and equal and opposite swept volumes."""
+    g0 = limited_gradient(W, h, limiter)
+    Wh = W - 0.5 * dt * flux_derivative(W, g0)
+    g1 = limited_gradient(Wh, h, limiter)
+    WL = Wh + 0.5 * h * g1
+    WR = np.roll(Wh - 0.5 * h * g1, -1, axis=0)
+    assert np.all(WL[:, 5] > 0) and np.all(WR[:, 5] > 0)
+    v = W[:, 1:4] / W[:, :1]
+    wf = 0.5 * (v + np.roll(v, -1, axis=0))
+    F = face_fluxes(WL[:, :5], WR[:, :5], wf, oracle.hll_1d if riemann else oracle.hllc_1d)
+    F = np.hstack([F, np.zeros((len(F), 1))])
+    mach = np.zeros(len(F))
+    for k in range(len(F)):
+        pl, pr = prim_in_face_frame(WL[k], wf[k]), prim_in_face_frame(WR[k], wf[k])
+        sl, ss, sr, _ = oracle.star_state(pl, pr, GAMMA)
+        al, ar = WL[k, 5] / WL[k, 0], WR[k, 5] / WR[k, 0]
+        if riemann:
+            fl, fr = pl[0] * pl[1] * al, pr[0] * pr[1] * ar
+            F[k, 5] = fl if sl >= 0 else fr if sr <= 0 else (sr * fl - sl * fr + sl * sr * (WR[k, 5] - WL[k, 5])) / (sr - sl)
+        else:
+            upwind_left = (ss >= 0) != (plant == "downwind_entropy")
+            F[k, 5] = F[k, 0] * (al if upwind_left else ar)
+        mach[k] = oracle.shock_mach(pl, pr, GAMMA)
+    V = h ** 3
+    U = W * V - dt * h * h * (F - np.roll(F, 1, axis=0))
+    mc = np.maximum(mach, np.roll(mach, 1))
+    Vn = V + (0.0 if plant == "start_volume" else 1.0) * dt * h * h * (wf[:, 0] - np.roll(wf[:, 0], 1))
+    energy = (mc >= mach_th) != (plant == "switch_inverted")
+    for i in range(len(U)):
+        m2 = np.dot(U[i, 1:4], U[i, 1:4])
+        if not energy[i]:
+            P = (U[i, 5] / U[i, 0]) * (U[i, 0] / Vn[i]) ** GAMMA
+            U[i, 4] = 0.5 * m2 / U[i, 0] + P * Vn[i] / (GAMMA - 1.0)
+        else:
+            P = (GAMMA - 1.0) * (U[i, 4] - 0.5 * m2 / U[i, 0]) / Vn[i]
+            U[i, 5] = U[i, 0] * P / (U[i, 0] / Vn[i]) ** GAMMA
+    return U, int(energy.sum())
+
+
 CASES = {
     "static_no_limiter_hllc": dict(eta=0.0, limiter=0, riemann=0),
     "static_s10_hllc": dict(eta=0.0, limiter=1, riemann=0),
@@ -223,6 +281,47 @@ def test_lattice_heun_step_is_the_one_dimensional_heun_scheme(oracle, limiter, s
     print(f"[1d heun limiter {limiter} {shape}] max error per component / max |U|: {err}")
     assert np.all(err <= 1e-13), err
     assert np.all(_max_error(out["U"], W1d[ix] * h ** 3)[[0, 1, 2, 4]] > 1e-6)
+
+
+ENTROPY_CASES = {  # the faces' Mach numbers reach 1.07-1.10 at the block's edges: 1.05 splits the cells
+    "switch_hllc": dict(riemann=0, mach_th=1.05),
+    "switch_hll": dict(riemann=1, mach_th=1.05),
+    "energy_everywhere": dict(riemann=0, mach_th=0.0),
+    "entropy_everywhere": dict(riemann=0, mach_th=1e300),
+}
+
+
+@pytest.mark.parametrize(**SHAPES)
+@pytest.mark.parametrize("case", list(ENTROPY_CASES))
+def test_lattice_entropy_step_is_the_one_dimensional_scheme(oracle, case, shape):
+    c = ENTROPY_CASES[case]
+    w, h, ix, W1d, dt = _setup(*shape)
+    rho = W1d[:, 0]
+    P = (GAMMA - 1.0) * (W1d[:, 4] - 0.5 * (W1d[:, 1] ** 2 + W1d[:, 2] ** 2) / rho)
+    W6 = np.hstack([W1d, (P / rho ** GAMMA * rho)[:, None]])
+    cfg = oracle.make_cfg(gamma=GAMMA, limiter=1, riemann=c["riemann"], entropy=1, mach_th=c["mach_th"])
+    out = oracle.step(w.pos, W6[ix] * h ** 3, w.box, cfg, dt=dt)
+    ref, n_energy = step_1d_entropy(W6, h, dt, 1, c["riemann"], c["mach_th"], oracle)
+    ref = ref[ix]
+    err = _max_error(out["U"], ref)
+    print(f"[1d entropy {case} {shape}] cells on the energy equation {n_energy} of {shape[0]}; error: {err}")
+    assert np.all(err <= 1e-13), err
+    if case.startswith("switch"):
+        assert 0 < n_energy < shape[0]
+
+
+@pytest.mark.parametrize("plant", ["start_volume", "downwind_entropy", "switch_inverted"])
+def test_a_planted_mistake_in_the_entropy_scheme_is_seen(oracle, plant):
+    w, h, ix, W1d, dt = _setup(32, 2, 2)
+    rho = W1d[:, 0]
+    P = (GAMMA - 1.0) * (W1d[:, 4] - 0.5 * (W1d[:, 1] ** 2 + W1d[:, 2] ** 2) / rho)
+    W6 = np.hstack([W1d, (P / rho ** GAMMA * rho)[:, None]])
+    cfg = oracle.make_cfg(gamma=GAMMA, limiter=1, entropy=1, mach_th=1.05)
+    out = oracle.step(w.pos, W6[ix] * h ** 3, w.box, cfg, dt=dt)
+    bad = step_1d_entropy(W6, h, dt, 1, 0, 1.05, oracle, plant=plant)[0][ix]
+    err = _max_error(out["U"], bad)[[4, 5]].max()
+    print(f"[entropy plant {plant}] {err:.2e}")
+    assert err > 1e-8, err
 
 
 @pytest.mark.parametrize("plant", ["full_step", "one_gradient", "wrong_side", "face_at_rest",
