@@ -168,7 +168,11 @@ mm_status mm_tessellate(mm_ctx *ctx, const double *pos, int64_t n, const double 
 /* Limited cell-centred gradient of per-volume states W[5][n] (Sec. 4.1):
  * grad W_i = M_i^-1 b_i with M_i = 1/2 sum_j A n (x) (c_j - c_i) and
  * b_i = 1/2 sum_j A (W_j - W_i) n, then the S10 factor min(1, psi_ij) and,
- * for limiter 2, the Duffell-MacFadyen factor.  grad[15][n] device.  The
+ * for limiter 2, the Duffell-MacFadyen factor min(1, max(0, theta (W_j -
+ * W_i) / Delta_ij)) over the neighbours whose Delta_ij = grad W_i . (c_j -
+ * c_i) exceeds 2^-40 |grad W_i|_1 |c_j - c_i|_1 in size (below that it is
+ * zero up to rounding, as toward the equal-valued transverse neighbours of
+ * a lattice with a planar state).  grad[15][n] device.  The
  * context forms the per-face A n and separations in its own workspace
  * (grown on demand, like the other stages'). */
 mm_status mm_gradients(mm_ctx *ctx, const mm_mesh *mesh, const double *W, double *grad);
