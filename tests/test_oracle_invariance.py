@@ -1,7 +1,8 @@
 """Symmetries of the oracle's whole step (Sec. 2-4): relabelling the cells,
-translating every generator through the periodic box, and mirroring the box
-(x -> L - x with the x velocity reversed) each commute with one step, to the
-rounding of sums taken in another order.  A mistake in an index (i for j),
+translating every generator through the periodic box, mirroring the box
+(x -> L - x with the x velocity reversed) and changing the units of length
+and velocity by powers of two each commute with one step, to the rounding of
+sums taken in another order.  A mistake in an index (i for j),
 an image shift, a normal's or a flux's sign, or a per-cell quantity read
 for the wrong cell breaks one of them; none needs the method's own formulas
 on this side."""
@@ -98,3 +99,21 @@ def test_a_wrong_index_breaks_relabelling(oracle):
     cfg, pos, U, S = _setup(oracle, "s10_hllc")
     P = oracle.step(pos, np.roll(U, 1, axis=0), BOX, cfg, dt=S["dt"])
     assert not np.all(_close(P["U"], np.roll(S["U"], 1, axis=0), rtol=1e-6))
+
+
+@pytest.mark.parametrize("name", list(CONFIGS))
+@pytest.mark.parametrize("s,a", [(2.0 ** -20, 1.0), (2.0 ** 20, 1.0), (1.0, 2.0 ** 10), (2.0 ** -7, 2.0 ** 5)],
+                         ids=["small", "large", "fast", "small_fast"])
+def test_power_of_two_units_commute_with_the_step(oracle, name, s, a):
+    """Lengths times s, velocities times a (pressures a^2, times s/a): the
+    charges of one step scale as (s^3) (1, a, a, a, a^2 [, a^2]) and the CFL
+    step as s/a.  Every tolerance inside the oracle is relative to a length
+    or a value of the configuration; an absolute one would show here."""
+    cfg, pos, U, S = _setup(oracle, name)
+    k = np.array([1.0, a, a, a, a * a] + ([a * a] if cfg.entropy else [])) * s ** 3
+    P = oracle.step(pos * s, U * k, BOX * s, cfg, dt=S["dt"] * s / a)
+    assert np.all(_close(P["U"], S["U"] * k))
+    assert P["dt_cfl"] == pytest.approx(S["dt_cfl"] * s / a, rel=1e-13)
+    d = P["pos"] - S["pos"] * s
+    d -= BOX * s * np.round(d / (BOX * s))
+    assert np.abs(d).max() <= 1e-13 * s
