@@ -13,10 +13,17 @@
  *   - the half-step uses the explicit Euler flux Jacobians A_d (Sec. 4.1);
  *   - the Riemann problem is rotated into an explicit (n, t1, t2) basis (Sec. 4).
  *
- * Readings where the paper is silent or garbled are the ones listed in the
- * project design notes: centroid Green-Gauss gradient M g = b, S10 limiter
- * over neighbour centroids, clamped Duffell-MacFadyen factor, Davis wave
- * speeds, outward-flux sign of the update, floors on rho and eps.
+ * Where the paper is silent or garbled it is read as: the centroid
+ * Green-Gauss gradient M g = b; the S10 limiter over neighbour centroids; the
+ * Duffell-MacFadyen factor clamped at 0 and counted only where Delta is
+ * nonzero beyond rounding; Davis wave speeds; the outward-flux sign of the
+ * update; floors on rho and eps; the entropy column as a passive scalar
+ * upwind of the contact, switched at the volume the faces sweep the cell to.
+ *
+ * Pins (CPU tests): closed-form lattice cells, Qhull's Voronoi diagram of the
+ * unrolled box, Toro's exact star states and the HLLC jump conditions, the
+ * one-dimensional scheme on planar lattices, the geometric conservation law,
+ * and the step's symmetries.
  */
 #include "mm_oracle.h"
 
