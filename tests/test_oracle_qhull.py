@@ -74,12 +74,33 @@ def _min_image(d, box):
     return d - box * np.round(d / box)
 
 
+def _lattice(kind, m, offset, jitter=0.0):
+    """Cubic, BCC or FCC lattice of m^3 conventional cells in the unit box,
+    shifted by `offset` spacings (inexact in binary), optionally perturbed
+    by `jitter` spacings: every Voronoi vertex is shared by more cells than
+    three planes define, the ties the clipper has to settle."""
+    s = 1.0 / m
+    basis = {"sc": [(0, 0, 0)], "bcc": [(0, 0, 0), (0.5, 0.5, 0.5)],
+             "fcc": [(0, 0, 0), (0.5, 0.5, 0), (0.5, 0, 0.5), (0, 0.5, 0.5)]}[kind]
+    p = np.array([((i + b[0] + offset) * s, (j + b[1] + offset) * s, (k + b[2] + offset) * s)
+                  for k in range(m) for j in range(m) for i in range(m) for b in basis])
+    if jitter:
+        p = p + jitter * s * np.random.default_rng(3).standard_normal(p.shape)
+    p = p % 1.0
+    return np.where(p >= 1.0, 0.0, p), np.ones(3)
+
+
 CASES = {
     "uniform_unit_box": lambda: (WL.random_points(200, seed=11), np.ones(3)),
     "uniform_flat_box": lambda: (WL.random_points(150, box=(2.0, 1.0, 0.5), seed=12),
                                  np.array([2.0, 1.0, 0.5])),
     "jittered_lattice": lambda: (WL.smooth_wave(5).pos, WL.smooth_wave(5).box),
     "clustered": lambda: (WL.clustered_points(400, seed=13), np.ones(3)),
+    "cubic_5_offset_0.1": lambda: _lattice("sc", 5, 0.1),
+    "bcc_4_offset_0.3": lambda: _lattice("bcc", 4, 0.3),
+    "fcc_3_offset_0.1": lambda: _lattice("fcc", 3, 0.1),
+    "cubic_6_jitter_1e-11": lambda: _lattice("sc", 6, 0.25, 1e-11),
+    "fcc_3_jitter_1e-11": lambda: _lattice("fcc", 3, 0.0, 1e-11),
 }
 
 
