@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(128, 6) k_gradient32(MeshDev m, HydroCfg c, Mi
         for (int e = e0; e < e1; ++e) {
             const Nbr32 q = nbr32(m, x, e);
             const float4 fq = x.fq[q.f];
-            const float4 o0 = rin[2 * q.o], o1 = rin[2 * q.o + 1];
+            const float4 o1 = rin[2 * q.o + 1];
             float dx, dy, dz;
             if (c.limiter == 3) {
                 // face centroid relative to this cell's centroid: x_f - r_i - d_i, or x_f - q - r_i - d_j
