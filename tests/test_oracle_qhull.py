@@ -101,6 +101,9 @@ CASES = {
     "fcc_3_offset_0.1": lambda: _lattice("fcc", 3, 0.1),
     "cubic_6_jitter_1e-11": lambda: _lattice("sc", 6, 0.25, 1e-11),
     "fcc_3_jitter_1e-11": lambda: _lattice("fcc", 3, 0.0, 1e-11),
+    # 80 of the 512 points of a grid of eighths: many cospherical ties, irregular cells
+    "grid_eighths_subset": lambda: (np.random.default_rng(14).permutation(
+        np.stack(np.meshgrid(*[np.arange(8) / 8.0] * 3, indexing="ij"), -1).reshape(-1, 3))[:80], np.ones(3)),
 }
 
 
