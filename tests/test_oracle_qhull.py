@@ -182,3 +182,35 @@ def test_the_comparison_sees_a_planted_mistake(oracle, what):
     Q = qhull_cells(pos, box)
     assert not mismatches(T, pos, box, Q, oracle.AREA_REL)[0]
     assert mismatches(_planted(T, what, box), pos, box, Q, oracle.AREA_REL)[0]
+
+
+def _fuzz_set(rng):
+    """One random point set: uniform, with coordinates on the box walls,
+    rounded to a grid of eighths (cospherical ties), or clustered, in a box
+    of aspect ratio up to 10."""
+    n = int(rng.integers(3, 120))
+    box = np.exp(rng.uniform(np.log(0.3), np.log(3.0), 3))
+    kind = int(rng.integers(0, 4))
+    pos = rng.uniform(0.0, 1.0, (n, 3)) * box
+    if kind == 1:
+        pos[rng.random((n, 3)) < 0.2] = 0.0
+    elif kind == 2:
+        pos = np.unique(np.round(pos / box * 8.0) / 8.0 * box, axis=0)
+    elif kind == 3:
+        pos = (rng.uniform(0.0, 1.0, 3) * box + rng.normal(0.0, 0.05, (n, 3)) * box) % box
+    pos = np.unique(np.where(pos >= box, 0.0, pos), axis=0)
+    return pos, box
+
+
+@pytest.mark.slow
+def test_seeded_fuzz_against_qhull(oracle):
+    rng = np.random.default_rng(2024)
+    runs = 0
+    while runs < 150:
+        pos, box = _fuzz_set(rng)
+        if len(pos) < 2:
+            continue
+        T = oracle.tessellate(pos, box, 1)
+        bad = mismatches(T, pos, box, qhull_cells(pos, box), oracle.AREA_REL)[0]
+        assert not bad, (pos.tolist(), box.tolist(), bad[:5])
+        runs += 1
