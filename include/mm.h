@@ -80,7 +80,10 @@ typedef struct {
                       /*    for bit); 0: solve and test every vertex in FP64 as it appears  */
     double bin_scale; /* neighbour-search bin edge in mean generator spacings (tunable)       */
     double mach_th;   /* energy/entropy switch: a cell whose largest face shock Mach number   */
-                      /*    is below mach_th takes its energy from its entropy (Sec. 4.3)     */
+                      /*    is below mach_th takes its energy from its entropy (Sec. 4.3);   */
+                      /*    a face between equal states reads 0 or 1 + O(eps), so values at  */
+                      /*    or below 1 let rounding decide in uniform regions (0 = energy    */
+                      /*    everywhere is exact)                                              */
     int entropy;      /* 1: charges carry a sixth row m A, A = P / rho^gamma, and the switch  */
                       /*    applies (FP64 hydro only); 0: five rows, energy equation only    */
     int integrator;   /* 0: half-step predictor with start-of-step geometry (Sec. 4.1);      */
