@@ -9,8 +9,9 @@ with g_y; every face moves with the mean velocity of its generators.  The
 scheme below is written from those passages, with the flux derivatives by a
 complex step and the y-direction Riemann problems in a frame whose normal
 is y; it checks what the one-dimensional reduction cannot: the limiter's
-factor shared between directions, the sum of the two half-step terms, and
-the y faces' rotation and boosts."""
+factor shared between directions, the sum of the two half-step terms, the
+y faces' rotation and boosts, and, with the entropy column, each cell's
+largest Mach number and swept volume over faces of both directions."""
 import numpy as np
 import pytest
 
@@ -132,3 +133,71 @@ def test_lattice_step_is_the_two_dimensional_scheme(oracle, shape, limiter, riem
     print(f"[2d {shape} limiter {limiter} riemann {riemann}] {err}")
     assert np.all(err <= 1e-13), err
     assert np.abs(out["U"] - W[ix, iy] * h ** 3).max() > 1e-6 * scale.max()
+
+
+def step_2d_entropy(W, h, dt, mach_th, oracle):
+    """The 2-D scheme with the entropy column (Sec. 4.3): rho A carried
+    through the half step as the passive flux (rho A) u, its face flux the
+    mass flux times A upwind of the contact, the faces' shock Mach numbers
+    from the face-frame states, and the switch at the volume V' the x and y
+    faces sweep the cell to."""
+    flux6 = lambda f: (lambda X: np.hstack([f(X[:, :5]), (X[:, 5] * f(X[:, :5])[:, 0] / X[:, 0])[:, None]]))
+    Fx6, Fy6 = flux6(euler_flux_x), flux6(euler_flux_y)
+    gx, gy = limited_gradients(W, h, 1)
+    eps = 1e-30
+    Wf, gxf, gyf = W.reshape(-1, 6), gx.reshape(-1, 6), gy.reshape(-1, 6)
+    dWdt = (Fx6(Wf + 1j * eps * gxf).imag + Fy6(Wf + 1j * eps * gyf).imag) / eps
+    Wh = W - 0.5 * dt * dWdt.reshape(W.shape)
+    gx, gy = limited_gradients(Wh, h, 1)
+    v = W[..., 1:4] / W[..., :1]
+    out, mach, vrate = [], [], []
+    for normal, g, wf in ((0, gx, 0.5 * (v + np.roll(v, -1, 0))), (1, gy, 0.5 * (v + np.roll(v, -1, 1)))):
+        WL, WR = Wh + 0.5 * h * g, np.roll(Wh - 0.5 * h * g, -1, normal)
+        F = fluxes(WL[..., :5], WR[..., :5], wf, normal, oracle.hllc_1d)
+        F6, M = np.zeros(F.shape[:-1]), np.zeros(F.shape[:-1])
+        order = [1, 2, 3] if normal == 0 else [2, 1, 3]
+        for k in np.ndindex(F.shape[:-1]):
+            prims = []
+            for X in (WL[k], WR[k]):
+                vel = X[1:4] / X[0] - wf[k]
+                P = (GAMMA - 1.0) * (X[4] - 0.5 * np.dot(X[1:4], X[1:4]) / X[0])
+                prims.append(np.array([X[0], vel[order[0] - 1], vel[order[1] - 1], vel[order[2] - 1], P]))
+            ss = oracle.star_state(prims[0], prims[1], GAMMA)[1]
+            F6[k] = F[k][0] * (WL[k][5] / WL[k][0] if ss >= 0 else WR[k][5] / WR[k][0])
+            M[k] = oracle.shock_mach(prims[0], prims[1], GAMMA)
+        out.append(np.concatenate([F, F6[..., None]], -1))
+        mach.append(M)
+        vrate.append(h * h * wf[..., normal])
+    Fx, Fy = out
+    U = W * h ** 3 - dt * h * h * (Fx - np.roll(Fx, 1, 0) + Fy - np.roll(Fy, 1, 1))
+    mc = np.maximum.reduce([mach[0], np.roll(mach[0], 1, 0), mach[1], np.roll(mach[1], 1, 1)])
+    Vn = h ** 3 + dt * (vrate[0] - np.roll(vrate[0], 1, 0) + vrate[1] - np.roll(vrate[1], 1, 1))
+    m2 = (U[..., 1:4] ** 2).sum(-1)
+    energy = mc >= mach_th
+    P_ent = (U[..., 5] / U[..., 0]) * (U[..., 0] / Vn) ** GAMMA
+    U[..., 4] = np.where(energy, U[..., 4], 0.5 * m2 / U[..., 0] + P_ent * Vn / (GAMMA - 1.0))
+    P_en = (GAMMA - 1.0) * (U[..., 4] - 0.5 * m2 / U[..., 0]) / Vn
+    U[..., 5] = np.where(energy, U[..., 0] * P_en / (U[..., 0] / Vn) ** GAMMA, U[..., 5])
+    return U, int(energy.sum())
+
+
+@pytest.mark.parametrize("mach_th", [1.02, 0.0, 1e300], ids=["split", "energy_everywhere", "entropy_everywhere"])
+def test_lattice_entropy_step_is_the_two_dimensional_scheme(oracle, mach_th):
+    nx, ny, nz = 20, 15, 2
+    pos, box, h, ix, iy = lattice_2d(nx, ny, nz)
+    W5 = state_2d(nx, ny, h)
+    rho = W5[..., 0]
+    P = (GAMMA - 1.0) * (W5[..., 4] - 0.5 * (W5[..., 1] ** 2 + W5[..., 2] ** 2) / rho)
+    W = np.concatenate([W5, (P / rho ** GAMMA * rho)[..., None]], -1)
+    dt = 0.25 * h / np.max(np.hypot(W5[..., 1], W5[..., 2]) / rho + np.sqrt(GAMMA * P / rho))
+    cfg = oracle.make_cfg(gamma=GAMMA, eta=1.0, limiter=1, entropy=1, mach_th=mach_th)
+    out = oracle.step(pos, W[ix, iy] * h ** 3, box, cfg, dt=dt)
+    ref, n_energy = step_2d_entropy(W, h, dt, mach_th, oracle)
+    ref = ref[ix, iy]
+    scale = np.abs(ref).max(axis=0)
+    scale[1:4] = scale[1:4].max()
+    err = np.abs(out["U"] - ref).max(axis=0) / scale
+    print(f"[2d entropy mach_th {mach_th}] energy cells {n_energy} of {nx * ny}; {err}")
+    assert np.all(err <= 1e-13), err
+    if mach_th == 1.02:
+        assert 0 < n_energy < nx * ny
