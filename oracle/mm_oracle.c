@@ -759,16 +759,19 @@ void orc_gradient(int64_t n, int64_t nf, const int32_t *fi, const int32_t *fj, c
                     else if (del < 0.0) p = (wmin[ng * c + k] - W[ng * c + k]) / del;
                     if (p < psi[ng * c + k]) psi[ng * c + k] = p;
                     /* the Duffell-MacFadyen ratio counts only where Delta is
-                     * nonzero (Sec. 4.1); a Delta within 2^-40 |g|_1 |d|_1, far
-                     * below what the gradient's and the centroids' own rounding
-                     * leaves, is zero in exact arithmetic (a gradient orthogonal
-                     * to d, as toward the equal-valued transverse neighbours of a
-                     * lattice) and does not count */
-                    double gd = (fabs(g[0]) + fabs(g[1]) + fabs(g[2])) * (fabs(dv[0]) + fabs(dv[1]) + fabs(dv[2]));
-                    if (cfg->limiter == 2 && fabs(del) > 0x1p-40 * gd) {
-                        double pd = cfg->theta * (W[ng * o + k] - W[ng * c + k]) / del;
-                        if (pd < 0.0) pd = 0.0;
-                        if (pd < psidm[ng * c + k]) psidm[ng * c + k] = pd;
+                     * nonzero (Sec. 4.1); a Delta within 2^-40 |g|_1 |d|_1 (well
+                     * above the ~1e-15 of it that the rounding of the gradient and
+                     * the centroids leaves, far below any Delta that matters) is
+                     * zero in exact arithmetic: a gradient orthogonal to d, as
+                     * toward the equal-valued transverse neighbours of a lattice
+                     * or across a row of symmetry; it does not count */
+                    if (cfg->limiter == 2) {
+                        double gd = (fabs(g[0]) + fabs(g[1]) + fabs(g[2])) * (fabs(dv[0]) + fabs(dv[1]) + fabs(dv[2]));
+                        if (fabs(del) > 0x1p-40 * gd) {
+                            double pd = cfg->theta * (W[ng * o + k] - W[ng * c + k]) / del;
+                            if (pd < 0.0) pd = 0.0;
+                            if (pd < psidm[ng * c + k]) psidm[ng * c + k] = pd;
+                        }
                     }
                 }
             }
