@@ -8,7 +8,11 @@ never better than the kernels' fused multiply-adds) against FP64.
   within B of the FP64 one.
 * The clipper's home-bin wall distances and ring coverage radius are FP32,
   lowered by a slack of 2e-6 max(L): the lowered values must never exceed the
-  exact ones."""
+  exact ones.
+* The clipper's FP32 vertices carry an error bound err, and its FP32 plane
+  tests a bound B built on it: err must bound the distance to the exact
+  vertex, B the error of the test value, and every sign B settles must be
+  the exact test's (tie margin included)."""
 import numpy as np
 
 U32 = np.float32
@@ -59,3 +63,93 @@ def test_clipper_wall_distances_stay_conservative():
             for r in (1, 2, 5):
                 R32 = (edge32.astype(U32) + U32(r) * bsf).astype(np.float64)
                 assert np.all(R32 * (1 - 1e-6) <= np.minimum(lo, hi) + r * bs), (L, g, r)
+
+
+def _f32(x):
+    return np.asarray(x, dtype=np.float64).astype(U32)
+
+
+def _fma(a, b, c):
+    # a * b is exact in FP64 for FP32 a, b; one rounding to FP32 after the add
+    return _f32(a.astype(np.float64) * b.astype(np.float64) + c.astype(np.float64))
+
+
+def _mul(a, b):
+    return _f32(a.astype(np.float64) * b.astype(np.float64))
+
+
+def _vertex32(qa, oa, qb, ob, qc, oc):
+    """The clipper's FP32 vertex of three planes q.v = o (Cramer's rule with
+    fused multiply-adds and a correctly rounded reciprocal) and its error
+    bound err = 3 u H (5.5 (|qa| + |qb| + |qc|) + 13 |v|_1), H = |qa||qb||qc| /
+    |det|; +inf where the kernel solves in FP64 instead."""
+    (ax, ay, az), (bx, by, bz), (cx, cy, cz) = (_f32(q).T for q in (qa, qb, qc))
+    ao, bo, co = _f32(oa), _f32(ob), _f32(oc)
+    bcx, bcy, bcz = _fma(by, cz, -_mul(bz, cy)), _fma(bz, cx, -_mul(bx, cz)), _fma(bx, cy, -_mul(by, cx))
+    cax, cay, caz = _fma(cy, az, -_mul(cz, ay)), _fma(cz, ax, -_mul(cx, az)), _fma(cx, ay, -_mul(cy, ax))
+    abx, aby, abz = _fma(ay, bz, -_mul(az, by)), _fma(az, bx, -_mul(ax, bz)), _fma(ax, by, -_mul(ay, bx))
+    det = _fma(ax, bcx, _fma(ay, bcy, _mul(az, bcz)))
+    with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
+        inv = _f32(1.0 / det.astype(np.float64))
+        x = _mul(_fma(ao, bcx, _fma(bo, cax, _mul(co, abx))), inv)
+        y = _mul(_fma(ao, bcy, _fma(bo, cay, _mul(co, aby))), inv)
+        z = _mul(_fma(ao, bcz, _fma(bo, caz, _mul(co, abz))), inv)
+        la, lb, lc = (np.sqrt(_mul(U32(2.0), o)) for o in (ao, bo, co))
+        H = _mul(_mul(_mul(la, lb), lc), np.abs(inv))
+        vn = np.abs(x) + np.abs(y) + np.abs(z)
+        u = U32(5.9604645e-8)
+        err = _mul(_mul(_mul(U32(3.0), u), H), U32(5.5) * (la + lb + lc) + U32(13.0) * vn)
+        ok = (u * H < U32(1e-3)) & (err < U32(1e30)) & (np.minimum(np.minimum(la, lb), lc) >= U32(3.7252903e-9)) \
+            & (np.maximum(np.maximum(la, lb), lc) <= U32(268435456.0))
+    return np.stack([x, y, z], 1), np.where(ok, err, np.inf)
+
+
+def test_clipper_vertex_and_plane_test_bounds():
+    """The filtered clipper classifies a vertex against a plane in FP32 and
+    trusts the sign of s = q.v - o only beyond its bound B = |q| err +
+    16 u (|q_x v_x| + |q_y v_y| + |q_z v_z| + o).  Emulated here: the FP32
+    vertex of three bisector planes and its err must bound the distance to
+    the exact vertex, B the error of s, and every sign B settles must be
+    the exact test's, the kernel's tie margin (2^13 units in the last place
+    of o) included.  Planes are bisectors of neighbours at distances 0.3..3
+    (o = |q|^2 / 2), some nearly parallel (ill-conditioned), at scales
+    2^-20, 1 and 2^20."""
+    rng = np.random.default_rng(1709)
+    m = 40000
+    worst_v, worst_s, settled = 0.0, 0.0, 0
+    for scale in (2.0 ** -20, 1.0, 2.0 ** 20):
+        def planes():
+            d = rng.normal(size=(m, 3))
+            d /= np.linalg.norm(d, axis=1, keepdims=True)
+            return d * rng.uniform(0.3, 3.0, (m, 1)) * scale
+        qa, qb, qc = planes(), planes(), planes()
+        near = rng.random(m) < 0.3  # nearly parallel third plane
+        qc[near] = qb[near] * (1.0 + 1e-3 * rng.normal(size=(near.sum(), 1))) + 1e-3 * scale * rng.normal(
+            size=(near.sum(), 3))
+        o = [0.5 * (q * q).sum(1) for q in (qa, qb, qc)]
+        v32, err = _vertex32(qa, o[0], qb, o[1], qc, o[2])
+        keep = np.isfinite(err)
+        A = np.stack([qa, qb, qc], 1)[keep]
+        v = np.linalg.solve(A, np.stack(o, 1)[keep][..., None])[..., 0]
+        dv = np.linalg.norm(v32[keep].astype(np.float64) - v, axis=1)
+        assert np.all(dv <= err[keep]), np.max(dv / err[keep])
+        worst_v = max(worst_v, float(np.max(dv / err[keep])))
+        # test planes against the kept vertices
+        qt = planes()[keep]
+        ot = 0.5 * (qt * qt).sum(1)
+        fq, fo = _f32(qt), _f32(ot)
+        V = v32[keep]
+        s32 = _fma(fq[:, 0], V[:, 0], _fma(fq[:, 1], V[:, 1], _fma(fq[:, 2], V[:, 2], -fo))).astype(np.float64)
+        mag = (np.abs(_mul(fq[:, 0], V[:, 0])) + np.abs(_mul(fq[:, 1], V[:, 1])) + np.abs(_mul(fq[:, 2], V[:, 2]))
+               + fo).astype(np.float64)
+        fqn = (np.sqrt(_mul(U32(2.0), fo)) * U32(1.0000005)).astype(np.float64)
+        B = fqn * err[keep].astype(np.float64) + 16.0 * 5.9604645e-8 * mag
+        s = (qt * v).sum(1) - ot
+        assert np.all(np.abs(s32 - s) <= B), np.max(np.abs(s32 - s) / B)
+        worst_s = max(worst_s, float(np.max(np.abs(s32 - s) / B)))
+        margin = np.spacing(ot) * 2.0 ** 13
+        beyond, inside = s32 > B * 1.00001, s32 < -B
+        assert np.all(s[beyond] > margin[beyond]) and np.all(s[inside] <= margin[inside])
+        settled += int(beyond.sum() + inside.sum())
+    print(f"[clipper bounds] worst |dv|/err {worst_v:.2f}, worst |ds|/B {worst_s:.2f}, {settled} tests settled in FP32")
+    assert settled > 0.9 * 3 * m * 0.5
