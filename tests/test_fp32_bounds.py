@@ -111,7 +111,8 @@ def test_clipper_vertex_and_plane_test_bounds():
     vertex of three bisector planes and its err must bound the distance to
     the exact vertex, B the error of s, and every sign B settles must be
     the exact test's, the kernel's tie margin (2^13 units in the last place
-    of o) included.  Planes are bisectors of neighbours at distances 0.3..3
+    of o) included; the FP32 bound of |v|^2 the security radius uses must not
+    fall below the exact one.  Planes are bisectors of neighbours at distances 0.3..3
     (o = |q|^2 / 2), some nearly parallel (ill-conditioned), at scales
     2^-20, 1 and 2^20."""
     rng = np.random.default_rng(1709)
@@ -134,6 +135,14 @@ def test_clipper_vertex_and_plane_test_bounds():
         dv = np.linalg.norm(v32[keep].astype(np.float64) - v, axis=1)
         assert np.all(dv <= err[keep]), np.max(dv / err[keep])
         worst_v = max(worst_v, float(np.max(dv / err[keep])))
+        # the security radius takes |v|^2 from the FP32 bound (|v| + err)^2 <=
+        # |v|^2 + err (2 |v|_1 + err), widened by 1e-5: never below the exact one
+        x, y, z = v32[keep].T
+        e = err[keep]
+        s2 = _fma(x, x, _fma(y, y, _mul(z, z)))
+        l1 = np.abs(x) + np.abs(y) + np.abs(z)
+        nr2 = _mul(_fma(e, _fma(U32(2.0) * np.ones_like(l1), l1, e), s2), U32(1.00001)).astype(np.float64)
+        assert np.all(nr2 >= (v * v).sum(1)), np.min(nr2 / (v * v).sum(1))
         # test planes against the kept vertices
         qt = planes()[keep]
         ot = 0.5 * (qt * qt).sum(1)
