@@ -9,6 +9,8 @@ never better than the kernels' fused multiply-adds) against FP64.
 * The clipper's home-bin wall distances and ring coverage radius are FP32,
   lowered by a slack of 2e-6 max(L): the lowered values must never exceed the
   exact ones.
+* The clipper's FP32 candidate filter keeps every neighbour image the exact
+  security-radius test keeps.
 * The clipper's FP32 vertices carry an error bound err, and its FP32 plane
   tests a bound B built on it: err must bound the distance to the exact
   vertex, B the error of the test value, and every sign B settles must be
@@ -162,3 +164,42 @@ def test_clipper_vertex_and_plane_test_bounds():
         settled += int(beyond.sum() + inside.sum())
     print(f"[clipper bounds] worst |dv|/err {worst_v:.2f}, worst |ds|/B {worst_s:.2f}, {settled} tests settled in FP32")
     assert settled > 0.9 * 3 * m * 0.5
+
+
+def test_clipper_candidate_filter_keeps_every_candidate_the_exact_test_keeps():
+    """The clipper gathers candidates with an FP32 |q|^2 (the FP32 copy of the
+    neighbour's position plus the FP32 image offset s L - p of the cell's
+    generator) against limk = 4 m (1 + 1e-5) + 2e-6 max(L) sqrt(4 m), m the
+    FP32 bound of the largest |v|^2; the exact test keeps |q|^2 <= 4 m.  At
+    the tightest case, an exact |q|^2 just inside 4 m, the FP32 filter must
+    keep it: separations from L/512 to L, image shifts of -1, 0, 1, boxes of
+    several shapes and scales."""
+    rng = np.random.default_rng(1710)
+    n = 200000
+    worst = 0.0
+    for L in (np.array([1.0, 1.0, 1.0]), np.array([1.0, 0.5, 2.0]), 2.0 ** 20 * np.array([1.0, 1.0, 0.25]),
+              2.0 ** -20 * np.array([3.0, 1.0, 1.0])):
+        Lmax = L.max()
+        p_i = rng.uniform(0.0, 1.0, (n, 3)) * L
+        shift = rng.integers(-1, 2, (n, 3))
+        # neighbour positions that put the exact separation at random lengths L/512..L
+        d = rng.normal(size=(n, 3))
+        d *= (Lmax * np.exp(rng.uniform(np.log(1.0 / 512), 0.0, (n, 1)))) / np.linalg.norm(d, axis=1, keepdims=True)
+        p_j = p_i + d - shift * L
+        ok = np.all((p_j >= 0.0) & (p_j < L), axis=1)
+        assert ok.sum() > 5000, ok.sum()
+        p_i, p_j, shift = p_i[ok], p_j[ok], shift[ok]
+        q = p_j + shift * L - p_i  # the exact separation of the candidate image
+        d2 = (q * q).sum(1)
+        m = _f32(d2 / 4.0)
+        m = np.where(4.0 * m.astype(np.float64) < d2, np.nextafter(m, U32(np.inf)), m)  # smallest FP32 with d2 <= 4 m
+        off = _f32(shift * L - p_i)
+        q32 = _f32(_f32(p_j).astype(np.float64) + off.astype(np.float64))
+        d2f = _fma(q32[:, 0], q32[:, 0], _fma(q32[:, 1], q32[:, 1], _mul(q32[:, 2], q32[:, 2])))
+        m4 = _mul(U32(4.0), m)
+        slack = _f32(2e-6 * Lmax)
+        limk = _fma(m4, U32(1.00001) * np.ones_like(m4), _mul(slack * np.ones_like(m4), np.sqrt(m4)))
+        assert np.all(d2f <= limk), np.max(d2f.astype(np.float64) - limk)
+        worst = max(worst, float(np.max((d2f.astype(np.float64) - 4.0 * m) / (limk.astype(np.float64) - 4.0 * m))))
+    print(f"[candidate filter] worst use of the margin {worst:.2f}")
+    assert worst < 1.0
